@@ -1,0 +1,315 @@
+"""Seeded synthetic inputs for syndrome-based LDPC reconciliation.
+
+This module builds parity-check matrices and channel frames.  It holds none of
+the decoder's arithmetic: it draws codes, bits, Gaussian noise and channel
+LLRs, and forms the syndrome s = H x (mod 2) that Alice would send (the
+decoder's input in syndrome-based reconciliation, paper section "Early
+Termination").  Both the CUDA decoder's tests/benchmark and the FP64 oracle
+consume what it returns; neither side imports the other.
+
+Conventions
+-----------
+* H is m x n (rows = check nodes, columns = variable nodes).
+* LLR L = ln P(x=0)/P(x=1); BPSK maps bit 0 -> +1, bit 1 -> -1, so with
+  y = (1 - 2x) + sigma * z the channel LLR is Lch = 2 y / sigma^2.
+* The noise level is set through the reconciliation efficiency
+  beta = R / C (section "Secret Key Rate"), with C the binary-input AWGN
+  capacity, solved for sigma by bisection.
+
+Seeds: a code of workload number c uses seed 1000 + c; frame f of workload c
+uses seed 2000 * c + f, each an independent numpy PCG64 stream.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = [
+    "CSRCode", "QCCode", "Frames", "random_csr_code", "qc_base_matrix",
+    "random_qc_code", "biawgn_capacity", "sigma_for_capacity", "make_frames",
+    "syndrome", "WORKLOADS", "workload_code", "workload_frames",
+]
+
+
+# --------------------------------------------------------------------------
+# Parity-check matrices
+# --------------------------------------------------------------------------
+@dataclass
+class CSRCode:
+    """Binary H in compressed-sparse-row form; columns sorted in each row."""
+    m: int
+    n: int
+    rowptr: np.ndarray  # int32 [m+1]
+    colidx: np.ndarray  # int32 [E]
+
+    @property
+    def edges(self) -> int:
+        return int(self.rowptr[-1])
+
+    @property
+    def rate(self) -> float:
+        """Design rate 1 - m/n (assumes full-rank H)."""
+        return 1.0 - self.m / self.n
+
+    def check_degrees(self) -> np.ndarray:
+        return np.diff(self.rowptr).astype(np.int64)
+
+    def var_degrees(self) -> np.ndarray:
+        return np.bincount(self.colidx, minlength=self.n).astype(np.int64)
+
+    def row_of_edge(self) -> np.ndarray:
+        return np.repeat(np.arange(self.m, dtype=np.int64), self.check_degrees())
+
+
+@dataclass
+class QCCode:
+    """Quasi-cyclic H: an mb x nb base matrix of circulant shifts.
+
+    shifts[i, j] = -1 is an all-zero Z x Z block; shifts[i, j] = s >= 0 is the
+    identity cyclically shifted so that check i*Z + t meets variable
+    j*Z + (t + s) mod Z.
+    """
+    mb: int
+    nb: int
+    Z: int
+    shifts: np.ndarray  # int32 [mb, nb]
+
+    @property
+    def m(self) -> int:
+        return self.mb * self.Z
+
+    @property
+    def n(self) -> int:
+        return self.nb * self.Z
+
+    @property
+    def edges(self) -> int:
+        return int((self.shifts >= 0).sum()) * self.Z
+
+    @property
+    def rate(self) -> float:
+        return 1.0 - self.mb / self.nb
+
+    def to_csr(self) -> CSRCode:
+        """Lift to the binary m x n matrix, rows in order, columns ascending."""
+        Z = self.Z
+        t = np.arange(Z, dtype=np.int64)
+        degs = []
+        cols_per_row = []
+        for i in range(self.mb):
+            js = [j for j in range(self.nb) if self.shifts[i, j] >= 0]
+            blk = np.empty((Z, len(js)), dtype=np.int64)
+            for k, j in enumerate(js):  # ascending j => ascending column index
+                blk[:, k] = j * Z + (t + int(self.shifts[i, j])) % Z
+            cols_per_row.append(blk.reshape(-1))
+            degs.append(np.full(Z, len(js), dtype=np.int64))
+        colidx = np.concatenate(cols_per_row) if cols_per_row else np.zeros(0, np.int64)
+        rowptr = np.concatenate([[0], np.cumsum(np.concatenate(degs))]) if degs else np.zeros(1)
+        return CSRCode(self.m, self.n, rowptr.astype(np.int32), colidx.astype(np.int32))
+
+
+def _collapse_rows(m: int, n: int, rows: np.ndarray, cols: np.ndarray) -> CSRCode:
+    """Sort (row, col) pairs, drop repeated pairs (H is a 0/1 adjacency)."""
+    key = np.unique(rows.astype(np.int64) * n + cols.astype(np.int64))
+    r = key // n
+    c = key % n
+    rowptr = np.zeros(m + 1, dtype=np.int64)
+    np.add.at(rowptr, r + 1, 1)
+    rowptr = np.cumsum(rowptr)
+    return CSRCode(m, n, rowptr.astype(np.int32), c.astype(np.int32))
+
+
+def random_csr_code(n: int, m: int, var_degree: int, check_degrees: dict[int, int],
+                    seed: int) -> CSRCode:
+    """Random code by seeded socket matching.
+
+    Every variable node gets `var_degree` sockets; `check_degrees` maps a check
+    degree to how many checks carry it (assigned to checks by a seeded
+    permutation).  A seeded permutation matches the two socket lists; repeated
+    (check, variable) pairs collapse to one edge, so a few degrees may drop.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    degs = np.concatenate([np.full(cnt, d, dtype=np.int64)
+                           for d, cnt in sorted(check_degrees.items())])
+    if degs.size != m:
+        raise ValueError("check degree counts must add up to m")
+    if int(degs.sum()) != n * var_degree:
+        raise ValueError("socket counts of the two sides differ")
+    degs = rng.permutation(degs)
+    check_sockets = np.repeat(np.arange(m, dtype=np.int64), degs)
+    var_sockets = np.repeat(np.arange(n, dtype=np.int64), var_degree)
+    var_sockets = var_sockets[rng.permutation(var_sockets.size)]
+    return _collapse_rows(m, n, check_sockets, var_sockets)
+
+
+def qc_base_matrix(mb: int, nb: int, col_weights: np.ndarray, seed: int) -> np.ndarray:
+    """Seeded 0/1 base matrix with the given column weights and row weights
+    as equal as the total allows (balanced assignment).
+
+    Columns are placed in a seeded order, heaviest first; each takes the rows
+    with the most remaining capacity, ties broken by a seeded random key.
+    Row capacities are floor/ceil of (total weight / mb), the larger ones on
+    seeded rows.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    col_weights = np.asarray(col_weights, dtype=np.int64)
+    if col_weights.size != nb or col_weights.max(initial=0) > mb:
+        raise ValueError("bad column weights")
+    total = int(col_weights.sum())
+    lo, extra = divmod(total, mb)
+    cap = np.full(mb, lo, dtype=np.int64)
+    cap[rng.permutation(mb)[:extra]] += 1
+    B = np.zeros((mb, nb), dtype=np.int8)
+    order = rng.permutation(nb)
+    order = order[np.argsort(-col_weights[order], kind="stable")]
+    for j in order:
+        w = int(col_weights[j])
+        tie = rng.random(mb)
+        rows = np.lexsort((tie, -cap))[:w]
+        if np.any(cap[rows] <= 0):
+            raise RuntimeError("row capacities exhausted")
+        B[rows, j] = 1
+        cap[rows] -= 1
+    return B
+
+
+def random_qc_code(mb: int, nb: int, Z: int, col_weights, seed: int) -> QCCode:
+    """QC code: seeded balanced base matrix, circulant shifts uniform in [0, Z)."""
+    rng = np.random.Generator(np.random.PCG64(seed + 7919))
+    B = qc_base_matrix(mb, nb, np.asarray(col_weights), seed)
+    shifts = np.where(B > 0, rng.integers(0, Z, size=B.shape), -1).astype(np.int32)
+    return QCCode(mb, nb, Z, shifts)
+
+
+# --------------------------------------------------------------------------
+# Channel: BIAWGN capacity and sigma for a target efficiency
+# --------------------------------------------------------------------------
+_GH_X, _GH_W = np.polynomial.hermite.hermgauss(160)
+
+
+def biawgn_capacity(sigma: float) -> float:
+    """Capacity (bits/use) of BPSK over AWGN with noise std sigma.
+
+    C = 1 - E[log2(1 + exp(-2Y/sigma^2))], Y ~ N(1, sigma^2), by
+    Gauss-Hermite quadrature (160 nodes).
+    """
+    y = 1.0 + math.sqrt(2.0) * sigma * _GH_X
+    f = np.logaddexp(0.0, -2.0 * y / (sigma * sigma)) / math.log(2.0)
+    return float(1.0 - (_GH_W * f).sum() / math.sqrt(math.pi))
+
+
+def sigma_for_capacity(target: float, lo: float = 0.05, hi: float = 80.0) -> float:
+    """Noise std at which biawgn_capacity(sigma) = target (bisection; C falls with sigma)."""
+    if not (0.0 < target < 1.0):
+        raise ValueError("capacity target must lie in (0, 1)")
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if biawgn_capacity(mid) > target:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+# --------------------------------------------------------------------------
+# Frames
+# --------------------------------------------------------------------------
+@dataclass
+class Frames:
+    x: np.ndarray         # uint8 [F, n]  Alice's bits
+    llr: np.ndarray       # float32 [F, n] channel LLRs at Bob
+    syndrome: np.ndarray  # uint8 [F, m]  s = H x mod 2
+    sigma: np.ndarray     # float64 [F]
+
+
+def syndrome(code, x: np.ndarray) -> np.ndarray:
+    """s = H x (mod 2) for x of shape [F, n] (or [n]); uint8 result."""
+    x = np.asarray(x, dtype=np.uint8)
+    squeeze = x.ndim == 1
+    x2 = x[None, :] if squeeze else x
+    if isinstance(code, QCCode):
+        Z = code.Z
+        out = np.zeros((x2.shape[0], code.mb, Z), dtype=np.uint8)
+        xb = x2.reshape(x2.shape[0], code.nb, Z)
+        for i in range(code.mb):
+            for j in range(code.nb):
+                s = int(code.shifts[i, j])
+                if s >= 0:
+                    out[:, i, :] ^= np.roll(xb[:, j, :], -s, axis=1)
+        out = out.reshape(x2.shape[0], code.m)
+    else:
+        vals = x2[:, code.colidx].astype(np.uint8)
+        deg = code.check_degrees()
+        out = np.zeros((x2.shape[0], code.m), dtype=np.uint8)
+        nz = deg > 0
+        starts = code.rowptr[:-1][nz]
+        if vals.shape[1] > 0:
+            red = np.bitwise_xor.reduceat(vals, starts, axis=1)
+            out[:, nz] = red
+    return out[0] if squeeze else out
+
+
+def make_frames(code, sigmas, seeds) -> Frames:
+    """One frame per (sigma, seed): x ~ U{0,1}^n, y = (1-2x) + sigma z,
+    Lch = 2y/sigma^2 rounded once to float32, s = H x."""
+    sigmas = np.asarray(sigmas, dtype=np.float64)
+    F = sigmas.size
+    n = code.n
+    x = np.empty((F, n), dtype=np.uint8)
+    llr = np.empty((F, n), dtype=np.float32)
+    for f in range(F):
+        rng = np.random.Generator(np.random.PCG64(int(seeds[f])))
+        xf = rng.integers(0, 2, size=n, dtype=np.uint8)
+        z = rng.standard_normal(n)
+        y = (1.0 - 2.0 * xf.astype(np.float64)) + sigmas[f] * z
+        x[f] = xf
+        llr[f] = (2.0 * y / (sigmas[f] ** 2)).astype(np.float32)
+    return Frames(x, llr, syndrome(code, x), sigmas)
+
+
+# --------------------------------------------------------------------------
+# The named workloads
+# --------------------------------------------------------------------------
+def _qc_weights_2_3(nb: int, n_w2: int, seed: int) -> np.ndarray:
+    rng = np.random.Generator(np.random.PCG64(seed + 104729))
+    w = np.full(nb, 3, dtype=np.int64)
+    w[rng.permutation(nb)[:n_w2]] = 2
+    return w
+
+
+# number -> description; sizes follow the workloads the paper simulates
+# (N = 1e6, R = 1/50, section "Simulations") and a small oracle-sized code.
+WORKLOADS = {
+    1: dict(name="csr_n4096_r0.1", kind="csr", n=4096, m=3686, var_degree=3,
+            check_degrees={3: 2456, 4: 1230}, frames=64, beta=0.9, rate=0.1,
+            max_iter=200),
+    2: dict(name="qc_n1e6_r0.02", kind="qc", mb=49, nb=50, Z=20000, n_w2=25,
+            frames=32, beta=0.93, rate=0.02, max_iter=500),
+    5: dict(name="qc_n1e6_r0.02_stream", kind="qc", mb=49, nb=50, Z=20000, n_w2=25,
+            frames=512, beta=0.95, rate=0.02, max_iter=1000, code_from=2),
+}
+
+
+def workload_code(number: int, Z: int | None = None):
+    """Code of a named workload; Z overrides the lifting size (same base matrix)."""
+    w = WORKLOADS[number]
+    code_no = w.get("code_from", number)
+    seed = 1000 + code_no
+    if w["kind"] == "csr":
+        return random_csr_code(w["n"], w["m"], w["var_degree"], w["check_degrees"], seed)
+    weights = _qc_weights_2_3(w["nb"], w["n_w2"], seed)
+    return random_qc_code(w["mb"], w["nb"], Z or w["Z"], weights, seed)
+
+
+def workload_frames(number: int, code, frames: int | None = None, first: int = 0,
+                    beta: float | None = None) -> Frames:
+    """Frames first..first+frames-1 of a named workload at efficiency beta."""
+    w = WORKLOADS[number]
+    F = w["frames"] if frames is None else frames
+    b = w["beta"] if beta is None else beta
+    rate = w["rate"]
+    sigma = sigma_for_capacity(rate / b)
+    seeds = [2000 * number + f for f in range(first, first + F)]
+    return make_frames(code, np.full(F, sigma), seeds)
