@@ -1,0 +1,388 @@
+"""Benchmark: syndrome-based sum-product LDPC decoding with early termination.
+
+One step = one ldpc_decode call over the workload's frames (inputs resident
+in HBM): by default the n = 1,000,000, R = 0.02 QC code (49 x 50 base,
+Z = 20000), 32 frames at beta = 0.93, max 500 iterations, the paper's rule
+(PCE-ET + VNR-ET).  The same frames are also decoded with the fixed-iteration
+baselines (PCE-ET only, and no early termination) for the comparison.
+
+Prints ONE JSON line (rank 0).  `python bench.py --impl reference` times the
+FP64 CPU oracle instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2507_03509_gb300 import gen  # noqa: E402
+
+METRIC = "decoded Mbit/s (PCE+VNR early termination), n=1e6 R=0.02"
+UNIT = "Mbit/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", type=int, default=2)
+    ap.add_argument("--frames", type=int, default=None)
+    ap.add_argument("--slots", type=int, default=0, help="max_active_frames (0 = automatic)")
+    ap.add_argument("--grid", type=int, default=0, help="grid_ctas (0 = all that fit)")
+    ap.add_argument("--compare-steps", type=int, default=2, help="timed steps of each fixed-iteration rule")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    return ap.parse_args()
+
+
+def algorithmic_bytes_per_frame_iter(code) -> int:
+    """8E (c2v read + write) + 12n (Lch read, APP write, APP read once)."""
+    return 8 * int(code.edges) + 12 * int(code.n)
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2507_03509_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload_name: str):
+    """DRAM bytes per frame-iteration from the committed ncu summary, if it was
+    taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "bp_decode_kernel_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    want = kernel_source_hash()
+    for line in open(path):
+        parts = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+        if parts.get("source") == want and parts.get("workload") == workload_name:
+            return float(parts["dram_bytes_per_frame_iter"])
+    return None
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) >= 9:
+                rows.append(p)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [s for s, r in zip(sm, rows) if num(r[3]) > 200.0] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(num(r[2]) for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (the reference arm and the cpu_baseline object)
+# ---------------------------------------------------------------------------
+def oracle_iters_mean(wl_name: str, rule: str):
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_{wl_name}_{rule}.txt")
+    if not os.path.exists(path):
+        return None
+    its = [int(l.split()[1]) for l in open(path) if l.strip() and not l.startswith("#")]
+    return float(np.mean(its)) if its else None
+
+
+def time_oracle_sample(code_csr, frames, max_sample_iters: int, target_s: float):
+    """Time the oracle on one frame per core for I iterations (rule NONE, so
+    every frame runs all I); returns (seconds per frame-iteration of the whole
+    machine, cores, frames, iterations)."""
+    import oracle
+    oracle.build()
+    cores = oracle.max_threads()
+    F = min(cores, frames.llr.shape[0])
+    llr, syn = frames.llr[:F], frames.syndrome[:F]
+    t0 = time.perf_counter()
+    oracle.decode(code_csr, llr, syn, 1, oracle.RULE_NONE)
+    t1 = time.perf_counter() - t0
+    iters = int(max(1, min(max_sample_iters, target_s / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.decode(code_csr, llr, syn, iters, oracle.RULE_NONE)
+    dt = time.perf_counter() - t0
+    return dt / (F * iters), cores, F, iters, dt
+
+
+def cpu_rate(code, wl, frames, target_s, d_mean, d_src):
+    csr = code.to_csr() if hasattr(code, "to_csr") else code
+    s_fi, cores, F, iters, dt = time_oracle_sample(csr, frames, wl["max_iter"], target_s)
+    mbps = code.n / (d_mean * s_fi) / 1e6
+    sample = (f"{F} frames x {iters} iterations of the FP64 oracle ({dt:.1f} s, {cores} threads); "
+              f"per-frame-iteration time scaled to mean D = {d_mean:.1f} ({d_src})")
+    return mbps, cores, sample, s_fi
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = gen.WORKLOADS[args.workload]
+    code = gen.workload_code(args.workload)
+    frames = gen.workload_frames(args.workload, code, frames=args.frames)
+    d_mean = oracle_iters_mean(wl["name"], "pce_vnr")
+    d_src = "oracle's own decisions on these frames"
+    if d_mean is None:
+        d_mean, d_src = float(wl["max_iter"]), "max_iter (no stored oracle decisions)"
+    target = max(1.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        mbps, cores, sample, _ = cpu_rate(code, wl, frames, target, d_mean, d_src)
+        if i >= args.warmup:
+            vals.append(mbps)
+    v = float(np.mean(vals))
+    ms = code.n * frames.llr.shape[0] / (v * 1e6) * 1e3
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "frames": int(frames.llr.shape[0]), "n": code.n, "m": code.m,
+                       "edges": int(code.edges), "beta": wl["beta"], "max_iter": wl["max_iter"],
+                       "rule": "pce_vnr"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2507_03509_gb300 import build
+    build.build()
+    from paper_2507_03509_gb300 import ldpc
+
+    wl = gen.WORKLOADS[args.workload]
+    code = gen.workload_code(args.workload)
+    F = args.frames or wl["frames"]
+    frames = gen.workload_frames(args.workload, code, frames=F, first=rank * F)  # weak scaling by frames
+
+    # CPU baseline first (rank 0, N = 1), before any GPU work in this process.
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_pending = True
+    else:
+        cpu_pending = False
+
+    graph = ldpc.Graph.from_code(code)
+    llr = torch.from_numpy(frames.llr).to(dev)
+    syn = torch.from_numpy(frames.syndrome).to(dev)
+    out = (torch.empty((F, code.n), dtype=torch.uint8, device=dev), torch.empty(F, dtype=torch.uint8, device=dev),
+           torch.empty(F, dtype=torch.int32, device=dev))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream(dev)
+    B = algorithmic_bytes_per_frame_iter(code)
+
+    def one(rule, stats):
+        return ldpc.decode(graph, llr, syn, wl["max_iter"], rule, out=out, stats=stats,
+                           max_active_frames=args.slots, grid_ctas=args.grid)
+
+    def timed(rule, steps, warmup):
+        for _ in range(warmup):
+            one(rule, ldpc.ldpc_decode_stats())
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        recs = []
+        for _ in range(steps):
+            flush.fill_(1.0)  # evict the previous step's data from L2 (outside the timed events)
+            st = ldpc.ldpc_decode_stats()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one(rule, st)
+            e1.record(stream)
+            e1.synchronize()
+            recs.append(dict(ms=e0.elapsed_time(e1), kernel_ms=st.kernel_ms, fi=st.frame_iterations,
+                             launches=st.kernel_launches, grid=st.grid_ctas, slots=st.active_frames))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        res = dict(ms=sum(r["ms"] for r in recs), kernel_ms=sum(r["kernel_ms"] for r in recs),
+                   fi=sum(r["fi"] for r in recs), launches=sum(r["launches"] for r in recs),
+                   grid=recs[-1]["grid"], slots=recs[-1]["slots"], steps=steps,
+                   per_launch_kernel_ms=[r["kernel_ms"] for r in recs])
+        flags = out[1].cpu().numpy()
+        iters = out[2].cpu().numpy()
+        bits = out[0]
+        errs = (bits.cpu().numpy() != frames.x).any(1)
+        res.update(fer=float(np.mean(errs | ((flags & 1) == 0))), d_mean=float(iters.mean()),
+                   success=int(((flags & 1) > 0).sum()), aborted=int(((flags & 2) > 0).sum()),
+                   ok_frames=int((~errs & ((flags & 1) > 0)).sum()))
+        return res
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    main = timed("pce_vnr", args.steps, max(3, args.warmup))
+    clk = clocks.stop()
+
+    ms_total = main["ms"]
+    if dist:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    bits_total = code.n * F * args.steps * world
+    value = bits_total / (ms_total * 1e-3) / 1e6
+    edge_msgs = main["fi"] * 2 * code.edges / (main["ms"] * 1e-3)
+    goodput = main["ok_frames"] * code.n * code.rate * args.steps / (main["ms"] * 1e-3) / 1e6
+
+    # fixed-iteration baselines on the same frames
+    comp = {}
+    for rule in ("pce", "none"):
+        r = timed(rule, args.compare_steps, 1)
+        comp[rule] = dict(mbit_s=code.n * F * r["steps"] / (r["ms"] * 1e-3) / 1e6, d_mean=r["d_mean"],
+                          fer=r["fer"], ms_per_step=r["ms"] / r["steps"],
+                          edge_msgs_per_s=r["fi"] * 2 * code.edges / (r["ms"] * 1e-3),
+                          hbm_frac=(r["fi"] * B / (r["kernel_ms"] * 1e-3) / 1e9) / hbm_peak()[0])
+
+    # roofline of the dominant kernel (the persistent decoder)
+    peak, peak_src = hbm_peak()
+    achieved = main["fi"] * B / (main["kernel_ms"] * 1e-3) / 1e9
+    traffic_fi = measured_traffic(wl["name"])
+    per_launch_fi = main["fi"] / max(1, main["steps"])
+
+    # end to end through the host-buffer entry point (pinned memory)
+    h_llr = torch.from_numpy(frames.llr).pin_memory()
+    h_syn = torch.from_numpy(frames.syndrome).pin_memory()
+    h_bits = torch.empty((F, code.n), dtype=torch.uint8).pin_memory()
+    h_flags = torch.empty(F, dtype=torch.uint8).pin_memory()
+    h_iters = torch.empty(F, dtype=torch.int32).pin_memory()
+    e2e_steps = max(1, min(args.steps, 5))
+    for _ in range(1):
+        ldpc.decode_host(graph, h_llr.numpy(), h_syn.numpy(), wl["max_iter"], "pce_vnr",
+                         out=(h_bits.numpy(), h_flags.numpy(), h_iters.numpy()), stream=stream.cuda_stream,
+                         max_active_frames=args.slots, grid_ctas=args.grid)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ldpc.decode_host(graph, h_llr.numpy(), h_syn.numpy(), wl["max_iter"], "pce_vnr",
+                         out=(h_bits.numpy(), h_flags.numpy(), h_iters.numpy()), stream=stream.cuda_stream,
+                         max_active_frames=args.slots, grid_ctas=args.grid)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": code.n * F * e2e_steps / e2e_s / 1e6, "unit": UNIT,
+           "h2d_bytes_per_step": int(frames.llr.nbytes + frames.syndrome.nbytes),
+           "d2h_bytes_per_step": int(F * code.n + F + 4 * F)}
+
+    if cpu_pending:
+        d_mean_o = oracle_iters_mean(wl["name"], "pce_vnr")
+        src = "oracle's own decisions on these frames"
+        if d_mean_o is None:
+            d_mean_o, src = main["d_mean"], "mean D of this run"
+        mbps, cores, sample, _ = cpu_rate(code, wl, frames, args.cpu_seconds, d_mean_o, src)
+        cpu = {"value": mbps, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["name"], "frames_per_gpu": F, "n": code.n, "m": code.m, "edges": int(code.edges),
+                   "rate": code.rate, "beta": wl["beta"], "max_iter": wl["max_iter"], "rule": "pce_vnr",
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "inputs 159 MB + decoder state > L2 (129 MB); L2 also flushed between steps",
+                   "slots": main["slots"], "grid_ctas": main["grid"]},
+        "d_mean": main["d_mean"], "fer": main["fer"], "success_frames": main["success"],
+        "aborted_frames": main["aborted"], "edge_msgs_per_s": edge_msgs, "goodput_mbit_s": goodput,
+        "fixed_iteration": comp,
+        "et_speedup": {"vs_pce": comp["pce"]["ms_per_step"] / (main["ms"] / args.steps),
+                       "vs_none": comp["none"]["ms_per_step"] / (main["ms"] / args.steps)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_src,
+                     "traffic": (traffic_fi * per_launch_fi) if traffic_fi else None,
+                     "algorithmic_bytes_per_launch": per_launch_fi * B,
+                     "kernel": "bp_decode_kernel<float,QcDev>",
+                     "kernel_ms_per_launch": main["kernel_ms"] / main["steps"]},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": main["launches"],
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,173 @@
+/*
+ * ldpc.h -- C ABI of the GB300 (sm_103a) syndrome-based sum-product LDPC
+ * decoder with early termination.
+ *
+ * The operation (arXiv 2507.03509, section "Early Termination"): belief
+ * propagation on the Tanner graph of a parity-check matrix H, at most D_max
+ * iterations, each iteration a variable-node update, a check-node update
+ * (tanh/atanh rule, sign flipped by the check's syndrome bit), a hard
+ * decision with a parity check (PCE-ET: stop once H x^ = s), and the
+ * variable-node-reliability test (VNR-ET: with q^(k) the sum over variable
+ * nodes of degree > 1 of the a-posteriori LLR magnitude after iteration k,
+ * stop once q^(k) < q^(k-1)).  Its throughput K = N R (1 - FER) / D_mean
+ * (Eq. 2) is what early termination raises.
+ *
+ * Conventions used everywhere below:
+ *   - H is m x n: rows are check nodes, columns variable nodes.
+ *   - LLR L = ln P(x=0)/P(x=1); hard decision x^ = 1 iff L < 0.
+ *   - The decoded word satisfies H x^ = s (mod 2) on success.
+ *   - All sizes are element counts.  All arrays are dense and row-major.
+ *
+ * Errors: every call returns an ldpc_status; nothing aborts, traps or
+ * prints.  Argument and graph errors are found on the host before any GPU
+ * work is queued; errors found on the GPU (a syndrome byte not 0/1, a
+ * synchronisation wait that ran out) come back from the same call.
+ *
+ * Threads: graph objects may be shared between threads for reading, but
+ * one graph runs one decode at a time (its workspace is reused).
+ */
+#ifndef LDPC_GB300_LDPC_H
+#define LDPC_GB300_LDPC_H
+
+#include <stdint.h>
+
+/* Symbols of the shared library are exported explicitly; everything else in
+ * it is hidden. */
+#if defined(__GNUC__)
+#define LDPC_API __attribute__((visibility("default")))
+#else
+#define LDPC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum ldpc_status {
+    LDPC_OK = 0,
+    LDPC_ERR_INVALID_ARG = 1,   /* null pointer, bad size, bad option, syndrome byte not 0/1 */
+    LDPC_ERR_INVALID_GRAPH = 2, /* malformed CSR / QC description */
+    LDPC_ERR_OOM = 3,           /* device or pinned-host allocation failed */
+    LDPC_ERR_CUDA = 4,          /* a CUDA runtime call failed (no device, launch error, ...) */
+    LDPC_ERR_TIMEOUT = 5        /* a grid-wide wait inside the decoder ran out; results invalid */
+} ldpc_status;
+
+/* Termination rule (paper section "Early Termination"; the baselines of
+ * section "Simulations" keep PCE-ET on and vary D_max). */
+typedef enum ldpc_term_rule {
+    LDPC_TERM_NONE = 0,    /* run exactly max_iter iterations; success = (H x^ = s) at the end */
+    LDPC_TERM_PCE = 1,     /* stop with success once H x^ = s                                   */
+    LDPC_TERM_PCE_VNR = 2  /* PCE-ET, then VNR-ET: abort once q^(k) < q^(k-1)                   */
+} ldpc_term_rule;
+
+/* Output flag bits, one byte per frame. */
+#define LDPC_FLAG_SUCCESS 1u /* the final hard decision satisfies H x^ = s */
+#define LDPC_FLAG_ABORTED 2u /* VNR-ET stopped the frame                   */
+
+/* Opaque decoder graph: library-owned, device-resident, with a cached
+ * workspace that grows on demand.  Bound to the CUDA device that was current
+ * when it was created. */
+typedef struct ldpc_graph ldpc_graph;
+
+/* Optional statistics of one decode call (host struct, filled on return). */
+typedef struct ldpc_decode_stats {
+    float kernel_ms;          /* device time of the persistent decode kernel (CUDA events) */
+    float total_ms;           /* device time of everything the call queued                  */
+    int32_t kernel_launches;  /* kernels this call launched                                 */
+    int32_t grid_ctas;        /* CTAs of the persistent kernel                              */
+    int32_t threads_per_cta;
+    int32_t active_frames;    /* frames decoded concurrently (slots)                        */
+    int64_t frame_iterations; /* sum over frames of iterations run (the D of each frame)    */
+} ldpc_decode_stats;
+
+/* Decode options.  Always start from ldpc_decode_opts_init(). */
+typedef struct ldpc_decode_opts {
+    int32_t vnr_first_iter;    /* first k at which VNR-ET compares q^(k) < q^(k-1); default 2.
+                                  1 compares q^(1) with q^(0) = sum over V of |Lch|.  >= 1.   */
+    float clamp;               /* message limit LMAX: v2c and c2v are clamped to [-LMAX, LMAX];
+                                  default 25.  Must be finite and > 0.                         */
+    int32_t fp64;              /* 0: FP32 messages (default).  1: FP64 debug mode, which takes
+                                  the tanh/atanh rule literally (slow on GB300's FP64 units).  */
+    int32_t max_active_frames; /* frames decoded concurrently, 0 = automatic.  Others wait in
+                                  a queue and start as running frames terminate.  <= 1024.     */
+    int32_t grid_ctas;         /* CTAs of the persistent kernel, 0 = all that fit on the GPU. */
+    int32_t trace_iters;       /* record messages of iterations 1..trace_iters (0 = off)      */
+    void* trace_c2v;           /* device [trace_iters][frames][E] check-to-variable messages,
+                                  edges in row-major order of H (CSR order; for QC codes the
+                                  lifted matrix's, columns ascending in each row).  float when
+                                  fp64 = 0, double when fp64 = 1.  May be NULL.                 */
+    void* trace_app;           /* device [trace_iters][frames][n] a-posteriori LLRs; float or
+                                  double as above.  May be NULL.                               */
+    double* trace_q;           /* device [trace_iters][frames] q^(k).  May be NULL.           */
+    ldpc_decode_stats* stats;  /* host; filled when not NULL                                   */
+} ldpc_decode_opts;
+
+/* Fill *opts with the defaults (vnr_first_iter 2, clamp 25, FP32, automatic
+ * concurrency and grid, no trace, no stats).  NULL is ignored. */
+LDPC_API void ldpc_decode_opts_init(ldpc_decode_opts* opts);
+
+/* Build a decoder graph from a binary H in check-major CSR form (paper:
+ * "a bipartite graph, which is defined by the parity check matrix H").
+ *   m, n     : checks, variables (m >= 1, n >= 1)
+ *   row_ptr  : host int32 [m+1], row_ptr[0] = 0, non-decreasing
+ *   col_idx  : host int32 [row_ptr[m]], each row strictly increasing, in [0, n)
+ *   out      : receives the new graph (set to NULL on error)
+ * Inputs are copied; the caller keeps ownership.  Limits: check degree
+ * <= 64, edges < 2^31.  Rows of degree 0 are allowed (always satisfied).
+ * Returns LDPC_ERR_INVALID_GRAPH for a malformed matrix. */
+LDPC_API ldpc_status ldpc_graph_create_csr(int32_t m, int32_t n, const int32_t* row_ptr,
+                                  const int32_t* col_idx, ldpc_graph** out);
+
+/* Build a decoder graph for a quasi-cyclic H given by an mb x nb base matrix
+ * of circulant shifts (host int32, row-major).  shifts[i*nb + j] = -1 is an
+ * all-zero Z x Z block; s in [0, Z) connects check i*Z + t to variable
+ * j*Z + (t + s) mod Z.  Limits: row weight <= 64, mb*Z, nb*Z and the edge
+ * count < 2^31.  Copied; the caller keeps ownership. */
+LDPC_API ldpc_status ldpc_graph_create_qc(int32_t mb, int32_t nb, int32_t Z, const int32_t* shifts,
+                                 ldpc_graph** out);
+
+/* Free a graph and its device workspace.  NULL is ignored.  Call it only when
+ * no decode on the graph is in flight. */
+LDPC_API void ldpc_graph_destroy(ldpc_graph* graph);
+
+/* Report m, n and the edge count (nonzeros of H).  Any output may be NULL. */
+LDPC_API ldpc_status ldpc_graph_info(const ldpc_graph* graph, int32_t* m, int32_t* n, int64_t* edges);
+
+/* Decode `frames` frames with flooding sum-product BP and the chosen
+ * termination rule (paper section "Early Termination").
+ *   llr       : device float [frames][n] channel LLRs (finite values)
+ *   syndrome  : device uint8 [frames][m], each byte 0 or 1
+ *   max_iter  : D_max >= 1
+ *   rule      : ldpc_term_rule
+ *   bits_out  : device uint8 [frames][n], the final hard decision (0/1)
+ *   flags_out : device uint8 [frames], LDPC_FLAG_* bits
+ *   iters_out : device int32 [frames], iterations run (the frame's D)
+ *   opts      : NULL for the defaults
+ *   cuda_stream : cudaStream_t to queue on (NULL = legacy default stream)
+ * All device buffers are caller-owned and must not overlap.  The work is
+ * stream-ordered; the call returns after the stream has reached its end
+ * (it reads one status word back), so outputs are ready on return.
+ * frames = 0 returns LDPC_OK without GPU work. */
+LDPC_API ldpc_status ldpc_decode(const ldpc_graph* graph, int32_t frames, const float* llr,
+                        const uint8_t* syndrome, int32_t max_iter, ldpc_term_rule rule,
+                        uint8_t* bits_out, uint8_t* flags_out, int32_t* iters_out,
+                        const ldpc_decode_opts* opts, void* cuda_stream);
+
+/* ldpc_decode with HOST buffers (same shapes and meaning): copies the inputs
+ * to library-owned device staging, decodes, copies the outputs back, and
+ * returns when they are in host memory.  Pinned host memory makes the copies
+ * asynchronous and faster; pageable memory works too.  trace_* options must
+ * be NULL here. */
+LDPC_API ldpc_status ldpc_decode_host(const ldpc_graph* graph, int32_t frames, const float* llr,
+                             const uint8_t* syndrome, int32_t max_iter, ldpc_term_rule rule,
+                             uint8_t* bits_out, uint8_t* flags_out, int32_t* iters_out,
+                             const ldpc_decode_opts* opts, void* cuda_stream);
+
+/* Static, human-readable name of a status code. */
+LDPC_API const char* ldpc_status_str(ldpc_status status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LDPC_GB300_LDPC_H */

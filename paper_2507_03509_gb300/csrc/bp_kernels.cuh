@@ -1,0 +1,813 @@
+// Device code of the GB300 syndrome-based sum-product decoder.
+//
+// One cooperative, persistent kernel runs the whole decode (paper, section
+// "Early Termination"): every step is
+//   phase A  check-node update of iteration k+1 for each running frame, with
+//            the syndrome test of the decision x^(k) fused into the same pass
+//            (the APP values it reads are the ones the decision uses);
+//            FP64 reduction of q^(k) = sum_{v in V} |APP_v^(k)|;
+//   barrier;
+//   decide   PCE-ET / VNR-ET / D_max for each running frame (every CTA takes
+//            the same decisions from the same global words);
+//   phase B  variable-node update APP^(k+1) = Lch + sum of c2v^(k+1) for the
+//            frames that go on, per-tile partials of q^(k+1); the hard
+//            decision of frames that stopped is written out, and their slot
+//            is refilled from the queue of waiting frames;
+//   barrier.
+// Frames run in "slots" (at most max_active_frames at once); stopped frames
+// cost no more work.  Barriers spin with a time limit and turn an expired
+// wait into an error word, never a hang.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ldpcgb {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kCPT = 4;                  // checks per thread in a check-node tile
+constexpr int kVPT = 4;                  // variables per thread in a variable-node tile
+constexpr int kCnTile = kThreads * kCPT;
+constexpr int kVnTile = kThreads * kVPT;
+constexpr int kMaxDeg = 64;              // largest check degree supported
+constexpr int kMaxSlots = 1024;
+
+enum : int { kErrNone = 0, kErrTimeout = 1, kErrSyndrome = 2 };
+enum : int { kModeFirst = 0, kModeFull = 1, kModeSynd = 2 };
+enum : int { kRuleNone = 0, kRulePce = 1, kRulePceVnr = 2 };
+
+struct Ctrl {
+    unsigned bar_count;
+    unsigned bar_gen;
+    int err;
+    int pad;
+    unsigned long long frame_iters;  // sum over frames of D
+};
+
+// Quasi-cyclic code: nonzero base blocks in row-major order (block id b).
+// Check i*Z + t meets variable col[b]*Z + (t + shift[b]) mod Z.
+// Messages of block b live at c2v[b*Z + p], p the variable's offset in its
+// column block, so the variable-node side reads them unrotated.
+struct QcDev {
+    int mb, nb, Z, nblk;
+    const int* row_ptr;            // [mb+1] first block of row i
+    const int* blk_col;            // [nblk]
+    const int* blk_shift;          // [nblk]
+    const int* col_ptr;            // [nb+1] into col_blk
+    const int* col_blk;            // [nblk] block ids of column j, ascending row
+};
+
+// General code: check-major CSR plus a variable-major list of edge ids.
+struct CsrDev {
+    int m, n;
+    const int* row_ptr;            // [m+1]
+    const int* col_idx;            // [E]
+    const int* var_ptr;            // [n+1]
+    const int* var_edge;           // [E] edge ids of variable v, ascending
+};
+
+template <typename T>
+struct Params {
+    int m, n;
+    long long E;
+    int frames, max_iter, rule, vnr_first_iter;
+    T lmax;
+    const float* llr;              // [frames][n]
+    const unsigned* sbits;         // [frames][swords] packed syndrome
+    int swords;
+    unsigned char* bits_out;       // [frames][n]
+    unsigned char* flags_out;      // [frames]
+    int* iters_out;                // [frames]
+    int slots;
+    T* c2v;                        // [slots][E]
+    T* app;                        // [slots][n]
+    double* qpart;                 // [slots][vn_tiles]
+    double* q0part;                // [slots][vn_tiles]
+    double* qval;                  // [slots]
+    double* q0val;                 // [slots]
+    int* unsat;                    // [2][slots]
+    Ctrl* ctrl;
+    int cn_tiles, vn_tiles;        // tiles per frame
+    int trace_iters;
+    T* trace_c2v;                  // [trace_iters][frames][E]
+    T* trace_app;                  // [trace_iters][frames][n]
+    double* trace_q;               // [trace_iters][frames]
+    unsigned long long timeout_ns;
+};
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
+__device__ __forceinline__ double ld_volatile(const double* p) { return *(const volatile double*)p; }
+
+__device__ __forceinline__ float clampm(float x, float l) { return fminf(fmaxf(x, -l), l); }
+__device__ __forceinline__ double clampm(double x, double l) { return fmin(fmax(x, -l), l); }
+__device__ __forceinline__ float absm(float x) { return fabsf(x); }
+__device__ __forceinline__ double absm(double x) { return fabs(x); }
+
+// Grid-wide barrier for a cooperative launch.  Thread 0 of each CTA arrives
+// on a counter; the last arrival resets it and releases a new generation.
+// A wait longer than timeout_ns (or any error raised elsewhere) ends it with
+// the error word set; the return value says whether the decode may go on.
+__device__ __forceinline__ bool grid_sync(Ctrl* ctrl, unsigned long long timeout_ns) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned gen = ld_acquire(&ctrl->bar_gen);
+        __threadfence();
+        const unsigned prev = atomicAdd(&ctrl->bar_count, 1u);
+        if (prev == gridDim.x - 1) {
+            ctrl->bar_count = 0;
+            st_release(&ctrl->bar_gen, gen + 1);
+        } else {
+            const unsigned long long t0 = global_ns();
+            unsigned spins = 0;
+            while (ld_acquire(&ctrl->bar_gen) == gen) {
+                if (ld_volatile(&ctrl->err) != kErrNone) break;
+                if (++spins > 64) __nanosleep(128);
+                if (global_ns() - t0 > timeout_ns) {
+                    atomicCAS(&ctrl->err, kErrNone, kErrTimeout);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ld_volatile(&ctrl->err) == kErrNone;
+}
+
+// ---------------------------------------------------------------------------
+// Check-node cores.  In: clamped v2c messages v[0..D).  Out: c2v messages
+// c2v_k = (1 - 2 s) * prod_{j != k} sgn(v_j) * |v_0 [+] ... (skip k) ... [+] v_{D-1}|
+// where [+] is the boxplus, 2 atanh(tanh(a/2) tanh(b/2)).
+//
+// FP32: signs and magnitudes are kept apart, so the rule is exactly odd in
+// every input.  A magnitude x maps to r = exp(-x); boxplus of magnitudes is
+// then r_a (+) r_b = (r_a + r_b) / (1 + r_a r_b) -- the tanh-product identity
+// rewritten for 1 - tanh, which neither saturates nor cancels in FP32 -- and
+// the result is -ln r.  Exclusive combinations come from prefix and suffix
+// products (forward-backward); a degree-2 check copies the other message.
+// FP64 (debug): the tanh/atanh rule literally, products by explicit loop.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rcomb(float a, float b) {
+    return __fdividef(a + b, fmaf(a, b, 1.0f));
+}
+
+template <int D>
+__device__ __forceinline__ void cn_core(const float (&v)[D], unsigned sbit, float lmax,
+                                        float (&out)[D]) {
+    if constexpr (D == 1) {
+        out[0] = sbit ? -lmax : lmax;
+    } else {
+        unsigned par = sbit;
+        bool ng[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            ng[k] = v[k] < 0.0f;
+            par ^= (unsigned)ng[k];
+        }
+        float mag[D];
+        if constexpr (D == 2) {
+            mag[0] = fabsf(v[1]);
+            mag[1] = fabsf(v[0]);
+        } else {
+            float r[D], pre[D], suf[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) r[k] = __expf(-fabsf(v[k]));
+            pre[0] = r[0];
+#pragma unroll
+            for (int k = 1; k < D - 1; ++k) pre[k] = rcomb(pre[k - 1], r[k]);
+            suf[D - 1] = r[D - 1];
+#pragma unroll
+            for (int k = D - 2; k >= 1; --k) suf[k] = rcomb(r[k], suf[k + 1]);
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                float ex = (k == 0) ? suf[1] : (k == D - 1) ? pre[D - 2] : rcomb(pre[k - 1], suf[k + 1]);
+                mag[k] = fminf(fmaxf(-__logf(ex), 0.0f), lmax);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) out[k] = (par ^ (unsigned)ng[k]) ? -mag[k] : mag[k];
+    }
+}
+
+template <int D>
+__device__ __forceinline__ void cn_core(const double (&v)[D], unsigned sbit, double lmax,
+                                        double (&out)[D]) {
+    double th[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) th[k] = tanh(0.5 * v[k]);
+    const double sg = sbit ? -1.0 : 1.0;
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        double prod = 1.0;
+#pragma unroll
+        for (int j = 0; j < D; ++j)
+            if (j != k) prod *= th[j];
+        out[k] = clampm(sg * 2.0 * atanh(prod), lmax);
+    }
+}
+
+// Degree > 8: the same rules with loops over local arrays.
+__device__ __noinline__ void cn_core_n(const float* v, int d, unsigned sbit, float lmax, float* out) {
+    float r[kMaxDeg], suf[kMaxDeg];
+    unsigned par = sbit;
+    for (int k = 0; k < d; ++k) {
+        par ^= (unsigned)(v[k] < 0.0f);
+        r[k] = __expf(-fabsf(v[k]));
+    }
+    suf[d - 1] = r[d - 1];
+    for (int k = d - 2; k >= 1; --k) suf[k] = rcomb(r[k], suf[k + 1]);
+    float pre = 0.0f;
+    for (int k = 0; k < d; ++k) {
+        float ex = (k == 0) ? suf[1] : (k == d - 1) ? pre : rcomb(pre, suf[k + 1]);
+        float mag = fminf(fmaxf(-__logf(ex), 0.0f), lmax);
+        out[k] = (par ^ (unsigned)(v[k] < 0.0f)) ? -mag : mag;
+        pre = (k == 0) ? r[0] : rcomb(pre, r[k]);
+    }
+}
+
+__device__ __noinline__ void cn_core_n(const double* v, int d, unsigned sbit, double lmax, double* out) {
+    double th[kMaxDeg];
+    for (int k = 0; k < d; ++k) th[k] = tanh(0.5 * v[k]);
+    const double sg = sbit ? -1.0 : 1.0;
+    for (int k = 0; k < d; ++k) {
+        double prod = 1.0;
+        for (int j = 0; j < d; ++j)
+            if (j != k) prod *= th[j];
+        out[k] = clampm(sg * 2.0 * atanh(prod), lmax);
+    }
+}
+
+__device__ __forceinline__ unsigned syndrome_bit(const unsigned* sb, int row) {
+    return (__ldg(sb + (row >> 5)) >> (row & 31)) & 1u;
+}
+
+// ---------------------------------------------------------------------------
+// Quasi-cyclic check-node tile: checks t0 .. t0+kCnTile-1 of base row i.
+// All loads of the tile's kCPT checks are issued before any arithmetic.
+// ---------------------------------------------------------------------------
+template <int D, typename T>
+__device__ __forceinline__ bool qc_cn_rows(const Params<T>& p, const QcDev& q, int s, int f, int k,
+                                           int mode, bool want_synd, int i, int t0, int b0) {
+    const int Z = q.Z;
+    int col[D], sh[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        col[j] = __ldg(q.blk_col + b0 + j);
+        sh[j] = __ldg(q.blk_shift + b0 + j);
+    }
+    T* c2v = p.c2v + (long long)s * p.E;
+    const T* app = p.app + (long long)s * p.n;
+    const float* llr = p.llr + (long long)f * p.n;
+    const unsigned* sb = p.sbits + (long long)f * p.swords;
+    int pos[kCPT][D];
+    T a[kCPT][D], o[kCPT][D];
+    bool ok[kCPT];
+#pragma unroll
+    for (int c = 0; c < kCPT; ++c) {
+        const int t = t0 + c * kThreads + (int)threadIdx.x;
+        ok[c] = t < Z;
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+            int pp = t + sh[j];
+            pp = pp >= Z ? pp - Z : pp;
+            pos[c][j] = pp;
+            a[c][j] = T(0);
+            o[c][j] = T(0);
+            if (ok[c]) {
+                if (mode == kModeFirst) {
+                    a[c][j] = T(__ldg(llr + (long long)col[j] * Z + pp));
+                } else {
+                    a[c][j] = app[(long long)col[j] * Z + pp];
+                    if (mode == kModeFull) o[c][j] = c2v[(long long)(b0 + j) * Z + pp];
+                }
+            }
+        }
+    }
+    bool unsat = false;
+#pragma unroll
+    for (int c = 0; c < kCPT; ++c) {
+        if (!ok[c]) continue;
+        const int t = t0 + c * kThreads + (int)threadIdx.x;
+        const unsigned sbit = syndrome_bit(sb, i * Z + t);
+        if (want_synd) {
+            unsigned pr = sbit;
+#pragma unroll
+            for (int j = 0; j < D; ++j) pr ^= (unsigned)(a[c][j] < T(0));
+            unsat |= pr != 0u;
+        }
+        if (mode == kModeSynd) continue;
+        T v[D], out[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) v[j] = clampm(a[c][j] - o[c][j], p.lmax);
+        cn_core<D>(v, sbit, p.lmax, out);
+#pragma unroll
+        for (int j = 0; j < D; ++j) c2v[(long long)(b0 + j) * Z + pos[c][j]] = out[j];
+        if (k < p.trace_iters && p.trace_c2v) {
+            T* tr = p.trace_c2v + ((long long)k * p.frames + f) * p.E + (long long)b0 * Z + (long long)t * D;
+#pragma unroll
+            for (int j = 0; j < D; ++j) tr[j] = out[j];
+        }
+    }
+    return unsat;
+}
+
+template <typename T>
+__device__ bool qc_cn_rows_n(const Params<T>& p, const QcDev& q, int s, int f, int k, int mode,
+                             bool want_synd, int i, int t0, int b0, int d) {
+    const int Z = q.Z;
+    T* c2v = p.c2v + (long long)s * p.E;
+    const T* app = p.app + (long long)s * p.n;
+    const float* llr = p.llr + (long long)f * p.n;
+    const unsigned* sb = p.sbits + (long long)f * p.swords;
+    bool unsat = false;
+    for (int c = 0; c < kCPT; ++c) {
+        const int t = t0 + c * kThreads + (int)threadIdx.x;
+        if (t >= Z) break;
+        const unsigned sbit = syndrome_bit(sb, i * Z + t);
+        T v[kMaxDeg], out[kMaxDeg];
+        unsigned pr = sbit;
+        for (int j = 0; j < d; ++j) {
+            int pp = t + __ldg(q.blk_shift + b0 + j);
+            pp = pp >= Z ? pp - Z : pp;
+            const long long vi = (long long)__ldg(q.blk_col + b0 + j) * Z + pp;
+            T a, o = T(0);
+            if (mode == kModeFirst) {
+                a = T(__ldg(llr + vi));
+            } else {
+                a = app[vi];
+                if (mode == kModeFull) o = c2v[(long long)(b0 + j) * Z + pp];
+            }
+            pr ^= (unsigned)(a < T(0));
+            v[j] = clampm(a - o, p.lmax);
+        }
+        if (want_synd) unsat |= pr != 0u;
+        if (mode == kModeSynd) continue;
+        cn_core_n(v, d, sbit, p.lmax, out);
+        for (int j = 0; j < d; ++j) {
+            int pp = t + __ldg(q.blk_shift + b0 + j);
+            pp = pp >= Z ? pp - Z : pp;
+            c2v[(long long)(b0 + j) * Z + pp] = out[j];
+        }
+        if (k < p.trace_iters && p.trace_c2v) {
+            T* tr = p.trace_c2v + ((long long)k * p.frames + f) * p.E + (long long)b0 * Z + (long long)t * d;
+            for (int j = 0; j < d; ++j) tr[j] = out[j];
+        }
+    }
+    return unsat;
+}
+
+template <typename T>
+__device__ __forceinline__ bool cn_tile(const Params<T>& p, const QcDev& q, int s, int f, int k,
+                                        int mode, bool want_synd, int tile) {
+    const int per_row = (q.Z + kCnTile - 1) / kCnTile;
+    const int i = tile / per_row;
+    const int t0 = (tile - i * per_row) * kCnTile;
+    const int b0 = __ldg(q.row_ptr + i);
+    const int d = __ldg(q.row_ptr + i + 1) - b0;
+    switch (d) {
+        case 0: {
+            bool unsat = false;
+            if (want_synd) {
+                const unsigned* sb = p.sbits + (long long)f * p.swords;
+                for (int c = 0; c < kCPT; ++c) {
+                    const int t = t0 + c * kThreads + (int)threadIdx.x;
+                    if (t < q.Z) unsat |= syndrome_bit(sb, i * q.Z + t) != 0u;
+                }
+            }
+            return unsat;
+        }
+        case 1: return qc_cn_rows<1, T>(p, q, s, f, k, mode, want_synd, i, t0, b0);
+        case 2: return qc_cn_rows<2, T>(p, q, s, f, k, mode, want_synd, i, t0, b0);
+        case 3: return qc_cn_rows<3, T>(p, q, s, f, k, mode, want_synd, i, t0, b0);
+        case 4: return qc_cn_rows<4, T>(p, q, s, f, k, mode, want_synd, i, t0, b0);
+        case 5: return qc_cn_rows<5, T>(p, q, s, f, k, mode, want_synd, i, t0, b0);
+        case 6: return qc_cn_rows<6, T>(p, q, s, f, k, mode, want_synd, i, t0, b0);
+        default: return qc_cn_rows_n<T>(p, q, s, f, k, mode, want_synd, i, t0, b0, d);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CSR check-node tile: checks tile*kCnTile ...; one check per thread-slot.
+// ---------------------------------------------------------------------------
+template <int D, typename T>
+__device__ __forceinline__ bool csr_cn_check(const Params<T>& p, const CsrDev& g, int s, int f, int k,
+                                             int mode, bool want_synd, int row, int e0) {
+    T* c2v = p.c2v + (long long)s * p.E;
+    const T* app = p.app + (long long)s * p.n;
+    const float* llr = p.llr + (long long)f * p.n;
+    const unsigned sbit = syndrome_bit(p.sbits + (long long)f * p.swords, row);
+    T a[D], o[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const int vi = __ldg(g.col_idx + e0 + j);
+        o[j] = T(0);
+        if (mode == kModeFirst) {
+            a[j] = T(__ldg(llr + vi));
+        } else {
+            a[j] = app[vi];
+            if (mode == kModeFull) o[j] = c2v[e0 + j];
+        }
+    }
+    bool unsat = false;
+    if (want_synd) {
+        unsigned pr = sbit;
+#pragma unroll
+        for (int j = 0; j < D; ++j) pr ^= (unsigned)(a[j] < T(0));
+        unsat = pr != 0u;
+    }
+    if (mode == kModeSynd) return unsat;
+    T v[D], out[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) v[j] = clampm(a[j] - o[j], p.lmax);
+    cn_core<D>(v, sbit, p.lmax, out);
+#pragma unroll
+    for (int j = 0; j < D; ++j) c2v[e0 + j] = out[j];
+    if (k < p.trace_iters && p.trace_c2v) {
+        T* tr = p.trace_c2v + ((long long)k * p.frames + f) * p.E + e0;
+#pragma unroll
+        for (int j = 0; j < D; ++j) tr[j] = out[j];
+    }
+    return unsat;
+}
+
+template <typename T>
+__device__ bool csr_cn_check_n(const Params<T>& p, const CsrDev& g, int s, int f, int k, int mode,
+                               bool want_synd, int row, int e0, int d) {
+    T* c2v = p.c2v + (long long)s * p.E;
+    const T* app = p.app + (long long)s * p.n;
+    const float* llr = p.llr + (long long)f * p.n;
+    const unsigned sbit = syndrome_bit(p.sbits + (long long)f * p.swords, row);
+    if (d == 0) return want_synd && sbit != 0u;
+    T v[kMaxDeg], out[kMaxDeg];
+    unsigned pr = sbit;
+    for (int j = 0; j < d; ++j) {
+        const int vi = __ldg(g.col_idx + e0 + j);
+        T a, o = T(0);
+        if (mode == kModeFirst) {
+            a = T(__ldg(llr + vi));
+        } else {
+            a = app[vi];
+            if (mode == kModeFull) o = c2v[e0 + j];
+        }
+        pr ^= (unsigned)(a < T(0));
+        v[j] = clampm(a - o, p.lmax);
+    }
+    const bool unsat = want_synd && pr != 0u;
+    if (mode == kModeSynd) return unsat;
+    cn_core_n(v, d, sbit, p.lmax, out);
+    for (int j = 0; j < d; ++j) c2v[e0 + j] = out[j];
+    if (k < p.trace_iters && p.trace_c2v) {
+        T* tr = p.trace_c2v + ((long long)k * p.frames + f) * p.E + e0;
+        for (int j = 0; j < d; ++j) tr[j] = out[j];
+    }
+    return unsat;
+}
+
+template <typename T>
+__device__ __forceinline__ bool cn_tile(const Params<T>& p, const CsrDev& g, int s, int f, int k,
+                                        int mode, bool want_synd, int tile) {
+    bool unsat = false;
+    for (int c = 0; c < kCPT; ++c) {
+        const int row = tile * kCnTile + c * kThreads + (int)threadIdx.x;
+        if (row >= g.m) break;
+        const int e0 = __ldg(g.row_ptr + row);
+        const int d = __ldg(g.row_ptr + row + 1) - e0;
+        switch (d) {
+            case 1: unsat |= csr_cn_check<1, T>(p, g, s, f, k, mode, want_synd, row, e0); break;
+            case 2: unsat |= csr_cn_check<2, T>(p, g, s, f, k, mode, want_synd, row, e0); break;
+            case 3: unsat |= csr_cn_check<3, T>(p, g, s, f, k, mode, want_synd, row, e0); break;
+            case 4: unsat |= csr_cn_check<4, T>(p, g, s, f, k, mode, want_synd, row, e0); break;
+            case 5: unsat |= csr_cn_check<5, T>(p, g, s, f, k, mode, want_synd, row, e0); break;
+            case 6: unsat |= csr_cn_check<6, T>(p, g, s, f, k, mode, want_synd, row, e0); break;
+            default: unsat |= csr_cn_check_n<T>(p, g, s, f, k, mode, want_synd, row, e0, d); break;
+        }
+    }
+    return unsat;
+}
+
+// ---------------------------------------------------------------------------
+// Variable-node tiles: APP^(k+1) = Lch + sum of c2v^(k+1) over the variable's
+// checks in ascending check order; per-tile sum of |APP| over V (degree > 1)
+// and, for the first iteration, of |Lch| over V.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void tile_sum_store(T acc, double* dst, double* s_red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) s_red[warp] = double(acc);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) t += s_red[w];
+        *dst = t;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void vn_tile(const Params<T>& p, const QcDev& q, int s, int f, int k, int tile,
+                                        double* s_red) {
+    const int Z = q.Z;
+    const int per_col = (Z + kVnTile - 1) / kVnTile;
+    const int j = tile / per_col;
+    const int u0 = (tile - j * per_col) * kVnTile;
+    const int cb0 = __ldg(q.col_ptr + j);
+    const int dv = __ldg(q.col_ptr + j + 1) - cb0;
+    const bool inV = dv > 1;
+    const bool want_q0 = (k == 0) && p.vnr_first_iter <= 1;
+    const T* c2v = p.c2v + (long long)s * p.E;
+    T* app = p.app + (long long)s * p.n;
+    const float* llr = p.llr + (long long)f * p.n;
+    T acc = T(0), acc0 = T(0);
+#pragma unroll
+    for (int c = 0; c < kVPT; ++c) {
+        const int u = u0 + c * kThreads + (int)threadIdx.x;
+        if (u < Z) {
+            const long long vi = (long long)j * Z + u;
+            const T L = T(__ldg(llr + vi));
+            T sum = L;
+            for (int b = 0; b < dv; ++b) sum += c2v[(long long)__ldg(q.col_blk + cb0 + b) * Z + u];
+            app[vi] = sum;
+            if (inV) {
+                acc += absm(sum);
+                acc0 += absm(L);
+            }
+            if (k < p.trace_iters && p.trace_app)
+                p.trace_app[((long long)k * p.frames + f) * p.n + vi] = sum;
+        }
+    }
+    tile_sum_store(acc, p.qpart + (long long)s * p.vn_tiles + tile, s_red);
+    if (want_q0) tile_sum_store(acc0, p.q0part + (long long)s * p.vn_tiles + tile, s_red);
+}
+
+template <typename T>
+__device__ __forceinline__ void vn_tile(const Params<T>& p, const CsrDev& g, int s, int f, int k, int tile,
+                                        double* s_red) {
+    const bool want_q0 = (k == 0) && p.vnr_first_iter <= 1;
+    const T* c2v = p.c2v + (long long)s * p.E;
+    T* app = p.app + (long long)s * p.n;
+    const float* llr = p.llr + (long long)f * p.n;
+    T acc = T(0), acc0 = T(0);
+#pragma unroll
+    for (int c = 0; c < kVPT; ++c) {
+        const int v = tile * kVnTile + c * kThreads + (int)threadIdx.x;
+        if (v < g.n) {
+            const int a0 = __ldg(g.var_ptr + v), a1 = __ldg(g.var_ptr + v + 1);
+            const T L = T(__ldg(llr + v));
+            T sum = L;
+            for (int a = a0; a < a1; ++a) sum += c2v[__ldg(g.var_edge + a)];
+            app[v] = sum;
+            if (a1 - a0 > 1) {
+                acc += absm(sum);
+                acc0 += absm(L);
+            }
+            if (k < p.trace_iters && p.trace_app) p.trace_app[((long long)k * p.frames + f) * p.n + v] = sum;
+        }
+    }
+    tile_sum_store(acc, p.qpart + (long long)s * p.vn_tiles + tile, s_red);
+    if (want_q0) tile_sum_store(acc0, p.q0part + (long long)s * p.vn_tiles + tile, s_red);
+}
+
+// Hard decision of a stopped frame: bits = [APP < 0] over the tile's variables.
+template <typename T>
+__device__ __forceinline__ void final_tile(const Params<T>& p, int s, int f, int tile) {
+    const T* app = p.app + (long long)s * p.n;
+    unsigned char* bits = p.bits_out + (long long)f * p.n;
+    for (int c = 0; c < kVPT; ++c) {
+        const long long v = (long long)tile * kVnTile + c * kThreads + threadIdx.x;
+        if (v < p.n) bits[v] = (unsigned char)(app[v] < T(0));
+    }
+}
+
+// QC tiles run per column block, so the variable index of a tile differs.
+template <typename T>
+__device__ __forceinline__ void final_tile(const Params<T>& p, const QcDev& q, int s, int f, int tile) {
+    const int per_col = (q.Z + kVnTile - 1) / kVnTile;
+    const int j = tile / per_col;
+    const int u0 = (tile - j * per_col) * kVnTile;
+    const T* app = p.app + (long long)s * p.n;
+    unsigned char* bits = p.bits_out + (long long)f * p.n;
+    for (int c = 0; c < kVPT; ++c) {
+        const int u = u0 + c * kThreads + (int)threadIdx.x;
+        if (u < q.Z) {
+            const long long v = (long long)j * q.Z + u;
+            bits[v] = (unsigned char)(app[v] < T(0));
+        }
+    }
+}
+template <typename T>
+__device__ __forceinline__ void final_tile(const Params<T>& p, const CsrDev&, int s, int f, int tile) {
+    final_tile(p, s, f, tile);
+}
+
+// Deterministic FP64 sum of a frame's per-tile partials (fixed order).
+__device__ __forceinline__ double block_sum_fixed(const double* part, int count, double* s_red) {
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < count; t += kThreads) acc += part[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) s_red[warp] = acc;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) t += s_red[w];
+    return t;  // same value in every thread
+}
+
+// ---------------------------------------------------------------------------
+// The persistent decoder.
+// ---------------------------------------------------------------------------
+template <typename T, class Code>
+__global__ void __launch_bounds__(kThreads) bp_decode_kernel(Params<T> p, Code code) {
+    extern __shared__ double smem_dyn[];
+    double* st_qprev = smem_dyn;                       // [slots]
+    int* st_frame = (int*)(st_qprev + p.slots);         // [slots]
+    int* st_k = st_frame + p.slots;                     // [slots]
+    int* st_new = st_k + p.slots;                       // [slots]
+    int* listA = st_new + p.slots;                      // [slots]
+    int* listB = listA + p.slots;                       // [slots]
+    __shared__ double s_red[kWarps];
+    __shared__ int s_nA, s_nB, s_next;
+
+    for (int s = threadIdx.x; s < p.slots; s += kThreads) {
+        st_frame[s] = s < p.frames ? s : -1;
+        st_k[s] = 0;
+        st_qprev[s] = 0.0;
+    }
+    if (threadIdx.x == 0) s_next = p.slots < p.frames ? p.slots : p.frames;
+    __syncthreads();
+    if (ld_volatile(&p.ctrl->err) != kErrNone) return;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    for (int step = 0;; ++step) {
+        const int par = step & 1;
+        // ---- running slots ------------------------------------------------
+        if (warp == 0) {
+            int cnt = 0;
+            for (int base = 0; base < p.slots; base += 32) {
+                const int s = base + lane;
+                const bool occ = s < p.slots && st_frame[s] >= 0;
+                const unsigned m = __ballot_sync(0xffffffffu, occ);
+                if (occ) listA[cnt + __popc(m & lt_mask)] = s;
+                cnt += __popc(m);
+            }
+            if (lane == 0) s_nA = cnt;
+        }
+        __syncthreads();
+        const int nA = s_nA;
+        if (nA == 0) break;
+
+        // ---- phase A: check nodes + syndrome of the current decision -----
+        const long long totalA = (long long)nA * p.cn_tiles;
+        for (long long it = blockIdx.x; it < totalA; it += gridDim.x) {
+            const int s = listA[it / p.cn_tiles];
+            const int tile = (int)(it % p.cn_tiles);
+            const int k = st_k[s];
+            const int mode = k == 0 ? kModeFirst : (k >= p.max_iter ? kModeSynd : kModeFull);
+            const bool want_synd = k >= 1 && (p.rule != kRuleNone || k >= p.max_iter);
+            const bool unsat = cn_tile<T>(p, code, s, st_frame[s], k, mode, want_synd, tile);
+            if (want_synd && __any_sync(0xffffffffu, unsat) && lane == 0)
+                atomicOr(&p.unsat[par * p.slots + s], 1);
+        }
+        // q^(k) of every running frame that has done an iteration
+        for (int i = blockIdx.x; i < nA; i += gridDim.x) {
+            const int s = listA[i];
+            const int k = st_k[s];
+            if (k < 1) continue;
+            const double qv = block_sum_fixed(p.qpart + (long long)s * p.vn_tiles, p.vn_tiles, s_red);
+            const bool with_q0 = k == 1 && p.vnr_first_iter <= 1;
+            double q0 = 0.0;
+            if (with_q0) q0 = block_sum_fixed(p.q0part + (long long)s * p.vn_tiles, p.vn_tiles, s_red);
+            if (threadIdx.x == 0) {
+                p.qval[s] = qv;
+                if (with_q0) p.q0val[s] = q0;
+                if (k <= p.trace_iters && p.trace_q) p.trace_q[(long long)(k - 1) * p.frames + st_frame[s]] = qv;
+            }
+        }
+        if (!grid_sync(p.ctrl, p.timeout_ns)) return;
+
+        // ---- decisions (warp 0 of every CTA, identical everywhere) --------
+        if (warp == 0) {
+            int cnt = 0, next = s_next;
+            for (int base = 0; base < p.slots; base += 32) {
+                const int s = base + lane;
+                int act = -1;  // 0 = continue, 1 = stop
+                if (s < p.slots && st_frame[s] >= 0) {
+                    const int k = st_k[s];
+                    const int f = st_frame[s];
+                    if (k == 0) {
+                        act = 0;
+                    } else {
+                        const bool sat = ld_volatile(&p.unsat[par * p.slots + s]) == 0;
+                        const double qv = ld_volatile(&p.qval[s]);
+                        const double qprev =
+                            (k == 1 && p.vnr_first_iter <= 1) ? ld_volatile(&p.q0val[s]) : st_qprev[s];
+                        const bool succ = p.rule != kRuleNone && sat;
+                        const bool abort_ = !succ && p.rule == kRulePceVnr && k >= p.vnr_first_iter && qv < qprev;
+                        const bool end = k >= p.max_iter;
+                        if (succ || abort_ || end) {
+                            act = 1;
+                            if (blockIdx.x == 0) {
+                                p.flags_out[f] = (unsigned char)((sat ? 1 : 0) | (abort_ ? 2 : 0));
+                                p.iters_out[f] = k;
+                                atomicAdd(&p.ctrl->frame_iters, (unsigned long long)k);
+                            }
+                        } else {
+                            act = 0;
+                            st_qprev[s] = qv;
+                        }
+                    }
+                }
+                const unsigned mAny = __ballot_sync(0xffffffffu, act >= 0);
+                const unsigned mStop = __ballot_sync(0xffffffffu, act == 1);
+                if (act >= 0) listB[cnt + __popc(mAny & lt_mask)] = s | (act << 16);
+                if (act == 1) {
+                    const int nf = next + __popc(mStop & lt_mask);
+                    st_new[s] = nf < p.frames ? nf : -1;
+                }
+                cnt += __popc(mAny);
+                next += __popc(mStop);
+            }
+            if (lane == 0) {
+                s_nB = cnt;
+                s_next = next < p.frames ? next : p.frames;
+            }
+        }
+        __syncthreads();
+        const int nB = s_nB;
+
+        // ---- phase B: variable nodes / write-out of stopped frames -------
+        const long long totalB = (long long)nB * p.vn_tiles;
+        for (long long it = blockIdx.x; it < totalB; it += gridDim.x) {
+            const int e = listB[it / p.vn_tiles];
+            const int s = e & 0xffff;
+            const int tile = (int)(it % p.vn_tiles);
+            if ((e >> 16) == 0)
+                vn_tile<T>(p, code, s, st_frame[s], st_k[s], tile, s_red);
+            else
+                final_tile<T>(p, code, s, st_frame[s], tile);
+        }
+        if (blockIdx.x == 0)
+            for (int s = threadIdx.x; s < p.slots; s += kThreads) p.unsat[(par ^ 1) * p.slots + s] = 0;
+        __syncthreads();
+        for (int i = threadIdx.x; i < nB; i += kThreads) {
+            const int e = listB[i];
+            const int s = e & 0xffff;
+            if ((e >> 16) == 0) {
+                st_k[s] += 1;
+            } else {
+                st_frame[s] = st_new[s];
+                st_k[s] = 0;
+                st_qprev[s] = 0.0;
+            }
+        }
+        if (!grid_sync(p.ctrl, p.timeout_ns)) return;
+    }
+}
+
+// Pack the syndrome bytes into bits, 32 checks per word; any byte other than
+// 0/1 raises kErrSyndrome (the decode kernel then returns at once).
+__global__ void pack_syndrome_kernel(const unsigned char* __restrict__ s, int frames, int m, int swords,
+                                     unsigned* __restrict__ out, Ctrl* ctrl) {
+    const long long nwarps_total = (long long)frames * swords;
+    const int lane = threadIdx.x & 31;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long stride = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long w = gw; w < nwarps_total; w += stride) {
+        const long long f = w / swords;
+        const int word = (int)(w - f * swords);
+        const int c = word * 32 + lane;
+        const unsigned char b = c < m ? s[f * m + c] : (unsigned char)0;
+        const unsigned bits = __ballot_sync(0xffffffffu, (b & 1u) != 0u);
+        const bool bad = __any_sync(0xffffffffu, b > 1u);
+        if (lane == 0) {
+            out[w] = bits;
+            if (bad) atomicCAS(&ctrl->err, kErrNone, kErrSyndrome);
+        }
+    }
+}
+
+}  // namespace ldpcgb

@@ -1,0 +1,498 @@
+// C ABI of the GB300 syndrome-based sum-product LDPC decoder (include/ldpc.h).
+//
+// Host side: validates graphs and arguments, keeps a device copy of each
+// graph and a workspace that grows on demand, packs the syndrome, launches
+// the cooperative persistent decoder (bp_kernels.cuh) and reads back one
+// status word.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/ldpc.h"
+#include "bp_kernels.cuh"
+
+using namespace ldpcgb;
+
+namespace {
+
+constexpr unsigned long long kBarrierTimeoutNs = 10ull * 1000ull * 1000ull * 1000ull;  // 10 s
+
+struct Workspace {
+    void* buf = nullptr;
+    size_t cap = 0;
+    Ctrl* ctrl = nullptr;      // separate small allocation
+    int* host_err = nullptr;   // pinned
+    unsigned long long* host_iters = nullptr;  // pinned
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // staging for ldpc_decode_host
+    void* stage = nullptr;
+    size_t stage_cap = 0;
+};
+
+}  // namespace
+
+struct ldpc_graph {
+    int kind = 0;  // 0 = CSR, 1 = QC
+    int device = 0;
+    int32_t m = 0, n = 0;
+    int64_t E = 0;
+    // QC description
+    int mb = 0, nb = 0, Z = 0, nblk = 0;
+    // device arrays (one allocation)
+    void* dmem = nullptr;
+    QcDev qc{};
+    CsrDev csr{};
+    int vn_tiles = 0, cn_tiles = 0;
+    Workspace ws;
+};
+
+namespace {
+
+ldpc_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return LDPC_OK;
+    if (e == cudaErrorMemoryAllocation) return LDPC_ERR_OOM;
+    return LDPC_ERR_CUDA;
+}
+
+#define LDPC_TRY(expr)                                   \
+    do {                                                 \
+        ldpc_status st_ = cuda_status(expr);             \
+        if (st_ != LDPC_OK) return st_;                  \
+    } while (0)
+
+// Upload a set of host int arrays into one device allocation.
+ldpc_status upload_arrays(const std::vector<std::vector<int>>& arrays, void** dmem,
+                          std::vector<const int*>& dptrs) {
+    size_t total = 0;
+    std::vector<size_t> off;
+    for (const auto& a : arrays) {
+        off.push_back(total);
+        total += ((a.size() * sizeof(int) + 255) / 256) * 256;
+    }
+    if (total == 0) total = 256;
+    void* d = nullptr;
+    LDPC_TRY(cudaMalloc(&d, total));
+    for (size_t i = 0; i < arrays.size(); ++i) {
+        if (!arrays[i].empty()) {
+            cudaError_t e = cudaMemcpy((char*)d + off[i], arrays[i].data(), arrays[i].size() * sizeof(int),
+                                       cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                cudaFree(d);
+                return cuda_status(e);
+            }
+        }
+        dptrs.push_back((const int*)((char*)d + off[i]));
+    }
+    *dmem = d;
+    return LDPC_OK;
+}
+
+void free_workspace(Workspace& ws) {
+    if (ws.buf) cudaFree(ws.buf);
+    if (ws.ctrl) cudaFree(ws.ctrl);
+    if (ws.host_err) cudaFreeHost(ws.host_err);
+    if (ws.host_iters) cudaFreeHost(ws.host_iters);
+    if (ws.stage) cudaFree(ws.stage);
+    for (auto& e : ws.ev)
+        if (e) cudaEventDestroy(e);
+    ws = Workspace{};
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Device layout of one decode's state.
+struct Layout {
+    size_t c2v, app, qpart, q0part, qval, q0val, unsat, sbits, total;
+};
+
+Layout make_layout(const ldpc_graph* g, int slots, size_t elem, int frames, int swords) {
+    Layout L{};
+    size_t o = 0;
+    L.c2v = o;    o = align_up(o + (size_t)slots * (size_t)g->E * elem, 256);
+    L.app = o;    o = align_up(o + (size_t)slots * (size_t)g->n * elem, 256);
+    L.qpart = o;  o = align_up(o + (size_t)slots * g->vn_tiles * sizeof(double), 256);
+    L.q0part = o; o = align_up(o + (size_t)slots * g->vn_tiles * sizeof(double), 256);
+    L.qval = o;   o = align_up(o + (size_t)slots * sizeof(double), 256);
+    L.q0val = o;  o = align_up(o + (size_t)slots * sizeof(double), 256);
+    L.unsat = o;  o = align_up(o + 2 * (size_t)slots * sizeof(int), 256);
+    L.sbits = o;  o = align_up(o + (size_t)frames * swords * sizeof(unsigned), 256);
+    L.total = o;
+    return L;
+}
+
+ldpc_status ensure_workspace(ldpc_graph* g, size_t bytes) {
+    Workspace& ws = g->ws;
+    if (!ws.ctrl) {
+        LDPC_TRY(cudaMalloc(&ws.ctrl, sizeof(Ctrl)));
+        LDPC_TRY(cudaHostAlloc(&ws.host_err, sizeof(int), cudaHostAllocDefault));
+        LDPC_TRY(cudaHostAlloc(&ws.host_iters, sizeof(unsigned long long), cudaHostAllocDefault));
+        for (auto& e : ws.ev) LDPC_TRY(cudaEventCreate(&e));
+    }
+    if (ws.cap < bytes) {
+        if (ws.buf) {
+            cudaFree(ws.buf);
+            ws.buf = nullptr;
+            ws.cap = 0;
+        }
+        LDPC_TRY(cudaMalloc(&ws.buf, bytes));
+        ws.cap = bytes;
+    }
+    return LDPC_OK;
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    cudaError_t enter(int dev) {
+        cudaError_t e = cudaGetDevice(&prev);
+        if (e != cudaSuccess) return e;
+        if (prev != dev) {
+            e = cudaSetDevice(dev);
+            changed = e == cudaSuccess;
+        }
+        return e;
+    }
+    ~DeviceGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+template <typename T, class Code>
+ldpc_status launch_decode(ldpc_graph* g, const Code& code, int frames, const float* llr,
+                          const uint8_t* syndrome, int max_iter, int rule, uint8_t* bits_out,
+                          uint8_t* flags_out, int32_t* iters_out, const ldpc_decode_opts& o,
+                          cudaStream_t stream) {
+    const int swords = (g->m + 31) / 32;
+    int slots = o.max_active_frames > 0 ? o.max_active_frames : frames;
+    slots = std::min(std::min(slots, frames), kMaxSlots);
+    const Layout L = make_layout(g, slots, sizeof(T), frames, swords);
+    ldpc_status st = ensure_workspace(g, L.total);
+    if (st != LDPC_OK) return st;
+    Workspace& ws = g->ws;
+    char* base = (char*)ws.buf;
+
+    auto kernel = bp_decode_kernel<T, Code>;
+    const size_t smem = (size_t)slots * (sizeof(double) + 5 * sizeof(int));
+    int dev = 0, sms = 0, per_sm = 0, coop = 0;
+    LDPC_TRY(cudaGetDevice(&dev));
+    LDPC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    LDPC_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) return LDPC_ERR_CUDA;
+    if (smem > 48 * 1024)
+        LDPC_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LDPC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem));
+    if (per_sm < 1) return LDPC_ERR_CUDA;
+    int grid = per_sm * sms;
+    if (o.grid_ctas > 0) grid = std::min(grid, o.grid_ctas);
+
+    Params<T> p{};
+    p.m = g->m;
+    p.n = g->n;
+    p.E = g->E;
+    p.frames = frames;
+    p.max_iter = max_iter;
+    p.rule = rule;
+    p.vnr_first_iter = o.vnr_first_iter;
+    p.lmax = T(o.clamp);
+    p.llr = llr;
+    p.sbits = (const unsigned*)(base + L.sbits);
+    p.swords = swords;
+    p.bits_out = bits_out;
+    p.flags_out = flags_out;
+    p.iters_out = iters_out;
+    p.slots = slots;
+    p.c2v = (T*)(base + L.c2v);
+    p.app = (T*)(base + L.app);
+    p.qpart = (double*)(base + L.qpart);
+    p.q0part = (double*)(base + L.q0part);
+    p.qval = (double*)(base + L.qval);
+    p.q0val = (double*)(base + L.q0val);
+    p.unsat = (int*)(base + L.unsat);
+    p.ctrl = ws.ctrl;
+    p.cn_tiles = g->cn_tiles;
+    p.vn_tiles = g->vn_tiles;
+    p.trace_iters = o.trace_iters;
+    p.trace_c2v = (T*)o.trace_c2v;
+    p.trace_app = (T*)o.trace_app;
+    p.trace_q = o.trace_q;
+    p.timeout_ns = kBarrierTimeoutNs;
+
+    const bool timing = o.stats != nullptr;
+    if (timing) LDPC_TRY(cudaEventRecord(ws.ev[0], stream));
+    LDPC_TRY(cudaMemsetAsync(ws.ctrl, 0, sizeof(Ctrl), stream));
+    LDPC_TRY(cudaMemsetAsync(p.unsat, 0, 2 * (size_t)slots * sizeof(int), stream));
+    {
+        const long long warps = (long long)frames * swords;
+        long long blocks = (warps * 32 + 255) / 256;
+        blocks = std::max(1LL, std::min(blocks, (long long)sms * 8));
+        pack_syndrome_kernel<<<(unsigned)blocks, 256, 0, stream>>>(syndrome, frames, g->m, swords,
+                                                                   (unsigned*)(base + L.sbits), ws.ctrl);
+        LDPC_TRY(cudaGetLastError());
+    }
+    if (timing) LDPC_TRY(cudaEventRecord(ws.ev[1], stream));
+    void* args[] = {(void*)&p, (void*)&code};
+    LDPC_TRY(cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(kThreads), args, smem, stream));
+    if (timing) LDPC_TRY(cudaEventRecord(ws.ev[2], stream));
+    LDPC_TRY(cudaMemcpyAsync(ws.host_err, &ws.ctrl->err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    LDPC_TRY(cudaMemcpyAsync(ws.host_iters, &ws.ctrl->frame_iters, sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, stream));
+    if (timing) LDPC_TRY(cudaEventRecord(ws.ev[3], stream));
+    LDPC_TRY(cudaStreamSynchronize(stream));
+    const int err = *ws.host_err;
+    if (timing) {
+        ldpc_decode_stats* s = o.stats;
+        cudaEventElapsedTime(&s->kernel_ms, ws.ev[1], ws.ev[2]);
+        cudaEventElapsedTime(&s->total_ms, ws.ev[0], ws.ev[3]);
+        s->kernel_launches = 2;
+        s->grid_ctas = grid;
+        s->threads_per_cta = kThreads;
+        s->active_frames = slots;
+        s->frame_iterations = (int64_t)*ws.host_iters;
+    }
+    if (err == kErrSyndrome) return LDPC_ERR_INVALID_ARG;
+    if (err == kErrTimeout) return LDPC_ERR_TIMEOUT;
+    if (err != kErrNone) return LDPC_ERR_CUDA;
+    return LDPC_OK;
+}
+
+ldpc_status check_decode_args(const ldpc_graph* graph, int32_t frames, const void* llr, const void* syndrome,
+                              int32_t max_iter, int rule, const void* bits_out, const void* flags_out,
+                              const void* iters_out, const ldpc_decode_opts& o) {
+    if (!graph || frames < 0 || max_iter < 1 || rule < LDPC_TERM_NONE || rule > LDPC_TERM_PCE_VNR)
+        return LDPC_ERR_INVALID_ARG;
+    if (frames > 0 && (!llr || !syndrome || !bits_out || !flags_out || !iters_out)) return LDPC_ERR_INVALID_ARG;
+    if (o.vnr_first_iter < 1 || !(o.clamp > 0.0f) || !std::isfinite(o.clamp)) return LDPC_ERR_INVALID_ARG;
+    if (o.fp64 != 0 && o.fp64 != 1) return LDPC_ERR_INVALID_ARG;
+    if (o.max_active_frames < 0 || o.max_active_frames > kMaxSlots || o.grid_ctas < 0 || o.trace_iters < 0)
+        return LDPC_ERR_INVALID_ARG;
+    if ((long long)frames * graph->n > (1LL << 40)) return LDPC_ERR_INVALID_ARG;
+    return LDPC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ldpc_decode_opts_init(ldpc_decode_opts* opts) {
+    if (!opts) return;
+    std::memset(opts, 0, sizeof(*opts));
+    opts->vnr_first_iter = 2;
+    opts->clamp = 25.0f;
+}
+
+const char* ldpc_status_str(ldpc_status s) {
+    switch (s) {
+        case LDPC_OK: return "ok";
+        case LDPC_ERR_INVALID_ARG: return "invalid argument";
+        case LDPC_ERR_INVALID_GRAPH: return "invalid graph";
+        case LDPC_ERR_OOM: return "out of memory";
+        case LDPC_ERR_CUDA: return "CUDA error";
+        case LDPC_ERR_TIMEOUT: return "grid synchronisation timed out";
+    }
+    return "unknown status";
+}
+
+ldpc_status ldpc_graph_create_csr(int32_t m, int32_t n, const int32_t* row_ptr, const int32_t* col_idx,
+                                  ldpc_graph** out) {
+    if (!out) return LDPC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (m < 1 || n < 1 || !row_ptr) return LDPC_ERR_INVALID_ARG;
+    if (row_ptr[0] != 0) return LDPC_ERR_INVALID_GRAPH;
+    for (int32_t r = 0; r < m; ++r) {
+        if (row_ptr[r + 1] < row_ptr[r]) return LDPC_ERR_INVALID_GRAPH;
+        if (row_ptr[r + 1] - row_ptr[r] > kMaxDeg) return LDPC_ERR_INVALID_GRAPH;
+    }
+    const int64_t E = row_ptr[m];
+    if (E > 0 && !col_idx) return LDPC_ERR_INVALID_ARG;
+    std::vector<int> vdeg(n, 0);
+    for (int32_t r = 0; r < m; ++r) {
+        for (int32_t e = row_ptr[r]; e < row_ptr[r + 1]; ++e) {
+            const int32_t v = col_idx[e];
+            if (v < 0 || v >= n) return LDPC_ERR_INVALID_GRAPH;
+            if (e > row_ptr[r] && col_idx[e - 1] >= v) return LDPC_ERR_INVALID_GRAPH;
+            vdeg[v]++;
+        }
+    }
+    std::vector<int> rp(row_ptr, row_ptr + m + 1), ci(col_idx, col_idx + E);
+    std::vector<int> vp(n + 1, 0), ve(E);
+    for (int v = 0; v < n; ++v) vp[v + 1] = vp[v] + vdeg[v];
+    std::vector<int> fill(vp.begin(), vp.end() - 1);
+    for (int64_t e = 0; e < E; ++e) ve[fill[ci[e]]++] = (int)e;  // ascending edge id per variable
+
+    ldpc_graph* g = new (std::nothrow) ldpc_graph();
+    if (!g) return LDPC_ERR_OOM;
+    cudaError_t ce = cudaGetDevice(&g->device);
+    if (ce != cudaSuccess) {
+        delete g;
+        return cuda_status(ce);
+    }
+    g->kind = 0;
+    g->m = m;
+    g->n = n;
+    g->E = E;
+    std::vector<const int*> d;
+    ldpc_status st = upload_arrays({rp, ci, vp, ve}, &g->dmem, d);
+    if (st != LDPC_OK) {
+        delete g;
+        return st;
+    }
+    g->csr = CsrDev{m, n, d[0], d[1], d[2], d[3]};
+    g->cn_tiles = (m + kCnTile - 1) / kCnTile;
+    g->vn_tiles = (n + kVnTile - 1) / kVnTile;
+    *out = g;
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_graph_create_qc(int32_t mb, int32_t nb, int32_t Z, const int32_t* shifts, ldpc_graph** out) {
+    if (!out) return LDPC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (mb < 1 || nb < 1 || Z < 1 || !shifts) return LDPC_ERR_INVALID_ARG;
+    if ((int64_t)mb * Z >= (1LL << 31) || (int64_t)nb * Z >= (1LL << 31)) return LDPC_ERR_INVALID_GRAPH;
+    std::vector<int> row_ptr(mb + 1, 0), blk_col, blk_shift, col_cnt(nb, 0);
+    for (int i = 0; i < mb; ++i) {
+        for (int j = 0; j < nb; ++j) {
+            const int32_t s = shifts[(int64_t)i * nb + j];
+            if (s < -1 || s >= Z) return LDPC_ERR_INVALID_GRAPH;
+            if (s >= 0) {
+                blk_col.push_back(j);
+                blk_shift.push_back(s);
+                col_cnt[j]++;
+            }
+        }
+        row_ptr[i + 1] = (int)blk_col.size();
+        if (row_ptr[i + 1] - row_ptr[i] > kMaxDeg) return LDPC_ERR_INVALID_GRAPH;
+    }
+    const int nblk = (int)blk_col.size();
+    if ((int64_t)nblk * Z >= (1LL << 31)) return LDPC_ERR_INVALID_GRAPH;
+    std::vector<int> col_ptr(nb + 1, 0), col_blk(nblk);
+    for (int j = 0; j < nb; ++j) col_ptr[j + 1] = col_ptr[j] + col_cnt[j];
+    std::vector<int> fill(col_ptr.begin(), col_ptr.end() - 1);
+    for (int b = 0; b < nblk; ++b) col_blk[fill[blk_col[b]]++] = b;  // row-major b => ascending row
+
+    ldpc_graph* g = new (std::nothrow) ldpc_graph();
+    if (!g) return LDPC_ERR_OOM;
+    cudaError_t ce = cudaGetDevice(&g->device);
+    if (ce != cudaSuccess) {
+        delete g;
+        return cuda_status(ce);
+    }
+    g->kind = 1;
+    g->mb = mb;
+    g->nb = nb;
+    g->Z = Z;
+    g->nblk = nblk;
+    g->m = mb * Z;
+    g->n = nb * Z;
+    g->E = (int64_t)nblk * Z;
+    std::vector<const int*> d;
+    ldpc_status st = upload_arrays({row_ptr, blk_col, blk_shift, col_ptr, col_blk}, &g->dmem, d);
+    if (st != LDPC_OK) {
+        delete g;
+        return st;
+    }
+    g->qc = QcDev{mb, nb, Z, nblk, d[0], d[1], d[2], d[3], d[4]};
+    g->cn_tiles = mb * ((Z + kCnTile - 1) / kCnTile);
+    g->vn_tiles = nb * ((Z + kVnTile - 1) / kVnTile);
+    *out = g;
+    return LDPC_OK;
+}
+
+void ldpc_graph_destroy(ldpc_graph* g) {
+    if (!g) return;
+    DeviceGuard guard;
+    guard.enter(g->device);
+    free_workspace(g->ws);
+    if (g->dmem) cudaFree(g->dmem);
+    delete g;
+}
+
+ldpc_status ldpc_graph_info(const ldpc_graph* g, int32_t* m, int32_t* n, int64_t* edges) {
+    if (!g) return LDPC_ERR_INVALID_ARG;
+    if (m) *m = g->m;
+    if (n) *n = g->n;
+    if (edges) *edges = g->E;
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_decode(const ldpc_graph* graph, int32_t frames, const float* llr, const uint8_t* syndrome,
+                        int32_t max_iter, ldpc_term_rule rule, uint8_t* bits_out, uint8_t* flags_out,
+                        int32_t* iters_out, const ldpc_decode_opts* opts, void* cuda_stream) {
+    ldpc_decode_opts o;
+    ldpc_decode_opts_init(&o);
+    if (opts) o = *opts;
+    ldpc_status st = check_decode_args(graph, frames, llr, syndrome, max_iter, (int)rule, bits_out, flags_out,
+                                       iters_out, o);
+    if (st != LDPC_OK) return st;
+    if (o.trace_iters > 0 && !o.trace_c2v && !o.trace_app && !o.trace_q) o.trace_iters = 0;
+    if (frames == 0) {
+        if (o.stats) std::memset(o.stats, 0, sizeof(*o.stats));
+        return LDPC_OK;
+    }
+    ldpc_graph* g = const_cast<ldpc_graph*>(graph);
+    DeviceGuard guard;
+    LDPC_TRY(guard.enter(g->device));
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    if (g->kind == 1) {
+        if (o.fp64)
+            return launch_decode<double>(g, g->qc, frames, llr, syndrome, max_iter, (int)rule, bits_out, flags_out,
+                                         iters_out, o, stream);
+        return launch_decode<float>(g, g->qc, frames, llr, syndrome, max_iter, (int)rule, bits_out, flags_out,
+                                    iters_out, o, stream);
+    }
+    if (o.fp64)
+        return launch_decode<double>(g, g->csr, frames, llr, syndrome, max_iter, (int)rule, bits_out, flags_out,
+                                     iters_out, o, stream);
+    return launch_decode<float>(g, g->csr, frames, llr, syndrome, max_iter, (int)rule, bits_out, flags_out,
+                                iters_out, o, stream);
+}
+
+ldpc_status ldpc_decode_host(const ldpc_graph* graph, int32_t frames, const float* llr, const uint8_t* syndrome,
+                             int32_t max_iter, ldpc_term_rule rule, uint8_t* bits_out, uint8_t* flags_out,
+                             int32_t* iters_out, const ldpc_decode_opts* opts, void* cuda_stream) {
+    ldpc_decode_opts o;
+    ldpc_decode_opts_init(&o);
+    if (opts) o = *opts;
+    ldpc_status st = check_decode_args(graph, frames, llr, syndrome, max_iter, (int)rule, bits_out, flags_out,
+                                       iters_out, o);
+    if (st != LDPC_OK) return st;
+    if (o.trace_c2v || o.trace_app || o.trace_q) return LDPC_ERR_INVALID_ARG;
+    if (frames == 0) return LDPC_OK;
+    ldpc_graph* g = const_cast<ldpc_graph*>(graph);
+    DeviceGuard guard;
+    LDPC_TRY(guard.enter(g->device));
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    const size_t n_llr = (size_t)frames * g->n * sizeof(float);
+    const size_t n_syn = (size_t)frames * g->m;
+    const size_t n_bits = (size_t)frames * g->n;
+    const size_t o_syn = align_up(n_llr, 256), o_bits = o_syn + align_up(n_syn, 256);
+    const size_t o_flags = o_bits + align_up(n_bits, 256), o_iters = o_flags + align_up((size_t)frames, 256);
+    const size_t total = o_iters + align_up((size_t)frames * sizeof(int32_t), 256);
+    Workspace& ws = g->ws;
+    if (ws.stage_cap < total) {
+        if (ws.stage) cudaFree(ws.stage);
+        ws.stage = nullptr;
+        ws.stage_cap = 0;
+        LDPC_TRY(cudaMalloc(&ws.stage, total));
+        ws.stage_cap = total;
+    }
+    char* d = (char*)ws.stage;
+    LDPC_TRY(cudaMemcpyAsync(d, llr, n_llr, cudaMemcpyHostToDevice, stream));
+    LDPC_TRY(cudaMemcpyAsync(d + o_syn, syndrome, n_syn, cudaMemcpyHostToDevice, stream));
+    st = ldpc_decode(graph, frames, (const float*)d, (const uint8_t*)(d + o_syn), max_iter, rule,
+                     (uint8_t*)(d + o_bits), (uint8_t*)(d + o_flags), (int32_t*)(d + o_iters), &o, cuda_stream);
+    if (st != LDPC_OK) return st;
+    LDPC_TRY(cudaMemcpyAsync(bits_out, d + o_bits, n_bits, cudaMemcpyDeviceToHost, stream));
+    LDPC_TRY(cudaMemcpyAsync(flags_out, d + o_flags, (size_t)frames, cudaMemcpyDeviceToHost, stream));
+    LDPC_TRY(cudaMemcpyAsync(iters_out, d + o_iters, (size_t)frames * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                             stream));
+    LDPC_TRY(cudaStreamSynchronize(stream));
+    return LDPC_OK;
+}
+
+}  // extern "C"

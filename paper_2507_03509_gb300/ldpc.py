@@ -1,0 +1,256 @@
+"""Python binding of the decoder's C ABI (include/ldpc.h): argument marshalling only.
+
+Every step of decoding runs in the CUDA library ``libldpc_gb300.so``; this
+module only passes pointers, sizes and the current CUDA stream.  Importing it
+raises ImportError when the library has not been built -- there is no
+fallback decoder.
+
+The functions keep the C names (``ldpc_graph_create_csr``,
+``ldpc_graph_create_qc``, ``ldpc_graph_destroy``, ``ldpc_graph_info``,
+``ldpc_decode``, ``ldpc_decode_host``, ``ldpc_status_str``); ``Graph`` and
+``decode`` are small conveniences on top.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libldpc_gb300.so")
+
+LDPC_OK = 0
+LDPC_ERR_INVALID_ARG = 1
+LDPC_ERR_INVALID_GRAPH = 2
+LDPC_ERR_OOM = 3
+LDPC_ERR_CUDA = 4
+LDPC_ERR_TIMEOUT = 5
+
+LDPC_TERM_NONE = 0
+LDPC_TERM_PCE = 1
+LDPC_TERM_PCE_VNR = 2
+
+LDPC_FLAG_SUCCESS = 1
+LDPC_FLAG_ABORTED = 2
+
+RULES = {"none": LDPC_TERM_NONE, "pce": LDPC_TERM_PCE, "pce_vnr": LDPC_TERM_PCE_VNR}
+
+EXPORTED = ("ldpc_decode_opts_init", "ldpc_graph_create_csr", "ldpc_graph_create_qc",
+            "ldpc_graph_destroy", "ldpc_graph_info", "ldpc_decode", "ldpc_decode_host",
+            "ldpc_status_str")
+
+
+class ldpc_decode_stats(ctypes.Structure):
+    _fields_ = [("kernel_ms", ctypes.c_float), ("total_ms", ctypes.c_float),
+                ("kernel_launches", ctypes.c_int32), ("grid_ctas", ctypes.c_int32),
+                ("threads_per_cta", ctypes.c_int32), ("active_frames", ctypes.c_int32),
+                ("frame_iterations", ctypes.c_int64)]
+
+
+class ldpc_decode_opts(ctypes.Structure):
+    _fields_ = [("vnr_first_iter", ctypes.c_int32), ("clamp", ctypes.c_float),
+                ("fp64", ctypes.c_int32), ("max_active_frames", ctypes.c_int32),
+                ("grid_ctas", ctypes.c_int32), ("trace_iters", ctypes.c_int32),
+                ("trace_c2v", ctypes.c_void_p), ("trace_app", ctypes.c_void_p),
+                ("trace_q", ctypes.c_void_p), ("stats", ctypes.POINTER(ldpc_decode_stats))]
+
+
+def _load():
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"decoder library {_LIB_PATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'` (needs nvcc)")
+    lib = ctypes.CDLL(_LIB_PATH)
+    P, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    pg = ctypes.POINTER(P)
+    lib.ldpc_decode_opts_init.argtypes = [ctypes.POINTER(ldpc_decode_opts)]
+    lib.ldpc_decode_opts_init.restype = None
+    lib.ldpc_graph_create_csr.argtypes = [i32, i32, P, P, pg]
+    lib.ldpc_graph_create_csr.restype = ctypes.c_int
+    lib.ldpc_graph_create_qc.argtypes = [i32, i32, i32, P, pg]
+    lib.ldpc_graph_create_qc.restype = ctypes.c_int
+    lib.ldpc_graph_destroy.argtypes = [P]
+    lib.ldpc_graph_destroy.restype = None
+    lib.ldpc_graph_info.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(i64)]
+    lib.ldpc_graph_info.restype = ctypes.c_int
+    dec = [P, i32, P, P, i32, ctypes.c_int, P, P, P, ctypes.POINTER(ldpc_decode_opts), P]
+    lib.ldpc_decode.argtypes = dec
+    lib.ldpc_decode.restype = ctypes.c_int
+    lib.ldpc_decode_host.argtypes = dec
+    lib.ldpc_decode_host.restype = ctypes.c_int
+    lib.ldpc_status_str.argtypes = [ctypes.c_int]
+    lib.ldpc_status_str.restype = ctypes.c_char_p
+    return lib
+
+
+_lib = _load()
+
+
+class LdpcError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {ldpc_status_str(status)} (status {status})")
+        self.status = status
+
+
+def _check(status: int, what: str):
+    if status != LDPC_OK:
+        raise LdpcError(status, what)
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+# --------------------------------------------------------------------------
+# C-named entry points
+# --------------------------------------------------------------------------
+def ldpc_status_str(status: int) -> str:
+    return _lib.ldpc_status_str(int(status)).decode()
+
+
+def ldpc_decode_opts_init() -> ldpc_decode_opts:
+    o = ldpc_decode_opts()
+    _lib.ldpc_decode_opts_init(ctypes.byref(o))
+    return o
+
+
+def ldpc_graph_create_csr(m: int, n: int, row_ptr, col_idx) -> int:
+    """Returns the opaque graph handle (int).  Raises LdpcError on failure."""
+    rp = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    ci = np.ascontiguousarray(col_idx, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(_lib.ldpc_graph_create_csr(int(m), int(n), rp.ctypes.data, ci.ctypes.data if ci.size else None,
+                                      ctypes.byref(h)), "ldpc_graph_create_csr")
+    return h.value
+
+
+def ldpc_graph_create_qc(mb: int, nb: int, Z: int, shifts) -> int:
+    sh = np.ascontiguousarray(shifts, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(_lib.ldpc_graph_create_qc(int(mb), int(nb), int(Z), sh.ctypes.data, ctypes.byref(h)),
+           "ldpc_graph_create_qc")
+    return h.value
+
+
+def ldpc_graph_destroy(handle: int) -> None:
+    _lib.ldpc_graph_destroy(handle)
+
+
+def ldpc_graph_info(handle: int):
+    m, n, e = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(_lib.ldpc_graph_info(handle, ctypes.byref(m), ctypes.byref(n), ctypes.byref(e)), "ldpc_graph_info")
+    return m.value, n.value, e.value
+
+
+def ldpc_decode(handle: int, frames: int, llr_ptr: int, syndrome_ptr: int, max_iter: int, rule: int,
+                bits_ptr: int, flags_ptr: int, iters_ptr: int, opts: ldpc_decode_opts | None,
+                stream: int) -> int:
+    """Raw call with device pointers; returns the status code."""
+    return _lib.ldpc_decode(handle, int(frames), llr_ptr, syndrome_ptr, int(max_iter), int(rule), bits_ptr,
+                            flags_ptr, iters_ptr, ctypes.byref(opts) if opts is not None else None, stream)
+
+
+def ldpc_decode_host(handle: int, frames: int, llr_ptr: int, syndrome_ptr: int, max_iter: int, rule: int,
+                     bits_ptr: int, flags_ptr: int, iters_ptr: int, opts: ldpc_decode_opts | None,
+                     stream: int) -> int:
+    """Raw call with host pointers; returns the status code."""
+    return _lib.ldpc_decode_host(handle, int(frames), llr_ptr, syndrome_ptr, int(max_iter), int(rule), bits_ptr,
+                                 flags_ptr, iters_ptr, ctypes.byref(opts) if opts is not None else None, stream)
+
+
+# --------------------------------------------------------------------------
+# Conveniences (torch tensors as device buffers)
+# --------------------------------------------------------------------------
+class Graph:
+    """Owns an ldpc_graph handle."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+        self.m, self.n, self.edges = ldpc_graph_info(handle)
+
+    @classmethod
+    def from_csr(cls, m, n, row_ptr, col_idx):
+        return cls(ldpc_graph_create_csr(m, n, row_ptr, col_idx))
+
+    @classmethod
+    def from_qc(cls, shifts, Z):
+        shifts = np.asarray(shifts)
+        return cls(ldpc_graph_create_qc(shifts.shape[0], shifts.shape[1], Z, shifts))
+
+    @classmethod
+    def from_code(cls, code):
+        """From a gen.CSRCode / gen.QCCode (anything with those fields)."""
+        if hasattr(code, "shifts"):
+            return cls.from_qc(code.shifts, code.Z)
+        return cls.from_csr(code.m, code.n, code.rowptr, code.colidx)
+
+    def close(self):
+        if self.handle:
+            ldpc_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def make_opts(vnr_first_iter=2, clamp=25.0, fp64=False, max_active_frames=0, grid_ctas=0,
+              trace_iters=0, trace_c2v=None, trace_app=None, trace_q=None, stats=None):
+    o = ldpc_decode_opts_init()
+    o.vnr_first_iter = vnr_first_iter
+    o.clamp = clamp
+    o.fp64 = 1 if fp64 else 0
+    o.max_active_frames = max_active_frames
+    o.grid_ctas = grid_ctas
+    o.trace_iters = trace_iters
+    o.trace_c2v = trace_c2v.data_ptr() if trace_c2v is not None else None
+    o.trace_app = trace_app.data_ptr() if trace_app is not None else None
+    o.trace_q = trace_q.data_ptr() if trace_q is not None else None
+    if stats is not None:
+        o.stats = ctypes.pointer(stats)
+    return o
+
+
+def decode(graph: Graph, llr, syndrome, max_iter: int, rule="pce_vnr", out=None, stream=None, **opt):
+    """Decode with device tensors (torch, cuda).  llr float32 [F, n], syndrome
+    uint8 [F, m].  Returns (bits uint8 [F, n], flags uint8 [F], iters int32 [F]).
+    Keyword options are those of make_opts()."""
+    import torch
+    rule = RULES[rule] if isinstance(rule, str) else int(rule)
+    if llr.dtype != torch.float32 or syndrome.dtype != torch.uint8:
+        raise TypeError("llr must be float32 and syndrome uint8")
+    if not (llr.is_cuda and syndrome.is_cuda and llr.is_contiguous() and syndrome.is_contiguous()):
+        raise ValueError("llr and syndrome must be contiguous CUDA tensors")
+    F = llr.shape[0]
+    if llr.shape != (F, graph.n) or syndrome.shape != (F, graph.m):
+        raise ValueError("llr / syndrome shapes do not match the graph")
+    if out is None:
+        out = (torch.empty((F, graph.n), dtype=torch.uint8, device=llr.device),
+               torch.empty(F, dtype=torch.uint8, device=llr.device),
+               torch.empty(F, dtype=torch.int32, device=llr.device))
+    bits, flags, iters = out
+    s = stream if stream is not None else torch.cuda.current_stream(llr.device)
+    o = make_opts(**opt)
+    st = ldpc_decode(graph.handle, F, llr.data_ptr(), syndrome.data_ptr(), max_iter, rule, bits.data_ptr(),
+                     flags.data_ptr(), iters.data_ptr(), o, s.cuda_stream)
+    _check(st, "ldpc_decode")
+    return bits, flags, iters
+
+
+def decode_host(graph: Graph, llr: np.ndarray, syndrome: np.ndarray, max_iter: int, rule="pce_vnr",
+                out=None, stream: int = 0, **opt):
+    """Decode host arrays (numpy, or pinned torch CPU tensors via .numpy()).
+    Returns numpy (bits, flags, iters); copies happen inside the call."""
+    rule = RULES[rule] if isinstance(rule, str) else int(rule)
+    llr = np.ascontiguousarray(llr, dtype=np.float32)
+    syndrome = np.ascontiguousarray(syndrome, dtype=np.uint8)
+    F = llr.shape[0]
+    if out is None:
+        out = (np.empty((F, graph.n), np.uint8), np.empty(F, np.uint8), np.empty(F, np.int32))
+    bits, flags, iters = out
+    o = make_opts(**opt)
+    st = ldpc_decode_host(graph.handle, F, llr.ctypes.data, syndrome.ctypes.data, max_iter, rule,
+                          bits.ctypes.data, flags.ctypes.data, iters.ctypes.data, o, stream)
+    _check(st, "ldpc_decode_host")
+    return bits, flags, iters

@@ -1,0 +1,88 @@
+"""C-ABI checks that need no GPU: the library builds for sm_103a, loads, exports
+every function that include/ldpc.h declares, and rejects malformed graphs and
+arguments on the host before any GPU work is queued."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "ldpc.h")
+
+
+@pytest.fixture(scope="module")
+def ldpc():
+    from paper_2507_03509_gb300 import build
+    build.build()
+    from paper_2507_03509_gb300 import ldpc as mod
+    return mod
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"\b(?:LDPC_API\s+)?(?:ldpc_status|void|const char\s*\*)\s+(ldpc_\w+)\s*\(", text)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("ldpc_graph_create_csr", "ldpc_graph_create_qc", "ldpc_graph_destroy", "ldpc_graph_info",
+              "ldpc_decode", "ldpc_decode_host", "ldpc_status_str", "ldpc_decode_opts_init"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(ldpc):
+    lib = ctypes.CDLL(ldpc.library_path())
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    assert set(declared_functions()) == set(ldpc.EXPORTED)
+
+
+def test_struct_layout_matches_header(ldpc):
+    # opts: 6 x 4-byte fields, then 4 pointers; stats: 2 floats, 4 ints, 1 int64
+    assert ctypes.sizeof(ldpc.ldpc_decode_opts) == 24 + 4 * 8
+    assert ctypes.sizeof(ldpc.ldpc_decode_stats) == 32
+    o = ldpc.ldpc_decode_opts_init()
+    assert o.vnr_first_iter == 2 and o.clamp == 25.0 and o.fp64 == 0 and o.trace_iters == 0
+
+
+def test_status_strings(ldpc):
+    assert ldpc.ldpc_status_str(0) == "ok"
+    assert "graph" in ldpc.ldpc_status_str(2)
+    assert ldpc.ldpc_status_str(99) == "unknown status"
+
+
+@pytest.mark.parametrize("rows,cols,n,why", [
+    ([1, 1], [0], 4, "row_ptr[0] != 0"),
+    ([0, 2, 1], [0, 1], 4, "decreasing row_ptr"),
+    ([0, 2], [1, 1], 4, "repeated column"),
+    ([0, 2], [2, 1], 4, "unsorted row"),
+    ([0, 1], [4], 4, "column out of range"),
+    ([0, 1], [-1], 4, "negative column"),
+    ([0, 65], list(range(65)), 70, "check degree above 64"),
+])
+def test_malformed_csr_is_rejected_on_host(ldpc, rows, cols, n, why):
+    with pytest.raises(ldpc.LdpcError) as ei:
+        ldpc.ldpc_graph_create_csr(len(rows) - 1, n, rows, cols)
+    assert ei.value.status == ldpc.LDPC_ERR_INVALID_GRAPH, why
+
+
+@pytest.mark.parametrize("shifts,Z,status", [
+    ([[0, 5]], 5, 2),          # shift == Z
+    ([[0, -2]], 5, 2),         # below -1
+    ([[0]], 0, 1),             # Z = 0
+    ([[0] * 65], 4, 2),        # row weight 65
+])
+def test_malformed_qc_is_rejected_on_host(ldpc, shifts, Z, status):
+    with pytest.raises(ldpc.LdpcError) as ei:
+        ldpc.ldpc_graph_create_qc(len(shifts), len(shifts[0]), Z, np.asarray(shifts))
+    assert ei.value.status == status
+
+
+def test_decode_argument_errors_need_no_gpu(ldpc):
+    # a null graph and bad sizes are refused before any CUDA call
+    assert ldpc.ldpc_decode(None, 1, 1, 1, 10, 2, 1, 1, 1, None, None) == ldpc.LDPC_ERR_INVALID_ARG
+    assert ldpc.ldpc_decode_host(None, 1, 1, 1, 10, 2, 1, 1, 1, None, None) == ldpc.LDPC_ERR_INVALID_ARG
