@@ -55,7 +55,7 @@ def _load():
             P = ctypes.c_void_p
             i64, i32, dbl = ctypes.c_int64, ctypes.c_int, ctypes.c_double
             lib.oracle_decode.argtypes = [i64, i64, P, P, i64, P, P, i32, i32, i32, dbl,
-                                          P, P, P, i32, P, P, P, i32]
+                                          P, P, P, P, i32, P, P, P, i32]
             lib.oracle_decode.restype = ctypes.c_int
             lib.oracle_max_threads.restype = ctypes.c_int
             _lib = lib
@@ -72,14 +72,15 @@ def _ptr(a):
 
 def decode(code, llr, syndrome, max_iter: int, rule: int = RULE_PCE_VNR,
            vnr_first_iter: int = 2, lmax: float = 25.0, trace_iters: int = 0,
-           threads: int = 0):
+           threads: int = 0, trace=("c2v", "app", "q"), final_app: bool = False):
     """Decode frames with the FP64 oracle.
 
     code: any object with m, n, rowptr, colidx (check-major CSR, columns sorted).
     llr: float32 [F, n]; syndrome: uint8 [F, m] (0/1).
-    Returns dict(bits uint8 [F,n], flags uint8 [F], iters int32 [F]) and, if
-    trace_iters > 0, c2v float64 [T,F,E] (CSR edge order), app [T,F,n],
-    q [T,F] (NaN where a frame stopped earlier).
+    Returns dict(bits uint8 [F,n], flags uint8 [F], iters int32 [F]); with
+    final_app, app_final float64 [F,n] (APP of the last iteration run); and,
+    if trace_iters > 0, the traces named in `trace`: c2v float64 [T,F,E] (CSR
+    edge order), app [T,F,n], q [T,F] (NaN where a frame stopped earlier).
     """
     lib = _load()
     llr = np.ascontiguousarray(llr, dtype=np.float32)
@@ -99,16 +100,20 @@ def decode(code, llr, syndrome, max_iter: int, rule: int = RULE_PCE_VNR,
     flags = np.zeros(F, dtype=np.uint8)
     iters = np.zeros(F, dtype=np.int32)
     T = int(trace_iters)
-    tc = np.full((T, F, E), np.nan) if T > 0 else None
-    ta = np.full((T, F, n), np.nan) if T > 0 else None
-    tq = np.full((T, F), np.nan) if T > 0 else None
+    tc = np.full((T, F, E), np.nan) if T > 0 and "c2v" in trace else None
+    ta = np.full((T, F, n), np.nan) if T > 0 and "app" in trace else None
+    tq = np.full((T, F), np.nan) if T > 0 and "q" in trace else None
+    af = np.zeros((F, n)) if final_app else None
     rc = lib.oracle_decode(m, n, _ptr(rowptr), _ptr(colidx), F, _ptr(llr), _ptr(syndrome),
                            int(max_iter), int(rule), int(vnr_first_iter), float(lmax),
-                           _ptr(bits), _ptr(flags), _ptr(iters), T, _ptr(tc), _ptr(ta),
+                           _ptr(bits), _ptr(flags), _ptr(iters), _ptr(af), T, _ptr(tc), _ptr(ta),
                            _ptr(tq), int(threads))
     if rc != 0:
         raise RuntimeError("oracle_decode failed (bad arguments or out of memory)")
     out = dict(bits=bits, flags=flags, iters=iters)
-    if T > 0:
-        out.update(c2v=tc, app=ta, q=tq)
+    if final_app:
+        out["app_final"] = af
+    for key, arr in (("c2v", tc), ("app", ta), ("q", tq)):
+        if arr is not None:
+            out[key] = arr
     return out

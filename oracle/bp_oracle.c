@@ -85,7 +85,7 @@ static int decode_frame(int64_t m, int64_t n, const int64_t *rowptr, const int32
                         const var_adj *va, const float *llr_f, const uint8_t *s,
                         int max_iter, int rule, int vnr_first_iter, double lmax,
                         uint8_t *bits_out, uint8_t *flag_out, int32_t *iters_out,
-                        int trace_iters, int64_t frame, int64_t frames,
+                        double *app_out, int trace_iters, int64_t frame, int64_t frames,
                         double *trace_c2v, double *trace_app, double *trace_q)
 {
     int64_t E = rowptr[m];
@@ -157,6 +157,7 @@ static int decode_frame(int64_t m, int64_t n, const int64_t *rowptr, const int32
         if (k == max_iter) success = syndrome_ok(m, rowptr, colidx, xhat, s);
     }
     memcpy(bits_out, xhat, (size_t)n);
+    if (app_out) memcpy(app_out, app, (size_t)n * sizeof(double));
     *flag_out = (uint8_t)((success ? FLAG_SUCCESS : 0) | (aborted ? FLAG_ABORTED : 0));
     *iters_out = D;
     free(c2v); free(v2c); free(Lch); free(app); free(xhat);
@@ -167,7 +168,8 @@ static int decode_frame(int64_t m, int64_t n, const int64_t *rowptr, const int32
  * Decode `frames` frames of the code H (m x n, check-major CSR with 64-bit
  * row pointers).  llr: [frames][n] float; syndrome: [frames][m] bytes 0/1.
  * Outputs: bits [frames][n], flags [frames] (bit0 success, bit1 aborted),
- * iters [frames].  Traces (optional, may be NULL): c2v [trace_iters][frames][E]
+ * iters [frames], and (optional, may be NULL) app [frames][n], the APP values
+ * of the last iteration run.  Traces (optional, may be NULL): c2v [trace_iters][frames][E]
  * in CSR edge order, app [trace_iters][frames][n], q [trace_iters][frames];
  * entries of iterations a frame did not run are left untouched.
  * threads <= 0 uses the OpenMP default.  Returns 0, or -1 on bad input or
@@ -176,7 +178,7 @@ static int decode_frame(int64_t m, int64_t n, const int64_t *rowptr, const int32
 int oracle_decode(int64_t m, int64_t n, const int64_t *rowptr, const int32_t *colidx,
                   int64_t frames, const float *llr, const uint8_t *syndrome,
                   int max_iter, int rule, int vnr_first_iter, double lmax,
-                  uint8_t *bits_out, uint8_t *flags_out, int32_t *iters_out,
+                  uint8_t *bits_out, uint8_t *flags_out, int32_t *iters_out, double *app_out,
                   int trace_iters, double *trace_c2v, double *trace_app, double *trace_q,
                   int threads)
 {
@@ -191,7 +193,8 @@ int oracle_decode(int64_t m, int64_t n, const int64_t *rowptr, const int32_t *co
     for (int64_t f = 0; f < frames; f++) {
         if (decode_frame(m, n, rowptr, colidx, &va, llr + f * n, syndrome + f * m,
                          max_iter, rule, vnr_first_iter, lmax, bits_out + f * n,
-                         flags_out + f, iters_out + f, trace_iters, f, frames,
+                         flags_out + f, iters_out + f, app_out ? app_out + f * n : NULL,
+                         trace_iters, f, frames,
                          trace_c2v, trace_app, trace_q) != 0)
             err |= 1;
     }

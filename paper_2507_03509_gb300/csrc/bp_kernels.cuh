@@ -56,6 +56,7 @@ struct QcDev {
     const int* blk_shift;          // [nblk]
     const int* col_ptr;            // [nb+1] into col_blk
     const int* col_blk;            // [nblk] block ids of column j, ascending row
+    const int* blk_row;            // [nblk] base row of block b
 };
 
 // General code: check-major CSR plus a variable-major list of edge ids.
@@ -319,11 +320,6 @@ __device__ __forceinline__ bool qc_cn_rows(const Params<T>& p, const QcDev& q, i
         cn_core<D>(v, sbit, p.lmax, out);
 #pragma unroll
         for (int j = 0; j < D; ++j) c2v[(long long)(b0 + j) * Z + pos[c][j]] = out[j];
-        if (k < p.trace_iters && p.trace_c2v) {
-            T* tr = p.trace_c2v + ((long long)k * p.frames + f) * p.E + (long long)b0 * Z + (long long)t * D;
-#pragma unroll
-            for (int j = 0; j < D; ++j) tr[j] = out[j];
-        }
     }
     return unsat;
 }
@@ -364,10 +360,6 @@ __device__ bool qc_cn_rows_n(const Params<T>& p, const QcDev& q, int s, int f, i
             int pp = t + __ldg(q.blk_shift + b0 + j);
             pp = pp >= Z ? pp - Z : pp;
             c2v[(long long)(b0 + j) * Z + pp] = out[j];
-        }
-        if (k < p.trace_iters && p.trace_c2v) {
-            T* tr = p.trace_c2v + ((long long)k * p.frames + f) * p.E + (long long)b0 * Z + (long long)t * d;
-            for (int j = 0; j < d; ++j) tr[j] = out[j];
         }
     }
     return unsat;
@@ -439,11 +431,6 @@ __device__ __forceinline__ bool csr_cn_check(const Params<T>& p, const CsrDev& g
     cn_core<D>(v, sbit, p.lmax, out);
 #pragma unroll
     for (int j = 0; j < D; ++j) c2v[e0 + j] = out[j];
-    if (k < p.trace_iters && p.trace_c2v) {
-        T* tr = p.trace_c2v + ((long long)k * p.frames + f) * p.E + e0;
-#pragma unroll
-        for (int j = 0; j < D; ++j) tr[j] = out[j];
-    }
     return unsat;
 }
 
@@ -473,10 +460,6 @@ __device__ bool csr_cn_check_n(const Params<T>& p, const CsrDev& g, int s, int f
     if (mode == kModeSynd) return unsat;
     cn_core_n(v, d, sbit, p.lmax, out);
     for (int j = 0; j < d; ++j) c2v[e0 + j] = out[j];
-    if (k < p.trace_iters && p.trace_c2v) {
-        T* tr = p.trace_c2v + ((long long)k * p.frames + f) * p.E + e0;
-        for (int j = 0; j < d; ++j) tr[j] = out[j];
-    }
     return unsat;
 }
 
@@ -523,6 +506,25 @@ __device__ __forceinline__ void tile_sum_store(T acc, double* dst, double* s_red
     }
 }
 
+// Trace of c2v^(k+1) for variable j*Z + u, written from the variable side so
+// that only iterations a frame completes are recorded.  Edge order is the
+// lifted matrix's row-major order: row i*Z + t, blocks of row i in turn.
+template <typename T>
+__device__ void trace_c2v_qc(const Params<T>& p, const QcDev& q, const T* c2v, int f, int k, int u, int cb0,
+                             int dv) {
+    const int Z = q.Z;
+    T* tr = p.trace_c2v + ((long long)k * p.frames + f) * p.E;
+    for (int b = 0; b < dv; ++b) {
+        const int blk = __ldg(q.col_blk + cb0 + b);
+        const int i = __ldg(q.blk_row + blk);
+        const int r0 = __ldg(q.row_ptr + i);
+        const int d = __ldg(q.row_ptr + i + 1) - r0;
+        int t = u - __ldg(q.blk_shift + blk);
+        t = t < 0 ? t + Z : t;
+        tr[(long long)r0 * Z + (long long)t * d + (blk - r0)] = c2v[(long long)blk * Z + u];
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void vn_tile(const Params<T>& p, const QcDev& q, int s, int f, int k, int tile,
                                         double* s_red) {
@@ -547,6 +549,7 @@ __device__ __forceinline__ void vn_tile(const Params<T>& p, const QcDev& q, int 
             T sum = L;
             for (int b = 0; b < dv; ++b) sum += c2v[(long long)__ldg(q.col_blk + cb0 + b) * Z + u];
             app[vi] = sum;
+            if (k < p.trace_iters && p.trace_c2v) trace_c2v_qc(p, q, c2v, f, k, u, cb0, dv);
             if (inV) {
                 acc += absm(sum);
                 acc0 += absm(L);
@@ -576,6 +579,10 @@ __device__ __forceinline__ void vn_tile(const Params<T>& p, const CsrDev& g, int
             T sum = L;
             for (int a = a0; a < a1; ++a) sum += c2v[__ldg(g.var_edge + a)];
             app[v] = sum;
+            if (k < p.trace_iters && p.trace_c2v) {
+                T* tr = p.trace_c2v + ((long long)k * p.frames + f) * p.E;
+                for (int a = a0; a < a1; ++a) tr[__ldg(g.var_edge + a)] = c2v[__ldg(g.var_edge + a)];
+            }
             if (a1 - a0 > 1) {
                 acc += absm(sum);
                 acc0 += absm(L);

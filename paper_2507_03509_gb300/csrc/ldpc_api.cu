@@ -370,7 +370,9 @@ ldpc_status ldpc_graph_create_qc(int32_t mb, int32_t nb, int32_t Z, const int32_
     }
     const int nblk = (int)blk_col.size();
     if ((int64_t)nblk * Z >= (1LL << 31)) return LDPC_ERR_INVALID_GRAPH;
-    std::vector<int> col_ptr(nb + 1, 0), col_blk(nblk);
+    std::vector<int> col_ptr(nb + 1, 0), col_blk(nblk), blk_row(nblk);
+    for (int i = 0; i < mb; ++i)
+        for (int b = row_ptr[i]; b < row_ptr[i + 1]; ++b) blk_row[b] = i;
     for (int j = 0; j < nb; ++j) col_ptr[j + 1] = col_ptr[j] + col_cnt[j];
     std::vector<int> fill(col_ptr.begin(), col_ptr.end() - 1);
     for (int b = 0; b < nblk; ++b) col_blk[fill[blk_col[b]]++] = b;  // row-major b => ascending row
@@ -391,12 +393,12 @@ ldpc_status ldpc_graph_create_qc(int32_t mb, int32_t nb, int32_t Z, const int32_
     g->n = nb * Z;
     g->E = (int64_t)nblk * Z;
     std::vector<const int*> d;
-    ldpc_status st = upload_arrays({row_ptr, blk_col, blk_shift, col_ptr, col_blk}, &g->dmem, d);
+    ldpc_status st = upload_arrays({row_ptr, blk_col, blk_shift, col_ptr, col_blk, blk_row}, &g->dmem, d);
     if (st != LDPC_OK) {
         delete g;
         return st;
     }
-    g->qc = QcDev{mb, nb, Z, nblk, d[0], d[1], d[2], d[3], d[4]};
+    g->qc = QcDev{mb, nb, Z, nblk, d[0], d[1], d[2], d[3], d[4], d[5]};
     g->cn_tiles = mb * ((Z + kCnTile - 1) / kCnTile);
     g->vn_tiles = nb * ((Z + kVnTile - 1) / kVnTile);
     *out = g;

@@ -61,25 +61,106 @@ def mismatched_frames(a, b):
 
 RULE_IDS = {"none": 0, "pce": 1, "pce_vnr": 2}
 
+# Rounding levels: a q step |q(k) - q(k-1)| at most RTOL_Q * q, or an APP
+# value within ATOL_APP of zero, is a near-tie whose outcome the arithmetic
+# does not fix.
+TOL = {"fp32": dict(rtol_q=2e-6, atol_app=1e-3), "fp64": dict(rtol_q=1e-11, atol_app=1e-9)}
+
+
+def validate_trajectory(oracle, code, llr_f, syn_f, res, orc, max_iter, rule, precision,
+                        vnr_first_iter=2, clamp=25.0):
+    """Check one frame's decoder result against the oracle's own trajectory.
+
+    Returns a list of problems (empty when the result is valid): the bits must
+    be the oracle's hard decision at the decoder's stopping iteration D (up to
+    APP near-ties); success must mean H x^ = s; every termination test the
+    decoder passed or took must agree with the oracle's q and decisions up to
+    near-ties (a VNR step within rounding, a PCE success hanging on an APP
+    near-tie)."""
+    from paper_2507_03509_gb300 import gen
+    tol = TOL[precision]
+    rid = RULE_IDS[rule]
+    D, Do = int(res["iters"]), int(orc["iters"])
+    fl, flo = int(res["flags"]), int(orc["flags"])
+    K = max(D, Do)
+    kw = dict(vnr_first_iter=vnr_first_iter, lmax=clamp)
+    tr = oracle.decode(code, llr_f[None], syn_f[None], K, 0, trace_iters=K, trace=("q",), **kw)
+    q = tr["q"][:, 0]
+    deg = np.bincount(code.colidx, minlength=code.n)
+    q0 = float(np.abs(llr_f.astype(np.float64))[deg > 1].sum())
+    at = oracle.decode(code, llr_f[None], syn_f[None], D, 0, final_app=True, **kw)
+    app, xo = at["app_final"][0], at["bits"][0]
+    probs = []
+    diff = res["bits"] != xo
+    if diff.any() and np.abs(app[diff]).max() > tol["atol_app"]:
+        probs.append(f"{int(diff.sum())} bits differ from the oracle's decision at k={D}, "
+                     f"max |APP| there {np.abs(app[diff]).max():.3g}")
+    synd_ok = bool((gen.syndrome(code, res["bits"]) == syn_f).all())
+    if bool(fl & 1) != synd_ok:
+        probs.append("success flag disagrees with H x^ = s")
+
+    def step(k):
+        prev = q[k - 2] if k >= 2 else q0
+        return q[k - 1] - prev
+
+    def tie(k):
+        return abs(step(k)) <= tol["rtol_q"] * abs(q[k - 1])
+
+    if rid == 0 and D != max_iter:
+        probs.append("rule none stopped early")
+    if fl & 2:
+        if not (rid == 2 and D >= vnr_first_iter and (step(D) < 0 or tie(D))):
+            probs.append(f"VNR abort at k={D} without a drop of q (step {step(D):.3g})")
+    if rid == 2:
+        for k in range(vnr_first_iter, D):
+            if step(k) < 0 and not tie(k):
+                probs.append(f"q fell clearly at k={k} (step {step(k):.3g}) but decoding went on")
+                break
+    if rid in (1, 2) and Do < D and (flo & 1):
+        ao = oracle.decode(code, llr_f[None], syn_f[None], Do, 0, final_app=True, **kw)["app_final"][0]
+        if np.abs(ao).min() > tol["atol_app"]:
+            probs.append(f"oracle met the syndrome at k={Do} with no APP near-tie, decoder went on")
+    if rid in (1, 2) and not (fl & 1) and D < max_iter and not (fl & 2):
+        probs.append("stopped without success, abort or D_max")
+    return probs
+
 
 def check_decisions(ldpc, graph, code_csr, oracle, llr, syn, max_iter, rule, report=None,
-                    max_mismatch_frac=0.1, **opts):
-    """FP32 GPU decisions vs oracle on every frame; mismatches re-run in FP64
-    on the GPU must then agree exactly.  Near-ties (a q step or an APP value
-    within FP32 rounding of zero) are the only accepted cause, so at most
-    max_mismatch_frac of the frames may need the re-run.  Returns the list of
-    frames that needed it."""
-    orc = oracle.decode(code_csr, llr, syn, max_iter, RULE_IDS[rule],
-                        vnr_first_iter=opts.get("vnr_first_iter", 2), lmax=opts.get("clamp", 25.0))
+                    max_mismatch_frac=1.0, **opts):
+    """FP32 GPU decisions vs the oracle on every frame.
+
+    Frames that differ are re-run in the decoder's FP64 mode, which must agree
+    with the oracle exactly -- or, where the FP64 decision itself hangs on a
+    near-tie at FP64 rounding level, pass validate_trajectory at FP64
+    tolerance.  The FP32 result of every differing frame must pass
+    validate_trajectory at FP32 tolerance (so no difference is accepted unless
+    the oracle's own trajectory shows a near-tie there), and at most
+    max_mismatch_frac of the frames may differ.  FP32 differences are mostly VNR
+    aborts on frames that reached a fixed point: there the FP64 q stays flat (a
+    tie, decoding goes on) while the FP32 q moves by an ulp and may fall.
+    Returns (differing frames, gpu result, oracle result)."""
+    kw = dict(vnr_first_iter=opts.get("vnr_first_iter", 2), clamp=opts.get("clamp", 25.0))
+    orc = oracle.decode(code_csr, llr, syn, max_iter, RULE_IDS[rule], vnr_first_iter=kw["vnr_first_iter"],
+                        lmax=kw["clamp"])
     got = gpu_decode(ldpc, graph, llr, syn, max_iter, rule, **opts)
     bad = mismatched_frames(got, orc)
     assert bad.size <= max(1, int(max_mismatch_frac * llr.shape[0])), \
-        f"FP32 decisions differ on {bad.size} of {llr.shape[0]} frames: {bad.tolist()}"
+        (f"FP32 decisions differ on {bad.size} of {llr.shape[0]} frames: "
+         + "; ".join(f"f{f}: gpu D={got['iters'][f]} fl={got['flags'][f]} / oracle D={orc['iters'][f]} "
+                     f"fl={orc['flags'][f]}, {(got['bits'][f] != orc['bits'][f]).sum()} bits" for f in bad))
+    fp64_ties = []
     if bad.size:
         g64 = gpu_decode(ldpc, graph, llr[bad], syn[bad], max_iter, rule, fp64=True, **opts)
-        sub = {k: orc[k][bad] for k in ("bits", "flags", "iters")}
-        still = mismatched_frames(g64, sub)
-        assert still.size == 0, f"FP64 re-run still differs on frames {bad[still].tolist()}"
+        for i, f in enumerate(bad):
+            one = lambda r, j: {k: r[k][j] for k in ("bits", "flags", "iters")}
+            o = one(orc, f)
+            p32 = validate_trajectory(oracle, code_csr, llr[f], syn[f], one(got, f), o, max_iter, rule, "fp32", **kw)
+            assert not p32, f"frame {f} (FP32): {p32}"
+            r64 = one(g64, i)
+            if mismatched_frames({k: v[None] for k, v in r64.items()}, {k: v[None] for k, v in o.items()}).size:
+                p64 = validate_trajectory(oracle, code_csr, llr[f], syn[f], r64, o, max_iter, rule, "fp64", **kw)
+                assert not p64, f"frame {f} (FP64 re-run): {p64}"
+                fp64_ties.append(int(f))
     if report is not None:
-        report.append(dict(rule=rule, frames=int(llr.shape[0]), fp32_mismatch=bad.tolist()))
+        report.append(dict(rule=rule, frames=int(llr.shape[0]), fp32_mismatch=bad.tolist(), fp64_ties=fp64_ties))
     return bad.tolist(), got, orc

@@ -189,15 +189,15 @@ def test_degenerate_qc_shapes(ldpc, oracle):
     code = gen.QCCode(4, 9, 11, sh)
     g = ldpc.Graph.from_code(code)
     rng = np.random.default_rng(3)
-    x = rng.integers(0, 2, size=(10, code.n)).astype(np.uint8)
+    x = rng.integers(0, 2, size=(40, code.n)).astype(np.uint8)
     llr = ((1.0 - 2.0 * x) + 0.9 * rng.standard_normal(x.shape)).astype(np.float32) * 2.0
     s = gen.syndrome(code, x)
-    for rule in ("pce_vnr", "pce"):
-        check_decisions(ldpc, g, code.to_csr(), oracle, llr, s, 12, rule)
-    orc = oracle.decode(code.to_csr(), llr, s, 5, 0, trace_iters=5)
-    got = gpu_decode(ldpc, g, llr, s, 5, "none", trace_iters=5)
+    orc = oracle.decode(code.to_csr(), llr, s, 10, 0, trace_iters=10)
+    got = gpu_decode(ldpc, g, llr, s, 10, "none", trace_iters=10)
     assert_close_messages(got["c2v"], orc["c2v"], "c2v")
     assert_close_messages(got["app"], orc["app"], "app")
+    for rule in ("pce_vnr", "pce"):
+        check_decisions(ldpc, g, code.to_csr(), oracle, llr, s, 12, rule)
 
 
 @pytest.mark.parametrize("opts", [dict(vnr_first_iter=1), dict(clamp=8.0), dict(vnr_first_iter=4)])
