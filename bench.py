@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--compare-steps", type=int, default=2, help="timed steps of each fixed-iteration rule")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    ap.add_argument("--max-iter", type=int, default=None, help="override D_max (profiling runs)")
+    ap.add_argument("--lean", action="store_true",
+                    help="only the timed decodes: no fixed-iteration runs, no host-buffer runs, no CPU baseline")
     return ap.parse_args()
 
 
@@ -226,14 +229,16 @@ def run_ours(args):
     build.build()
     from paper_2507_03509_gb300 import ldpc
 
-    wl = gen.WORKLOADS[args.workload]
+    wl = dict(gen.WORKLOADS[args.workload])
+    if args.max_iter:
+        wl["max_iter"] = args.max_iter
     code = gen.workload_code(args.workload)
     F = args.frames or wl["frames"]
     frames = gen.workload_frames(args.workload, code, frames=F, first=rank * F)  # weak scaling by frames
 
     # CPU baseline first (rank 0, N = 1), before any GPU work in this process.
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.lean:
         cpu_pending = True
     else:
         cpu_pending = False
@@ -301,7 +306,7 @@ def run_ours(args):
 
     # fixed-iteration baselines on the same frames
     comp = {}
-    for rule in ("pce", "none"):
+    for rule in (() if args.lean else ("pce", "none")):
         r = timed(rule, args.compare_steps, 1)
         comp[rule] = dict(mbit_s=code.n * F * r["steps"] / (r["ms"] * 1e-3) / 1e6, d_mean=r["d_mean"],
                           fer=r["fer"], ms_per_step=r["ms"] / r["steps"],
@@ -320,8 +325,8 @@ def run_ours(args):
     h_bits = torch.empty((F, code.n), dtype=torch.uint8).pin_memory()
     h_flags = torch.empty(F, dtype=torch.uint8).pin_memory()
     h_iters = torch.empty(F, dtype=torch.int32).pin_memory()
-    e2e_steps = max(1, min(args.steps, 5))
-    for _ in range(1):
+    e2e_steps = 0 if args.lean else max(1, min(args.steps, 5))
+    for _ in range(1 if e2e_steps else 0):
         ldpc.decode_host(graph, h_llr.numpy(), h_syn.numpy(), wl["max_iter"], "pce_vnr",
                          out=(h_bits.numpy(), h_flags.numpy(), h_iters.numpy()), stream=stream.cuda_stream,
                          max_active_frames=args.slots, grid_ctas=args.grid)
@@ -332,7 +337,7 @@ def run_ours(args):
                          out=(h_bits.numpy(), h_flags.numpy(), h_iters.numpy()), stream=stream.cuda_stream,
                          max_active_frames=args.slots, grid_ctas=args.grid)
     e2e_s = time.perf_counter() - t0
-    e2e = {"value": code.n * F * e2e_steps / e2e_s / 1e6, "unit": UNIT,
+    e2e = None if not e2e_steps else {"value": code.n * F * e2e_steps / e2e_s / 1e6, "unit": UNIT,
            "h2d_bytes_per_step": int(frames.llr.nbytes + frames.syndrome.nbytes),
            "d2h_bytes_per_step": int(F * code.n + F + 4 * F)}
 
@@ -358,8 +363,9 @@ def run_ours(args):
         "d_mean": main["d_mean"], "fer": main["fer"], "success_frames": main["success"],
         "aborted_frames": main["aborted"], "edge_msgs_per_s": edge_msgs, "goodput_mbit_s": goodput,
         "fixed_iteration": comp,
-        "et_speedup": {"vs_pce": comp["pce"]["ms_per_step"] / (main["ms"] / args.steps),
-                       "vs_none": comp["none"]["ms_per_step"] / (main["ms"] / args.steps)},
+        "et_speedup": None if not comp else {
+            "vs_pce": comp["pce"]["ms_per_step"] / (main["ms"] / args.steps),
+            "vs_none": comp["none"]["ms_per_step"] / (main["ms"] / args.steps)},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src,
                      "traffic": (traffic_fi * per_launch_fi) if traffic_fi else None,

@@ -26,7 +26,7 @@ namespace ldpcgb {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kCPT = 4;                  // checks per thread in a check-node tile
+constexpr int kCPT = 2;                  // checks per thread in a check-node tile
 constexpr int kVPT = 4;                  // variables per thread in a variable-node tile
 constexpr int kCnTile = kThreads * kCPT;
 constexpr int kVnTile = kThreads * kVPT;
@@ -83,8 +83,8 @@ struct Params {
     int slots;
     T* c2v;                        // [slots][E]
     T* app;                        // [slots][n]
-    double* qpart;                 // [slots][vn_tiles]
-    double* q0part;                // [slots][vn_tiles]
+    double* qpart;                 // [slots][vn_tiles * kWarps] per-warp partial sums
+    double* q0part;                // [slots][vn_tiles * kWarps]
     double* qval;                  // [slots]
     double* q0val;                 // [slots]
     int* unsat;                    // [2][slots]
@@ -95,6 +95,7 @@ struct Params {
     T* trace_app;                  // [trace_iters][frames][n]
     double* trace_q;               // [trace_iters][frames]
     unsigned long long timeout_ns;
+    int vec4;                      // 16-byte variable-node path allowed (Z % 4 == 0, aligned llr)
 };
 
 // ---------------------------------------------------------------------------
@@ -264,26 +265,30 @@ __device__ __forceinline__ unsigned syndrome_bit(const unsigned* sb, int row) {
 // All loads of the tile's kCPT checks are issued before any arithmetic.
 // ---------------------------------------------------------------------------
 template <int D, typename T>
-__device__ __forceinline__ bool qc_cn_rows(const Params<T>& p, const QcDev& q, int s, int f, int k,
-                                           int mode, bool want_synd, int i, int t0, int b0) {
+__device__ __forceinline__ bool qc_cn_rows(const Params<T>& p, const QcDev& q, int s, int f, int mode,
+                                           bool want_synd, int i, int t0, int b0) {
     const int Z = q.Z;
-    int col[D], sh[D];
+    T* c2v = p.c2v + (size_t)s * (size_t)p.E;
+    const T* app = p.app + (size_t)s * (size_t)p.n;
+    const float* llr = p.llr + (size_t)f * (size_t)p.n;
+    const unsigned* sb = p.sbits + (size_t)f * (size_t)p.swords;
+    int sh[D];
+    const T* ap[D];
+    const float* lp[D];
+    T* cp[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        col[j] = __ldg(q.blk_col + b0 + j);
+        const int col = __ldg(q.blk_col + b0 + j);
         sh[j] = __ldg(q.blk_shift + b0 + j);
+        ap[j] = app + col * Z;
+        lp[j] = llr + col * Z;
+        cp[j] = c2v + (b0 + j) * Z;
     }
-    T* c2v = p.c2v + (long long)s * p.E;
-    const T* app = p.app + (long long)s * p.n;
-    const float* llr = p.llr + (long long)f * p.n;
-    const unsigned* sb = p.sbits + (long long)f * p.swords;
     int pos[kCPT][D];
     T a[kCPT][D], o[kCPT][D];
-    bool ok[kCPT];
 #pragma unroll
     for (int c = 0; c < kCPT; ++c) {
         const int t = t0 + c * kThreads + (int)threadIdx.x;
-        ok[c] = t < Z;
 #pragma unroll
         for (int j = 0; j < D; ++j) {
             int pp = t + sh[j];
@@ -291,12 +296,12 @@ __device__ __forceinline__ bool qc_cn_rows(const Params<T>& p, const QcDev& q, i
             pos[c][j] = pp;
             a[c][j] = T(0);
             o[c][j] = T(0);
-            if (ok[c]) {
+            if (t < Z) {
                 if (mode == kModeFirst) {
-                    a[c][j] = T(__ldg(llr + (long long)col[j] * Z + pp));
+                    a[c][j] = T(__ldg(lp[j] + pp));
                 } else {
-                    a[c][j] = app[(long long)col[j] * Z + pp];
-                    if (mode == kModeFull) o[c][j] = c2v[(long long)(b0 + j) * Z + pp];
+                    a[c][j] = ap[j][pp];
+                    if (mode == kModeFull) o[c][j] = cp[j][pp];
                 }
             }
         }
@@ -304,8 +309,8 @@ __device__ __forceinline__ bool qc_cn_rows(const Params<T>& p, const QcDev& q, i
     bool unsat = false;
 #pragma unroll
     for (int c = 0; c < kCPT; ++c) {
-        if (!ok[c]) continue;
         const int t = t0 + c * kThreads + (int)threadIdx.x;
+        if (t >= Z) continue;
         const unsigned sbit = syndrome_bit(sb, i * Z + t);
         if (want_synd) {
             unsigned pr = sbit;
@@ -319,13 +324,13 @@ __device__ __forceinline__ bool qc_cn_rows(const Params<T>& p, const QcDev& q, i
         for (int j = 0; j < D; ++j) v[j] = clampm(a[c][j] - o[c][j], p.lmax);
         cn_core<D>(v, sbit, p.lmax, out);
 #pragma unroll
-        for (int j = 0; j < D; ++j) c2v[(long long)(b0 + j) * Z + pos[c][j]] = out[j];
+        for (int j = 0; j < D; ++j) cp[j][pos[c][j]] = out[j];
     }
     return unsat;
 }
 
 template <typename T>
-__device__ bool qc_cn_rows_n(const Params<T>& p, const QcDev& q, int s, int f, int k, int mode,
+__device__ bool qc_cn_rows_n(const Params<T>& p, const QcDev& q, int s, int f, int mode,
                              bool want_synd, int i, int t0, int b0, int d) {
     const int Z = q.Z;
     T* c2v = p.c2v + (long long)s * p.E;
@@ -385,13 +390,13 @@ __device__ __forceinline__ bool cn_tile(const Params<T>& p, const QcDev& q, int 
             }
             return unsat;
         }
-        case 1: return qc_cn_rows<1, T>(p, q, s, f, k, mode, want_synd, i, t0, b0);
-        case 2: return qc_cn_rows<2, T>(p, q, s, f, k, mode, want_synd, i, t0, b0);
-        case 3: return qc_cn_rows<3, T>(p, q, s, f, k, mode, want_synd, i, t0, b0);
-        case 4: return qc_cn_rows<4, T>(p, q, s, f, k, mode, want_synd, i, t0, b0);
-        case 5: return qc_cn_rows<5, T>(p, q, s, f, k, mode, want_synd, i, t0, b0);
-        case 6: return qc_cn_rows<6, T>(p, q, s, f, k, mode, want_synd, i, t0, b0);
-        default: return qc_cn_rows_n<T>(p, q, s, f, k, mode, want_synd, i, t0, b0, d);
+        case 1: return qc_cn_rows<1, T>(p, q, s, f, mode, want_synd, i, t0, b0);
+        case 2: return qc_cn_rows<2, T>(p, q, s, f, mode, want_synd, i, t0, b0);
+        case 3: return qc_cn_rows<3, T>(p, q, s, f, mode, want_synd, i, t0, b0);
+        case 4: return qc_cn_rows<4, T>(p, q, s, f, mode, want_synd, i, t0, b0);
+        case 5: return qc_cn_rows<5, T>(p, q, s, f, mode, want_synd, i, t0, b0);
+        case 6: return qc_cn_rows<6, T>(p, q, s, f, mode, want_synd, i, t0, b0);
+        default: return qc_cn_rows_n<T>(p, q, s, f, mode, want_synd, i, t0, b0, d);
     }
 }
 
@@ -487,23 +492,15 @@ __device__ __forceinline__ bool cn_tile(const Params<T>& p, const CsrDev& g, int
 
 // ---------------------------------------------------------------------------
 // Variable-node tiles: APP^(k+1) = Lch + sum of c2v^(k+1) over the variable's
-// checks in ascending check order; per-tile sum of |APP| over V (degree > 1)
-// and, for the first iteration, of |Lch| over V.
+// checks in ascending check order; per-warp sums of |APP| over V (degree > 1)
+// and, for the first iteration, of |Lch| over V.  The per-warp partials go to
+// fixed positions (tile * kWarps + warp), so q is a fixed-order sum.
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ __forceinline__ void tile_sum_store(T acc, double* dst, double* s_red) {
+__device__ __forceinline__ void warp_sum_store(T acc, double* dst) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    __syncthreads();
-    if (lane == 0) s_red[warp] = double(acc);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) t += s_red[w];
-        *dst = t;
-    }
+    if ((threadIdx.x & 31) == 0) dst[threadIdx.x >> 5] = double(acc);
 }
 
 // Trace of c2v^(k+1) for variable j*Z + u, written from the variable side so
@@ -513,7 +510,7 @@ template <typename T>
 __device__ void trace_c2v_qc(const Params<T>& p, const QcDev& q, const T* c2v, int f, int k, int u, int cb0,
                              int dv) {
     const int Z = q.Z;
-    T* tr = p.trace_c2v + ((long long)k * p.frames + f) * p.E;
+    T* tr = p.trace_c2v + ((size_t)k * p.frames + f) * (size_t)p.E;
     for (int b = 0; b < dv; ++b) {
         const int blk = __ldg(q.col_blk + cb0 + b);
         const int i = __ldg(q.blk_row + blk);
@@ -521,54 +518,122 @@ __device__ void trace_c2v_qc(const Params<T>& p, const QcDev& q, const T* c2v, i
         const int d = __ldg(q.row_ptr + i + 1) - r0;
         int t = u - __ldg(q.blk_shift + blk);
         t = t < 0 ? t + Z : t;
-        tr[(long long)r0 * Z + (long long)t * d + (blk - r0)] = c2v[(long long)blk * Z + u];
+        tr[(size_t)r0 * Z + (size_t)t * d + (blk - r0)] = c2v[(size_t)blk * Z + u];
     }
 }
 
-template <typename T>
-__device__ __forceinline__ void vn_tile(const Params<T>& p, const QcDev& q, int s, int f, int k, int tile,
-                                        double* s_red) {
+// DV > 0: compile-time column degree; DV == 0: runtime degree dv.
+template <int DV, typename T>
+__device__ __forceinline__ void qc_vn_cols(const Params<T>& p, const QcDev& q, int s, int f, int k, int tile,
+                                           int j, int u0, int cb0, int dv) {
+    constexpr bool kFixed = DV > 0;
     const int Z = q.Z;
-    const int per_col = (Z + kVnTile - 1) / kVnTile;
+    const int nd = kFixed ? DV : dv;
+    const bool inV = nd > 1;
+    const bool want_q0 = (k == 0) && p.vnr_first_iter <= 1;
+    const T* c2v = p.c2v + (size_t)s * (size_t)p.E;
+    T* app = p.app + (size_t)s * (size_t)p.n + j * Z;
+    const float* llr = p.llr + (size_t)f * (size_t)p.n + j * Z;
+    const T* cb[kFixed ? DV : 1];
+    if constexpr (kFixed) {
+#pragma unroll
+        for (int b = 0; b < DV; ++b) cb[b] = c2v + __ldg(q.col_blk + cb0 + b) * Z;
+    }
+    T acc = T(0), acc0 = T(0);
+    bool vec = false;
+    if constexpr (sizeof(T) == 4) vec = p.vec4 != 0;
+    if (vec) {
+        // four consecutive variables per thread, 16-byte loads and stores
+        const int u = u0 + 4 * (int)threadIdx.x;
+        if (u < Z) {
+            const float4 L = __ldg(reinterpret_cast<const float4*>(llr + u));
+            float4 sum = L;
+            if constexpr (kFixed) {
+                float4 m[DV];
+#pragma unroll
+                for (int b = 0; b < DV; ++b) m[b] = *reinterpret_cast<const float4*>(cb[b] + u);
+#pragma unroll
+                for (int b = 0; b < DV; ++b) {
+                    sum.x += m[b].x;
+                    sum.y += m[b].y;
+                    sum.z += m[b].z;
+                    sum.w += m[b].w;
+                }
+            } else {
+                for (int b = 0; b < nd; ++b) {
+                    const float4 m = *reinterpret_cast<const float4*>(c2v + __ldg(q.col_blk + cb0 + b) * Z + u);
+                    sum.x += m.x;
+                    sum.y += m.y;
+                    sum.z += m.z;
+                    sum.w += m.w;
+                }
+            }
+            *reinterpret_cast<float4*>(reinterpret_cast<float*>(app) + u) = sum;
+            if (inV) {
+                acc = T((fabsf(sum.x) + fabsf(sum.y)) + (fabsf(sum.z) + fabsf(sum.w)));
+                if (want_q0) acc0 = T((fabsf(L.x) + fabsf(L.y)) + (fabsf(L.z) + fabsf(L.w)));
+            }
+            if (k < p.trace_iters) {
+                const float sv[4] = {sum.x, sum.y, sum.z, sum.w};
+                for (int e = 0; e < 4; ++e) {
+                    if (p.trace_app)
+                        p.trace_app[((size_t)k * p.frames + f) * (size_t)p.n + j * Z + u + e] = T(sv[e]);
+                    if (p.trace_c2v) trace_c2v_qc(p, q, c2v, f, k, u + e, cb0, nd);
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < kVPT; ++c) {
+            const int u = u0 + c * kThreads + (int)threadIdx.x;
+            if (u < Z) {
+                const T L = T(__ldg(llr + u));
+                T sum = L;
+                if constexpr (kFixed) {
+#pragma unroll
+                    for (int b = 0; b < DV; ++b) sum += cb[b][u];
+                } else {
+                    for (int b = 0; b < nd; ++b) sum += c2v[__ldg(q.col_blk + cb0 + b) * Z + u];
+                }
+                app[u] = sum;
+                if (inV) {
+                    acc += absm(sum);
+                    acc0 += absm(L);
+                }
+                if (k < p.trace_iters) {
+                    if (p.trace_app) p.trace_app[((size_t)k * p.frames + f) * (size_t)p.n + j * Z + u] = sum;
+                    if (p.trace_c2v) trace_c2v_qc(p, q, c2v, f, k, u, cb0, nd);
+                }
+            }
+        }
+    }
+    const size_t part = ((size_t)s * p.vn_tiles + tile) * kWarps;
+    warp_sum_store(acc, p.qpart + part);
+    if (want_q0) warp_sum_store(acc0, p.q0part + part);
+}
+
+template <typename T>
+__device__ __forceinline__ void vn_tile(const Params<T>& p, const QcDev& q, int s, int f, int k, int tile) {
+    const int per_col = (q.Z + kVnTile - 1) / kVnTile;
     const int j = tile / per_col;
     const int u0 = (tile - j * per_col) * kVnTile;
     const int cb0 = __ldg(q.col_ptr + j);
     const int dv = __ldg(q.col_ptr + j + 1) - cb0;
-    const bool inV = dv > 1;
-    const bool want_q0 = (k == 0) && p.vnr_first_iter <= 1;
-    const T* c2v = p.c2v + (long long)s * p.E;
-    T* app = p.app + (long long)s * p.n;
-    const float* llr = p.llr + (long long)f * p.n;
-    T acc = T(0), acc0 = T(0);
-#pragma unroll
-    for (int c = 0; c < kVPT; ++c) {
-        const int u = u0 + c * kThreads + (int)threadIdx.x;
-        if (u < Z) {
-            const long long vi = (long long)j * Z + u;
-            const T L = T(__ldg(llr + vi));
-            T sum = L;
-            for (int b = 0; b < dv; ++b) sum += c2v[(long long)__ldg(q.col_blk + cb0 + b) * Z + u];
-            app[vi] = sum;
-            if (k < p.trace_iters && p.trace_c2v) trace_c2v_qc(p, q, c2v, f, k, u, cb0, dv);
-            if (inV) {
-                acc += absm(sum);
-                acc0 += absm(L);
-            }
-            if (k < p.trace_iters && p.trace_app)
-                p.trace_app[((long long)k * p.frames + f) * p.n + vi] = sum;
-        }
+    switch (dv) {
+        case 1: qc_vn_cols<1, T>(p, q, s, f, k, tile, j, u0, cb0, dv); break;
+        case 2: qc_vn_cols<2, T>(p, q, s, f, k, tile, j, u0, cb0, dv); break;
+        case 3: qc_vn_cols<3, T>(p, q, s, f, k, tile, j, u0, cb0, dv); break;
+        case 4: qc_vn_cols<4, T>(p, q, s, f, k, tile, j, u0, cb0, dv); break;
+        default: qc_vn_cols<0, T>(p, q, s, f, k, tile, j, u0, cb0, dv); break;
     }
-    tile_sum_store(acc, p.qpart + (long long)s * p.vn_tiles + tile, s_red);
-    if (want_q0) tile_sum_store(acc0, p.q0part + (long long)s * p.vn_tiles + tile, s_red);
 }
 
 template <typename T>
-__device__ __forceinline__ void vn_tile(const Params<T>& p, const CsrDev& g, int s, int f, int k, int tile,
-                                        double* s_red) {
+__device__ __forceinline__ void vn_tile(const Params<T>& p, const CsrDev& g, int s, int f, int k, int tile) {
     const bool want_q0 = (k == 0) && p.vnr_first_iter <= 1;
-    const T* c2v = p.c2v + (long long)s * p.E;
-    T* app = p.app + (long long)s * p.n;
-    const float* llr = p.llr + (long long)f * p.n;
+    const T* c2v = p.c2v + (size_t)s * (size_t)p.E;
+    T* app = p.app + (size_t)s * (size_t)p.n;
+    const float* llr = p.llr + (size_t)f * (size_t)p.n;
     T acc = T(0), acc0 = T(0);
 #pragma unroll
     for (int c = 0; c < kVPT; ++c) {
@@ -579,19 +644,22 @@ __device__ __forceinline__ void vn_tile(const Params<T>& p, const CsrDev& g, int
             T sum = L;
             for (int a = a0; a < a1; ++a) sum += c2v[__ldg(g.var_edge + a)];
             app[v] = sum;
-            if (k < p.trace_iters && p.trace_c2v) {
-                T* tr = p.trace_c2v + ((long long)k * p.frames + f) * p.E;
-                for (int a = a0; a < a1; ++a) tr[__ldg(g.var_edge + a)] = c2v[__ldg(g.var_edge + a)];
-            }
             if (a1 - a0 > 1) {
                 acc += absm(sum);
                 acc0 += absm(L);
             }
-            if (k < p.trace_iters && p.trace_app) p.trace_app[((long long)k * p.frames + f) * p.n + v] = sum;
+            if (k < p.trace_iters) {
+                if (p.trace_app) p.trace_app[((size_t)k * p.frames + f) * (size_t)p.n + v] = sum;
+                if (p.trace_c2v) {
+                    T* tr = p.trace_c2v + ((size_t)k * p.frames + f) * (size_t)p.E;
+                    for (int a = a0; a < a1; ++a) tr[__ldg(g.var_edge + a)] = c2v[__ldg(g.var_edge + a)];
+                }
+            }
         }
     }
-    tile_sum_store(acc, p.qpart + (long long)s * p.vn_tiles + tile, s_red);
-    if (want_q0) tile_sum_store(acc0, p.q0part + (long long)s * p.vn_tiles + tile, s_red);
+    const size_t part = ((size_t)s * p.vn_tiles + tile) * kWarps;
+    warp_sum_store(acc, p.qpart + part);
+    if (want_q0) warp_sum_store(acc0, p.q0part + part);
 }
 
 // Hard decision of a stopped frame: bits = [APP < 0] over the tile's variables.
@@ -646,7 +714,7 @@ __device__ __forceinline__ double block_sum_fixed(const double* part, int count,
 // The persistent decoder.
 // ---------------------------------------------------------------------------
 template <typename T, class Code>
-__global__ void __launch_bounds__(kThreads) bp_decode_kernel(Params<T> p, Code code) {
+__global__ void __launch_bounds__(kThreads, 4) bp_decode_kernel(Params<T> p, Code code) {
     extern __shared__ double smem_dyn[];
     double* st_qprev = smem_dyn;                       // [slots]
     int* st_frame = (int*)(st_qprev + p.slots);         // [slots]
@@ -688,10 +756,11 @@ __global__ void __launch_bounds__(kThreads) bp_decode_kernel(Params<T> p, Code c
         if (nA == 0) break;
 
         // ---- phase A: check nodes + syndrome of the current decision -----
-        const long long totalA = (long long)nA * p.cn_tiles;
-        for (long long it = blockIdx.x; it < totalA; it += gridDim.x) {
-            const int s = listA[it / p.cn_tiles];
-            const int tile = (int)(it % p.cn_tiles);
+        const unsigned totalA = (unsigned)nA * (unsigned)p.cn_tiles;
+        for (unsigned it = blockIdx.x; it < totalA; it += gridDim.x) {
+            const unsigned si = it / (unsigned)p.cn_tiles;
+            const int s = listA[si];
+            const int tile = (int)(it - si * (unsigned)p.cn_tiles);
             const int k = st_k[s];
             const int mode = k == 0 ? kModeFirst : (k >= p.max_iter ? kModeSynd : kModeFull);
             const bool want_synd = k >= 1 && (p.rule != kRuleNone || k >= p.max_iter);
@@ -704,10 +773,11 @@ __global__ void __launch_bounds__(kThreads) bp_decode_kernel(Params<T> p, Code c
             const int s = listA[i];
             const int k = st_k[s];
             if (k < 1) continue;
-            const double qv = block_sum_fixed(p.qpart + (long long)s * p.vn_tiles, p.vn_tiles, s_red);
+            const int np = p.vn_tiles * kWarps;
+            const double qv = block_sum_fixed(p.qpart + (size_t)s * np, np, s_red);
             const bool with_q0 = k == 1 && p.vnr_first_iter <= 1;
             double q0 = 0.0;
-            if (with_q0) q0 = block_sum_fixed(p.q0part + (long long)s * p.vn_tiles, p.vn_tiles, s_red);
+            if (with_q0) q0 = block_sum_fixed(p.q0part + (size_t)s * np, np, s_red);
             if (threadIdx.x == 0) {
                 p.qval[s] = qv;
                 if (with_q0) p.q0val[s] = q0;
@@ -767,13 +837,14 @@ __global__ void __launch_bounds__(kThreads) bp_decode_kernel(Params<T> p, Code c
         const int nB = s_nB;
 
         // ---- phase B: variable nodes / write-out of stopped frames -------
-        const long long totalB = (long long)nB * p.vn_tiles;
-        for (long long it = blockIdx.x; it < totalB; it += gridDim.x) {
-            const int e = listB[it / p.vn_tiles];
+        const unsigned totalB = (unsigned)nB * (unsigned)p.vn_tiles;
+        for (unsigned it = blockIdx.x; it < totalB; it += gridDim.x) {
+            const unsigned si = it / (unsigned)p.vn_tiles;
+            const int e = listB[si];
             const int s = e & 0xffff;
-            const int tile = (int)(it % p.vn_tiles);
+            const int tile = (int)(it - si * (unsigned)p.vn_tiles);
             if ((e >> 16) == 0)
-                vn_tile<T>(p, code, s, st_frame[s], st_k[s], tile, s_red);
+                vn_tile<T>(p, code, s, st_frame[s], st_k[s], tile);
             else
                 final_tile<T>(p, code, s, st_frame[s], tile);
         }

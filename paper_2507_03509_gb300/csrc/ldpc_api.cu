@@ -115,8 +115,8 @@ Layout make_layout(const ldpc_graph* g, int slots, size_t elem, int frames, int 
     size_t o = 0;
     L.c2v = o;    o = align_up(o + (size_t)slots * (size_t)g->E * elem, 256);
     L.app = o;    o = align_up(o + (size_t)slots * (size_t)g->n * elem, 256);
-    L.qpart = o;  o = align_up(o + (size_t)slots * g->vn_tiles * sizeof(double), 256);
-    L.q0part = o; o = align_up(o + (size_t)slots * g->vn_tiles * sizeof(double), 256);
+    L.qpart = o;  o = align_up(o + (size_t)slots * g->vn_tiles * kWarps * sizeof(double), 256);
+    L.q0part = o; o = align_up(o + (size_t)slots * g->vn_tiles * kWarps * sizeof(double), 256);
     L.qval = o;   o = align_up(o + (size_t)slots * sizeof(double), 256);
     L.q0val = o;  o = align_up(o + (size_t)slots * sizeof(double), 256);
     L.unsat = o;  o = align_up(o + 2 * (size_t)slots * sizeof(int), 256);
@@ -222,6 +222,7 @@ ldpc_status launch_decode(ldpc_graph* g, const Code& code, int frames, const flo
     p.trace_app = (T*)o.trace_app;
     p.trace_q = o.trace_q;
     p.timeout_ns = kBarrierTimeoutNs;
+    p.vec4 = (g->kind == 1 && (g->Z % 4) == 0 && ((uintptr_t)llr % 16) == 0) ? 1 : 0;
 
     const bool timing = o.stats != nullptr;
     if (timing) LDPC_TRY(cudaEventRecord(ws.ev[0], stream));
