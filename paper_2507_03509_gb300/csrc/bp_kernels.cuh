@@ -261,143 +261,161 @@ __device__ __forceinline__ unsigned syndrome_bit(const unsigned* sb, int row) {
 }
 
 // ---------------------------------------------------------------------------
-// Quasi-cyclic check-node tile: checks t0 .. t0+kCnTile-1 of base row i.
-// All loads of the tile's kCPT checks are issued before any arithmetic.
+// Quasi-cyclic check-node item: checks t in [t0, t0 + kQcCnChunk) of base row
+// i.  The row's block pointers are set up once; each thread then walks the
+// chunk two checks at a time (both checks' loads issued before any
+// arithmetic).  MODE and SYND are compile-time so the hot loop carries no
+// mode tests: kModeFirst reads Lch with c2v = 0, kModeFull reads APP and the
+// old c2v, kModeSynd only tests the syndrome of the current decision.
 // ---------------------------------------------------------------------------
-template <int D, typename T>
-__device__ __forceinline__ bool qc_cn_rows(const Params<T>& p, const QcDev& q, int s, int f, int mode,
-                                           bool want_synd, int i, int t0, int b0) {
+constexpr int kQcCnChunk = 2048;         // checks of one base row per item
+constexpr int kQcVnChunk = 4096;         // variables of one base column per item
+
+template <int D, int MODE, bool SYND, typename T>
+__device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, int s, int f, int i, int t0,
+                                           int b0) {
     const int Z = q.Z;
+    const int t_end = min(t0 + kQcCnChunk, Z);
     T* c2v = p.c2v + (size_t)s * (size_t)p.E;
     const T* app = p.app + (size_t)s * (size_t)p.n;
     const float* llr = p.llr + (size_t)f * (size_t)p.n;
-    const unsigned* sb = p.sbits + (size_t)f * (size_t)p.swords;
-    int sh[D];
-    const T* ap[D];
-    const float* lp[D];
-    T* cp[D];
+    const unsigned* sb = p.sbits + (size_t)f * (size_t)p.swords + (size_t)i * Z / 32;
+    const int sbit0 = (i * Z) & 31;  // bit offset of check (i, 0) in its word
+    // per-block offsets: variable column (col*Z) and message block ((b0+j)*Z)
+    int sh[D], vo[D], mo[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        const int col = __ldg(q.blk_col + b0 + j);
         sh[j] = __ldg(q.blk_shift + b0 + j);
-        ap[j] = app + col * Z;
-        lp[j] = llr + col * Z;
-        cp[j] = c2v + (b0 + j) * Z;
+        vo[j] = __ldg(q.blk_col + b0 + j) * Z;
+        mo[j] = (b0 + j) * Z;
     }
-    int pos[kCPT][D];
-    T a[kCPT][D], o[kCPT][D];
+    bool unsat = false;
+    for (int tb = t0 + (int)threadIdx.x; tb < t_end; tb += 2 * kThreads) {
+        int pos[2][D];
+        T a[2][D], o[2][D];
+        bool ok[2];
 #pragma unroll
-    for (int c = 0; c < kCPT; ++c) {
-        const int t = t0 + c * kThreads + (int)threadIdx.x;
+        for (int c = 0; c < 2; ++c) {
+            const int t = tb + c * kThreads;
+            ok[c] = t < t_end;
 #pragma unroll
-        for (int j = 0; j < D; ++j) {
-            int pp = t + sh[j];
-            pp = pp >= Z ? pp - Z : pp;
-            pos[c][j] = pp;
-            a[c][j] = T(0);
-            o[c][j] = T(0);
-            if (t < Z) {
-                if (mode == kModeFirst) {
-                    a[c][j] = T(__ldg(lp[j] + pp));
+            for (int j = 0; j < D; ++j) {
+                int pp = t + sh[j];
+                pp = pp >= Z ? pp - Z : pp;
+                pp = ok[c] ? pp : 0;  // in-bounds dummy position for the guarded tail
+                pos[c][j] = pp;
+                if constexpr (MODE == kModeFirst) {
+                    a[c][j] = T(__ldg(llr + vo[j] + pp));
+                    o[c][j] = T(0);
                 } else {
-                    a[c][j] = ap[j][pp];
-                    if (mode == kModeFull) o[c][j] = cp[j][pp];
+                    a[c][j] = app[vo[j] + pp];
+                    o[c][j] = MODE == kModeFull ? c2v[mo[j] + pp] : T(0);
                 }
             }
         }
-    }
-    bool unsat = false;
 #pragma unroll
-    for (int c = 0; c < kCPT; ++c) {
-        const int t = t0 + c * kThreads + (int)threadIdx.x;
-        if (t >= Z) continue;
-        const unsigned sbit = syndrome_bit(sb, i * Z + t);
-        if (want_synd) {
-            unsigned pr = sbit;
+        for (int c = 0; c < 2; ++c) {
+            if (!ok[c]) continue;
+            const int t = tb + c * kThreads;
+            const int bit = sbit0 + t;
+            const unsigned sbit = (__ldg(sb + (bit >> 5)) >> (bit & 31)) & 1u;
+            if constexpr (SYND) {
+                unsigned pr = sbit;
 #pragma unroll
-            for (int j = 0; j < D; ++j) pr ^= (unsigned)(a[c][j] < T(0));
-            unsat |= pr != 0u;
+                for (int j = 0; j < D; ++j) pr ^= (unsigned)(a[c][j] < T(0));
+                unsat |= pr != 0u;
+            }
+            if constexpr (MODE != kModeSynd) {
+                T v[D], out[D];
+#pragma unroll
+                for (int j = 0; j < D; ++j) v[j] = clampm(a[c][j] - o[c][j], p.lmax);
+                cn_core<D>(v, sbit, p.lmax, out);
+#pragma unroll
+                for (int j = 0; j < D; ++j) c2v[mo[j] + pos[c][j]] = out[j];
+            }
         }
-        if (mode == kModeSynd) continue;
-        T v[D], out[D];
-#pragma unroll
-        for (int j = 0; j < D; ++j) v[j] = clampm(a[c][j] - o[c][j], p.lmax);
-        cn_core<D>(v, sbit, p.lmax, out);
-#pragma unroll
-        for (int j = 0; j < D; ++j) cp[j][pos[c][j]] = out[j];
     }
     return unsat;
 }
 
-template <typename T>
-__device__ bool qc_cn_rows_n(const Params<T>& p, const QcDev& q, int s, int f, int mode,
-                             bool want_synd, int i, int t0, int b0, int d) {
+// Rows of weight > 6: runtime degree, local arrays.
+template <int MODE, bool SYND, typename T>
+__device__ bool qc_cn_item_n(const Params<T>& p, const QcDev& q, int s, int f, int i, int t0, int b0, int d) {
     const int Z = q.Z;
-    T* c2v = p.c2v + (long long)s * p.E;
-    const T* app = p.app + (long long)s * p.n;
-    const float* llr = p.llr + (long long)f * p.n;
-    const unsigned* sb = p.sbits + (long long)f * p.swords;
+    const int t_end = min(t0 + kQcCnChunk, Z);
+    T* c2v = p.c2v + (size_t)s * (size_t)p.E;
+    const T* app = p.app + (size_t)s * (size_t)p.n;
+    const float* llr = p.llr + (size_t)f * (size_t)p.n;
+    const unsigned* sb = p.sbits + (size_t)f * (size_t)p.swords;
     bool unsat = false;
-    for (int c = 0; c < kCPT; ++c) {
-        const int t = t0 + c * kThreads + (int)threadIdx.x;
-        if (t >= Z) break;
+    for (int t = t0 + (int)threadIdx.x; t < t_end; t += kThreads) {
         const unsigned sbit = syndrome_bit(sb, i * Z + t);
         T v[kMaxDeg], out[kMaxDeg];
         unsigned pr = sbit;
         for (int j = 0; j < d; ++j) {
             int pp = t + __ldg(q.blk_shift + b0 + j);
             pp = pp >= Z ? pp - Z : pp;
-            const long long vi = (long long)__ldg(q.blk_col + b0 + j) * Z + pp;
+            const int vi = __ldg(q.blk_col + b0 + j) * Z + pp;
             T a, o = T(0);
-            if (mode == kModeFirst) {
+            if (MODE == kModeFirst) {
                 a = T(__ldg(llr + vi));
             } else {
                 a = app[vi];
-                if (mode == kModeFull) o = c2v[(long long)(b0 + j) * Z + pp];
+                if (MODE == kModeFull) o = c2v[(b0 + j) * Z + pp];
             }
             pr ^= (unsigned)(a < T(0));
             v[j] = clampm(a - o, p.lmax);
         }
-        if (want_synd) unsat |= pr != 0u;
-        if (mode == kModeSynd) continue;
-        cn_core_n(v, d, sbit, p.lmax, out);
-        for (int j = 0; j < d; ++j) {
-            int pp = t + __ldg(q.blk_shift + b0 + j);
-            pp = pp >= Z ? pp - Z : pp;
-            c2v[(long long)(b0 + j) * Z + pp] = out[j];
+        if (SYND) unsat |= pr != 0u;
+        if constexpr (MODE != kModeSynd) {
+            cn_core_n(v, d, sbit, p.lmax, out);
+            for (int j = 0; j < d; ++j) {
+                int pp = t + __ldg(q.blk_shift + b0 + j);
+                pp = pp >= Z ? pp - Z : pp;
+                c2v[(b0 + j) * Z + pp] = out[j];
+            }
         }
     }
     return unsat;
 }
 
-template <typename T>
-__device__ __forceinline__ bool cn_tile(const Params<T>& p, const QcDev& q, int s, int f, int k,
-                                        int mode, bool want_synd, int tile) {
-    const int per_row = (q.Z + kCnTile - 1) / kCnTile;
-    const int i = tile / per_row;
-    const int t0 = (tile - i * per_row) * kCnTile;
-    const int b0 = __ldg(q.row_ptr + i);
-    const int d = __ldg(q.row_ptr + i + 1) - b0;
+template <int MODE, bool SYND, typename T>
+__device__ __forceinline__ bool qc_cn_dispatch(const Params<T>& p, const QcDev& q, int s, int f, int i, int t0,
+                                               int b0, int d) {
     switch (d) {
         case 0: {
             bool unsat = false;
-            if (want_synd) {
-                const unsigned* sb = p.sbits + (long long)f * p.swords;
-                for (int c = 0; c < kCPT; ++c) {
-                    const int t = t0 + c * kThreads + (int)threadIdx.x;
-                    if (t < q.Z) unsat |= syndrome_bit(sb, i * q.Z + t) != 0u;
-                }
+            if (SYND) {
+                const unsigned* sb = p.sbits + (size_t)f * (size_t)p.swords;
+                const int t_end = min(t0 + kQcCnChunk, q.Z);
+                for (int t = t0 + (int)threadIdx.x; t < t_end; t += kThreads)
+                    unsat |= syndrome_bit(sb, i * q.Z + t) != 0u;
             }
             return unsat;
         }
-        case 1: return qc_cn_rows<1, T>(p, q, s, f, mode, want_synd, i, t0, b0);
-        case 2: return qc_cn_rows<2, T>(p, q, s, f, mode, want_synd, i, t0, b0);
-        case 3: return qc_cn_rows<3, T>(p, q, s, f, mode, want_synd, i, t0, b0);
-        case 4: return qc_cn_rows<4, T>(p, q, s, f, mode, want_synd, i, t0, b0);
-        case 5: return qc_cn_rows<5, T>(p, q, s, f, mode, want_synd, i, t0, b0);
-        case 6: return qc_cn_rows<6, T>(p, q, s, f, mode, want_synd, i, t0, b0);
-        default: return qc_cn_rows_n<T>(p, q, s, f, mode, want_synd, i, t0, b0, d);
+        case 1: return qc_cn_item<1, MODE, SYND, T>(p, q, s, f, i, t0, b0);
+        case 2: return qc_cn_item<2, MODE, SYND, T>(p, q, s, f, i, t0, b0);
+        case 3: return qc_cn_item<3, MODE, SYND, T>(p, q, s, f, i, t0, b0);
+        case 4: return qc_cn_item<4, MODE, SYND, T>(p, q, s, f, i, t0, b0);
+        case 5: return qc_cn_item<5, MODE, SYND, T>(p, q, s, f, i, t0, b0);
+        case 6: return qc_cn_item<6, MODE, SYND, T>(p, q, s, f, i, t0, b0);
+        default: return qc_cn_item_n<MODE, SYND, T>(p, q, s, f, i, t0, b0, d);
     }
+}
+
+template <typename T>
+__device__ __forceinline__ bool cn_tile(const Params<T>& p, const QcDev& q, int s, int f, int k,
+                                        int mode, bool want_synd, int tile) {
+    const int per_row = (q.Z + kQcCnChunk - 1) / kQcCnChunk;
+    const int i = tile / per_row;
+    const int t0 = (tile - i * per_row) * kQcCnChunk;
+    const int b0 = __ldg(q.row_ptr + i);
+    const int d = __ldg(q.row_ptr + i + 1) - b0;
+    (void)k;
+    if (mode == kModeFirst) return qc_cn_dispatch<kModeFirst, false, T>(p, q, s, f, i, t0, b0, d);
+    if (mode == kModeSynd) return qc_cn_dispatch<kModeSynd, true, T>(p, q, s, f, i, t0, b0, d);
+    if (want_synd) return qc_cn_dispatch<kModeFull, true, T>(p, q, s, f, i, t0, b0, d);
+    return qc_cn_dispatch<kModeFull, false, T>(p, q, s, f, i, t0, b0, d);
 }
 
 // ---------------------------------------------------------------------------
@@ -522,15 +540,20 @@ __device__ void trace_c2v_qc(const Params<T>& p, const QcDev& q, const T* c2v, i
     }
 }
 
-// DV > 0: compile-time column degree; DV == 0: runtime degree dv.
+// Quasi-cyclic variable-node item: variables u in [u0, u0 + kQcVnChunk) of
+// base column j.  DV > 0: compile-time column degree; DV == 0: runtime dv.
+// With vec (Z % 4 == 0, aligned Lch) each thread handles groups of four
+// consecutive variables with 16-byte loads and stores.
 template <int DV, typename T>
 __device__ __forceinline__ void qc_vn_cols(const Params<T>& p, const QcDev& q, int s, int f, int k, int tile,
                                            int j, int u0, int cb0, int dv) {
     constexpr bool kFixed = DV > 0;
     const int Z = q.Z;
+    const int u_end = min(u0 + kQcVnChunk, Z);
     const int nd = kFixed ? DV : dv;
     const bool inV = nd > 1;
     const bool want_q0 = (k == 0) && p.vnr_first_iter <= 1;
+    const bool tracing = k < p.trace_iters;
     const T* c2v = p.c2v + (size_t)s * (size_t)p.E;
     T* app = p.app + (size_t)s * (size_t)p.n + j * Z;
     const float* llr = p.llr + (size_t)f * (size_t)p.n + j * Z;
@@ -543,9 +566,7 @@ __device__ __forceinline__ void qc_vn_cols(const Params<T>& p, const QcDev& q, i
     bool vec = false;
     if constexpr (sizeof(T) == 4) vec = p.vec4 != 0;
     if (vec) {
-        // four consecutive variables per thread, 16-byte loads and stores
-        const int u = u0 + 4 * (int)threadIdx.x;
-        if (u < Z) {
+        for (int u = u0 + 4 * (int)threadIdx.x; u < u_end; u += 4 * kThreads) {
             const float4 L = __ldg(reinterpret_cast<const float4*>(llr + u));
             float4 sum = L;
             if constexpr (kFixed) {
@@ -570,10 +591,10 @@ __device__ __forceinline__ void qc_vn_cols(const Params<T>& p, const QcDev& q, i
             }
             *reinterpret_cast<float4*>(reinterpret_cast<float*>(app) + u) = sum;
             if (inV) {
-                acc = T((fabsf(sum.x) + fabsf(sum.y)) + (fabsf(sum.z) + fabsf(sum.w)));
-                if (want_q0) acc0 = T((fabsf(L.x) + fabsf(L.y)) + (fabsf(L.z) + fabsf(L.w)));
+                acc += T((fabsf(sum.x) + fabsf(sum.y)) + (fabsf(sum.z) + fabsf(sum.w)));
+                if (want_q0) acc0 += T((fabsf(L.x) + fabsf(L.y)) + (fabsf(L.z) + fabsf(L.w)));
             }
-            if (k < p.trace_iters) {
+            if (tracing) {
                 const float sv[4] = {sum.x, sum.y, sum.z, sum.w};
                 for (int e = 0; e < 4; ++e) {
                     if (p.trace_app)
@@ -583,27 +604,23 @@ __device__ __forceinline__ void qc_vn_cols(const Params<T>& p, const QcDev& q, i
             }
         }
     } else {
+        for (int u = u0 + (int)threadIdx.x; u < u_end; u += kThreads) {
+            const T L = T(__ldg(llr + u));
+            T sum = L;
+            if constexpr (kFixed) {
 #pragma unroll
-        for (int c = 0; c < kVPT; ++c) {
-            const int u = u0 + c * kThreads + (int)threadIdx.x;
-            if (u < Z) {
-                const T L = T(__ldg(llr + u));
-                T sum = L;
-                if constexpr (kFixed) {
-#pragma unroll
-                    for (int b = 0; b < DV; ++b) sum += cb[b][u];
-                } else {
-                    for (int b = 0; b < nd; ++b) sum += c2v[__ldg(q.col_blk + cb0 + b) * Z + u];
-                }
-                app[u] = sum;
-                if (inV) {
-                    acc += absm(sum);
-                    acc0 += absm(L);
-                }
-                if (k < p.trace_iters) {
-                    if (p.trace_app) p.trace_app[((size_t)k * p.frames + f) * (size_t)p.n + j * Z + u] = sum;
-                    if (p.trace_c2v) trace_c2v_qc(p, q, c2v, f, k, u, cb0, nd);
-                }
+                for (int b = 0; b < DV; ++b) sum += cb[b][u];
+            } else {
+                for (int b = 0; b < nd; ++b) sum += c2v[__ldg(q.col_blk + cb0 + b) * Z + u];
+            }
+            app[u] = sum;
+            if (inV) {
+                acc += absm(sum);
+                acc0 += absm(L);
+            }
+            if (tracing) {
+                if (p.trace_app) p.trace_app[((size_t)k * p.frames + f) * (size_t)p.n + j * Z + u] = sum;
+                if (p.trace_c2v) trace_c2v_qc(p, q, c2v, f, k, u, cb0, nd);
             }
         }
     }
@@ -614,9 +631,9 @@ __device__ __forceinline__ void qc_vn_cols(const Params<T>& p, const QcDev& q, i
 
 template <typename T>
 __device__ __forceinline__ void vn_tile(const Params<T>& p, const QcDev& q, int s, int f, int k, int tile) {
-    const int per_col = (q.Z + kVnTile - 1) / kVnTile;
+    const int per_col = (q.Z + kQcVnChunk - 1) / kQcVnChunk;
     const int j = tile / per_col;
-    const int u0 = (tile - j * per_col) * kVnTile;
+    const int u0 = (tile - j * per_col) * kQcVnChunk;
     const int cb0 = __ldg(q.col_ptr + j);
     const int dv = __ldg(q.col_ptr + j + 1) - cb0;
     switch (dv) {
@@ -673,21 +690,16 @@ __device__ __forceinline__ void final_tile(const Params<T>& p, int s, int f, int
     }
 }
 
-// QC tiles run per column block, so the variable index of a tile differs.
+// QC items run per column block, so the variable range of an item differs.
 template <typename T>
 __device__ __forceinline__ void final_tile(const Params<T>& p, const QcDev& q, int s, int f, int tile) {
-    const int per_col = (q.Z + kVnTile - 1) / kVnTile;
+    const int per_col = (q.Z + kQcVnChunk - 1) / kQcVnChunk;
     const int j = tile / per_col;
-    const int u0 = (tile - j * per_col) * kVnTile;
-    const T* app = p.app + (long long)s * p.n;
-    unsigned char* bits = p.bits_out + (long long)f * p.n;
-    for (int c = 0; c < kVPT; ++c) {
-        const int u = u0 + c * kThreads + (int)threadIdx.x;
-        if (u < q.Z) {
-            const long long v = (long long)j * q.Z + u;
-            bits[v] = (unsigned char)(app[v] < T(0));
-        }
-    }
+    const int u0 = (tile - j * per_col) * kQcVnChunk;
+    const int u_end = min(u0 + kQcVnChunk, q.Z);
+    const T* app = p.app + (size_t)s * (size_t)p.n + j * q.Z;
+    unsigned char* bits = p.bits_out + (size_t)f * (size_t)p.n + j * q.Z;
+    for (int u = u0 + (int)threadIdx.x; u < u_end; u += kThreads) bits[u] = (unsigned char)(app[u] < T(0));
 }
 template <typename T>
 __device__ __forceinline__ void final_tile(const Params<T>& p, const CsrDev&, int s, int f, int tile) {

@@ -400,8 +400,8 @@ ldpc_status ldpc_graph_create_qc(int32_t mb, int32_t nb, int32_t Z, const int32_
         return st;
     }
     g->qc = QcDev{mb, nb, Z, nblk, d[0], d[1], d[2], d[3], d[4], d[5]};
-    g->cn_tiles = mb * ((Z + kCnTile - 1) / kCnTile);
-    g->vn_tiles = nb * ((Z + kVnTile - 1) / kVnTile);
+    g->cn_tiles = mb * ((Z + kQcCnChunk - 1) / kQcCnChunk);
+    g->vn_tiles = nb * ((Z + kQcVnChunk - 1) / kQcVnChunk);
     *out = g;
     return LDPC_OK;
 }
