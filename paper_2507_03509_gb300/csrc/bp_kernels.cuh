@@ -289,13 +289,15 @@ __device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, i
         vo[j] = __ldg(q.blk_col + b0 + j) * Z;
         mo[j] = (b0 + j) * Z;
     }
+    // checks in flight per thread: more for light rows (memory-level parallelism)
+    constexpr int NC = 2;
     bool unsat = false;
-    for (int tb = t0 + (int)threadIdx.x; tb < t_end; tb += 2 * kThreads) {
-        int pos[2][D];
-        T a[2][D], o[2][D];
-        bool ok[2];
+    for (int tb = t0 + (int)threadIdx.x; tb < t_end; tb += NC * kThreads) {
+        int pos[NC][D];
+        T a[NC][D], o[NC][D];
+        bool ok[NC];
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
+        for (int c = 0; c < NC; ++c) {
             const int t = tb + c * kThreads;
             ok[c] = t < t_end;
 #pragma unroll
@@ -314,7 +316,7 @@ __device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, i
             }
         }
 #pragma unroll
-        for (int c = 0; c < 2; ++c) {
+        for (int c = 0; c < NC; ++c) {
             if (!ok[c]) continue;
             const int t = tb + c * kThreads;
             const int bit = sbit0 + t;
