@@ -49,7 +49,8 @@ typedef enum ldpc_status {
     LDPC_ERR_INVALID_GRAPH = 2, /* malformed CSR / QC description */
     LDPC_ERR_OOM = 3,           /* device or pinned-host allocation failed */
     LDPC_ERR_CUDA = 4,          /* a CUDA runtime call failed (no device, launch error, ...) */
-    LDPC_ERR_TIMEOUT = 5        /* a grid-wide wait inside the decoder ran out; results invalid */
+    LDPC_ERR_TIMEOUT = 5,       /* a grid-wide wait inside the decoder ran out; results invalid */
+    LDPC_ERR_TOO_LARGE = 6      /* the problem does not fit ldpc_decode_qc_noalloc's fixed scratch */
 } ldpc_status;
 
 /* Termination rule (paper section "Early Termination"; the baselines of
@@ -162,6 +163,40 @@ LDPC_API ldpc_status ldpc_decode_host(const ldpc_graph* graph, int32_t frames, c
                              const uint8_t* syndrome, int32_t max_iter, ldpc_term_rule rule,
                              uint8_t* bits_out, uint8_t* flags_out, int32_t* iters_out,
                              const ldpc_decode_opts* opts, void* cuda_stream);
+
+/* Device scratch that ldpc_decode_qc_noalloc works in: one fixed array of this
+ * many bytes, reserved on every GPU that loads the library, for as long as the
+ * library stays loaded. */
+#define LDPC_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+
+/* ldpc_graph_create_qc + ldpc_decode in one call that allocates nothing.
+ * The paper has no counterpart: this is a service for callers that must not
+ * allocate device memory themselves -- real-time reconciliation loops whose
+ * latency budget cannot absorb cudaMalloc/cudaFree (both can synchronise the
+ * device and take unbounded time), and host processes whose memory manager
+ * reserves the GPU's memory up front and forbids allocations outside it.
+ *
+ * Arguments: the QC base matrix as in ldpc_graph_create_qc (host int32
+ * mb x nb, -1 = zero block), then the inputs and outputs as in ldpc_decode
+ * (device buffers, caller-owned).  The decode uses the default options (FP32,
+ * vnr_first_iter 2, clamp 25).  The graph tables and all decoder state live in
+ * one file-scope device array of LDPC_NOALLOC_SCRATCH_BYTES; as many frames as
+ * fit are decoded at once and the rest wait in the queue.
+ *
+ * Limits: the packed syndrome of all frames plus the state of one frame
+ * (about 14 bytes per edge plus 8 bytes per variable) must fit the scratch,
+ * else LDPC_ERR_TOO_LARGE is returned before any GPU work.
+ *
+ * Set-up: the first call on each device looks up that device's address of the
+ * scratch array (with that device current); later calls reuse it.
+ * Sharing: every call on a device uses the same scratch, which keeps whatever
+ * the previous call left (the call clears what has to start at zero).  Calls
+ * whose GPU work overlaps -- on two streams, or from two threads -- race on it,
+ * so callers must order them.  The call returns after its stream has drained. */
+LDPC_API ldpc_status ldpc_decode_qc_noalloc(int32_t mb, int32_t nb, int32_t Z, const int32_t* shifts,
+                                            int32_t frames, const float* llr, const uint8_t* syndrome,
+                                            int32_t max_iter, ldpc_term_rule rule, uint8_t* bits_out,
+                                            uint8_t* flags_out, int32_t* iters_out, void* cuda_stream);
 
 /* Static, human-readable name of a status code. */
 LDPC_API const char* ldpc_status_str(ldpc_status status);

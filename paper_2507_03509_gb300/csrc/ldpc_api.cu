@@ -10,6 +10,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -295,6 +296,7 @@ const char* ldpc_status_str(ldpc_status s) {
         case LDPC_ERR_OOM: return "out of memory";
         case LDPC_ERR_CUDA: return "CUDA error";
         case LDPC_ERR_TIMEOUT: return "grid synchronisation timed out";
+        case LDPC_ERR_TOO_LARGE: return "problem too large for the fixed no-allocation scratch";
     }
     return "unknown status";
 }
@@ -499,3 +501,195 @@ ldpc_status ldpc_decode_host(const ldpc_graph* graph, int32_t frames, const floa
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Entry point that allocates nothing: ldpc_decode_qc_noalloc.
+//
+// For callers that must not allocate device memory (real-time loops that
+// cannot pay for cudaMalloc/cudaFree, hosts whose memory manager owns the
+// GPU's memory).  All device state lives in one file-scope array; the host
+// side only copies the QC tables in, clears the control words and launches
+// the same two kernels ldpc_decode uses.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr size_t kNoallocBytes = LDPC_NOALLOC_SCRATCH_BYTES;
+constexpr int kNoallocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+
+std::mutex g_noalloc_mutex;
+void* g_noalloc_addr[kNoallocMaxDevices] = {};
+
+// Device address of the scratch on the current device.  In host code the
+// array's name is only a host-side stand-in, so the address is looked up once
+// per device with that device current.
+ldpc_status noalloc_scratch(int dev, char** out) {
+    if (dev < 0 || dev >= kNoallocMaxDevices) return LDPC_ERR_CUDA;
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || ptr == nullptr) return cuda_status(e == cudaSuccess ? cudaErrorUnknown : e);
+        g_noalloc_addr[dev] = ptr;
+    }
+    *out = (char*)g_noalloc_addr[dev];
+    return LDPC_OK;
+}
+
+struct NoallocLayout {
+    size_t ctrl, tables, sbits, unsat, qval, q0val, qpart, q0part, c2v, app, total;
+    int slots;
+};
+
+// Carve the scratch for `slots` concurrent frames; total > kNoallocBytes means it does not fit.
+NoallocLayout noalloc_layout(size_t table_ints, int64_t n, int64_t E, int vn_tiles, int frames, int swords,
+                             int slots) {
+    NoallocLayout L{};
+    size_t o = 0;
+    L.ctrl = o;   o = align_up(o + sizeof(Ctrl), 256);
+    L.tables = o; o = align_up(o + table_ints * sizeof(int), 256);
+    L.sbits = o;  o = align_up(o + (size_t)frames * swords * sizeof(unsigned), 256);
+    L.unsat = o;  o = align_up(o + 2 * (size_t)slots * sizeof(int), 256);
+    L.qval = o;   o = align_up(o + (size_t)slots * sizeof(double), 256);
+    L.q0val = o;  o = align_up(o + (size_t)slots * sizeof(double), 256);
+    L.qpart = o;  o = align_up(o + (size_t)slots * vn_tiles * kWarps * sizeof(double), 256);
+    L.q0part = o; o = align_up(o + (size_t)slots * vn_tiles * kWarps * sizeof(double), 256);
+    L.c2v = o;    o = align_up(o + (size_t)slots * (size_t)E * sizeof(float), 256);
+    L.app = o;    o = align_up(o + (size_t)slots * (size_t)n * sizeof(float), 256);
+    L.total = o;
+    L.slots = slots;
+    return L;
+}
+
+}  // namespace
+
+extern "C" ldpc_status ldpc_decode_qc_noalloc(int32_t mb, int32_t nb, int32_t Z, const int32_t* shifts,
+                                              int32_t frames, const float* llr, const uint8_t* syndrome,
+                                              int32_t max_iter, ldpc_term_rule rule, uint8_t* bits_out,
+                                              uint8_t* flags_out, int32_t* iters_out, void* cuda_stream) {
+    // ---- host-side checks (nothing queued yet) ----
+    if (mb < 1 || nb < 1 || Z < 1 || !shifts) return LDPC_ERR_INVALID_ARG;
+    if (frames < 0 || max_iter < 1 || (int)rule < LDPC_TERM_NONE || (int)rule > LDPC_TERM_PCE_VNR)
+        return LDPC_ERR_INVALID_ARG;
+    if (frames > 0 && (!llr || !syndrome || !bits_out || !flags_out || !iters_out)) return LDPC_ERR_INVALID_ARG;
+    if ((int64_t)mb * Z >= (1LL << 31) || (int64_t)nb * Z >= (1LL << 31)) return LDPC_ERR_INVALID_GRAPH;
+    std::vector<int> row_ptr(mb + 1, 0), blk_col, blk_shift, col_cnt(nb, 0);
+    for (int i = 0; i < mb; ++i) {
+        for (int j = 0; j < nb; ++j) {
+            const int32_t sv = shifts[(int64_t)i * nb + j];
+            if (sv < -1 || sv >= Z) return LDPC_ERR_INVALID_GRAPH;
+            if (sv >= 0) {
+                blk_col.push_back(j);
+                blk_shift.push_back(sv);
+                col_cnt[j]++;
+            }
+        }
+        row_ptr[i + 1] = (int)blk_col.size();
+        if (row_ptr[i + 1] - row_ptr[i] > kMaxDeg) return LDPC_ERR_INVALID_GRAPH;
+    }
+    const int nblk = (int)blk_col.size();
+    if ((int64_t)nblk * Z >= (1LL << 31)) return LDPC_ERR_INVALID_GRAPH;
+    std::vector<int> col_ptr(nb + 1, 0), col_blk(nblk), blk_row(nblk);
+    for (int i = 0; i < mb; ++i)
+        for (int b = row_ptr[i]; b < row_ptr[i + 1]; ++b) blk_row[b] = i;
+    for (int j = 0; j < nb; ++j) col_ptr[j + 1] = col_ptr[j] + col_cnt[j];
+    {
+        std::vector<int> fill(col_ptr.begin(), col_ptr.end() - 1);
+        for (int b = 0; b < nblk; ++b) col_blk[fill[blk_col[b]]++] = b;
+    }
+    // one host table, uploaded in one copy: row_ptr | blk_col | blk_shift | col_ptr | col_blk | blk_row
+    std::vector<int> table;
+    table.reserve((size_t)(mb + 1) + 4 * (size_t)nblk + (size_t)(nb + 1));
+    size_t off[6];
+    const std::vector<int>* parts[6] = {&row_ptr, &blk_col, &blk_shift, &col_ptr, &col_blk, &blk_row};
+    for (int k = 0; k < 6; ++k) {
+        off[k] = table.size();
+        table.insert(table.end(), parts[k]->begin(), parts[k]->end());
+    }
+    const int32_t m = mb * Z, n = nb * Z;
+    const int64_t E = (int64_t)nblk * Z;
+    const int swords = (m + 31) / 32;
+    const int vn_tiles = nb * ((Z + kQcVnChunk - 1) / kQcVnChunk);
+    const int cn_tiles = mb * ((Z + kQcCnChunk - 1) / kQcCnChunk);
+    if (frames == 0) return LDPC_OK;
+    int slots = std::min(frames, kMaxSlots);
+    while (slots > 0 && noalloc_layout(table.size(), n, E, vn_tiles, frames, swords, slots).total > kNoallocBytes)
+        --slots;
+    if (slots < 1) return LDPC_ERR_TOO_LARGE;
+    const NoallocLayout L = noalloc_layout(table.size(), n, E, vn_tiles, frames, swords, slots);
+
+    // ---- device work, all inside the fixed scratch ----
+    int dev = 0, sms = 0, per_sm = 0, coop = 0;
+    LDPC_TRY(cudaGetDevice(&dev));
+    char* base = nullptr;
+    ldpc_status st = noalloc_scratch(dev, &base);
+    if (st != LDPC_OK) return st;
+    cudaStream_t stream = (cudaStream_t)cuda_stream;
+    LDPC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    LDPC_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) return LDPC_ERR_CUDA;
+    auto kernel = bp_decode_kernel<float, QcDev>;
+    const size_t smem = (size_t)slots * (sizeof(double) + 5 * sizeof(int));
+    if (smem > 48 * 1024)
+        LDPC_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LDPC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem));
+    if (per_sm < 1) return LDPC_ERR_CUDA;
+    const int grid = per_sm * sms;
+
+    int* dtab = (int*)(base + L.tables);
+    LDPC_TRY(cudaMemcpyAsync(dtab, table.data(), table.size() * sizeof(int), cudaMemcpyHostToDevice, stream));
+    const QcDev code{mb, nb, Z, nblk, dtab + off[0], dtab + off[1], dtab + off[2], dtab + off[3], dtab + off[4],
+                     dtab + off[5]};
+    Ctrl* ctrl = (Ctrl*)(base + L.ctrl);
+    LDPC_TRY(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), stream));
+    LDPC_TRY(cudaMemsetAsync(base + L.unsat, 0, 2 * (size_t)slots * sizeof(int), stream));
+
+    Params<float> p{};
+    p.m = m;
+    p.n = n;
+    p.E = E;
+    p.frames = frames;
+    p.max_iter = max_iter;
+    p.rule = (int)rule;
+    p.vnr_first_iter = 2;
+    p.lmax = 25.0f;
+    p.llr = llr;
+    p.sbits = (const unsigned*)(base + L.sbits);
+    p.swords = swords;
+    p.bits_out = bits_out;
+    p.flags_out = flags_out;
+    p.iters_out = iters_out;
+    p.slots = slots;
+    p.c2v = (float*)(base + L.c2v);
+    p.app = (float*)(base + L.app);
+    p.qpart = (double*)(base + L.qpart);
+    p.q0part = (double*)(base + L.q0part);
+    p.qval = (double*)(base + L.qval);
+    p.q0val = (double*)(base + L.q0val);
+    p.unsat = (int*)(base + L.unsat);
+    p.ctrl = ctrl;
+    p.cn_tiles = cn_tiles;
+    p.vn_tiles = vn_tiles;
+    p.trace_iters = 0;
+    p.timeout_ns = kBarrierTimeoutNs;
+    p.vec4 = ((Z % 4) == 0 && ((uintptr_t)llr % 16) == 0) ? 1 : 0;
+    {
+        const long long warps = (long long)frames * swords;
+        long long blocks = (warps * 32 + 255) / 256;
+        blocks = std::max(1LL, std::min(blocks, (long long)sms * 8));
+        pack_syndrome_kernel<<<(unsigned)blocks, 256, 0, stream>>>(syndrome, frames, m, swords,
+                                                                   (unsigned*)(base + L.sbits), ctrl);
+        LDPC_TRY(cudaGetLastError());
+    }
+    void* args[] = {(void*)&p, (void*)&code};
+    LDPC_TRY(cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(kThreads), args, smem, stream));
+    int err = 0;
+    LDPC_TRY(cudaMemcpyAsync(&err, &ctrl->err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    LDPC_TRY(cudaStreamSynchronize(stream));
+    if (err == kErrSyndrome) return LDPC_ERR_INVALID_ARG;
+    if (err == kErrTimeout) return LDPC_ERR_TIMEOUT;
+    if (err != kErrNone) return LDPC_ERR_CUDA;
+    return LDPC_OK;
+}
+

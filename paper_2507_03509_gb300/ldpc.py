@@ -25,6 +25,7 @@ LDPC_ERR_INVALID_GRAPH = 2
 LDPC_ERR_OOM = 3
 LDPC_ERR_CUDA = 4
 LDPC_ERR_TIMEOUT = 5
+LDPC_ERR_TOO_LARGE = 6
 
 LDPC_TERM_NONE = 0
 LDPC_TERM_PCE = 1
@@ -37,7 +38,9 @@ RULES = {"none": LDPC_TERM_NONE, "pce": LDPC_TERM_PCE, "pce_vnr": LDPC_TERM_PCE_
 
 EXPORTED = ("ldpc_decode_opts_init", "ldpc_graph_create_csr", "ldpc_graph_create_qc",
             "ldpc_graph_destroy", "ldpc_graph_info", "ldpc_decode", "ldpc_decode_host",
-            "ldpc_status_str")
+            "ldpc_status_str", "ldpc_decode_qc_noalloc")
+
+NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 
 
 class ldpc_decode_stats(ctypes.Structure):
@@ -79,6 +82,8 @@ def _load():
     lib.ldpc_decode_host.restype = ctypes.c_int
     lib.ldpc_status_str.argtypes = [ctypes.c_int]
     lib.ldpc_status_str.restype = ctypes.c_char_p
+    lib.ldpc_decode_qc_noalloc.argtypes = [i32, i32, i32, P, i32, P, P, i32, ctypes.c_int, P, P, P, P]
+    lib.ldpc_decode_qc_noalloc.restype = ctypes.c_int
     return lib
 
 
@@ -155,6 +160,19 @@ def ldpc_decode_host(handle: int, frames: int, llr_ptr: int, syndrome_ptr: int, 
     """Raw call with host pointers; returns the status code."""
     return _lib.ldpc_decode_host(handle, int(frames), llr_ptr, syndrome_ptr, int(max_iter), int(rule), bits_ptr,
                                  flags_ptr, iters_ptr, ctypes.byref(opts) if opts is not None else None, stream)
+
+
+def ldpc_decode_qc_noalloc(mb: int, nb: int, Z: int, shifts, frames: int, llr_ptr: int, syndrome_ptr: int,
+                           max_iter: int, rule: int, bits_ptr: int, flags_ptr: int, iters_ptr: int,
+                           stream: int) -> int:
+    """Raw call of the entry point that allocates no device memory (for callers
+    that must not allocate: real-time loops, hosts whose memory manager owns the
+    GPU).  shifts is a host int32 mb x nb array; the other pointers are device
+    buffers as in ldpc_decode.  Returns the status code."""
+    sh = np.ascontiguousarray(shifts, dtype=np.int32)
+    return _lib.ldpc_decode_qc_noalloc(int(mb), int(nb), int(Z), sh.ctypes.data, int(frames), llr_ptr,
+                                       syndrome_ptr, int(max_iter), int(rule), bits_ptr, flags_ptr, iters_ptr,
+                                       stream)
 
 
 # --------------------------------------------------------------------------

@@ -82,6 +82,15 @@ def test_malformed_qc_is_rejected_on_host(ldpc, shifts, Z, status):
     assert ei.value.status == status
 
 
+def test_noalloc_rejects_oversize_before_any_gpu_work(ldpc):
+    # one Z = 2^30 circulant: its packed syndrome alone exceeds the fixed scratch
+    st = ldpc.ldpc_decode_qc_noalloc(1, 1, 1 << 30, np.zeros((1, 1), np.int32), 1, 16, 16, 10, 2, 16, 16, 16, None)
+    assert st == ldpc.LDPC_ERR_TOO_LARGE
+    assert "too large" in ldpc.ldpc_status_str(st)
+    assert ldpc.ldpc_decode_qc_noalloc(1, 1, 4, np.full((1, 1), 4, np.int32), 1, 16, 16, 10, 2, 16, 16, 16,
+                                       None) == ldpc.LDPC_ERR_INVALID_GRAPH
+
+
 def test_decode_argument_errors_need_no_gpu(ldpc):
     # a null graph and bad sizes are refused before any CUDA call
     assert ldpc.ldpc_decode(None, 1, 1, 1, 10, 2, 1, 1, 1, None, None) == ldpc.LDPC_ERR_INVALID_ARG
