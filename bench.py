@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--frames", type=int, default=None)
     ap.add_argument("--slots", type=int, default=0, help="max_active_frames (0 = automatic)")
     ap.add_argument("--grid", type=int, default=0, help="grid_ctas (0 = all that fit)")
+    ap.add_argument("--groups", type=int, default=0, help="independent CTA groups (0 = automatic)")
     ap.add_argument("--compare-steps", type=int, default=2, help="timed steps of each fixed-iteration rule")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
@@ -254,7 +255,7 @@ def run_ours(args):
 
     def one(rule, stats):
         return ldpc.decode(graph, llr, syn, wl["max_iter"], rule, out=out, stats=stats,
-                           max_active_frames=args.slots, grid_ctas=args.grid)
+                           max_active_frames=args.slots, grid_ctas=args.grid, groups=args.groups)
 
     def timed(rule, steps, warmup):
         for _ in range(warmup):
@@ -329,13 +330,13 @@ def run_ours(args):
     for _ in range(1 if e2e_steps else 0):
         ldpc.decode_host(graph, h_llr.numpy(), h_syn.numpy(), wl["max_iter"], "pce_vnr",
                          out=(h_bits.numpy(), h_flags.numpy(), h_iters.numpy()), stream=stream.cuda_stream,
-                         max_active_frames=args.slots, grid_ctas=args.grid)
+                         max_active_frames=args.slots, grid_ctas=args.grid, groups=args.groups)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         ldpc.decode_host(graph, h_llr.numpy(), h_syn.numpy(), wl["max_iter"], "pce_vnr",
                          out=(h_bits.numpy(), h_flags.numpy(), h_iters.numpy()), stream=stream.cuda_stream,
-                         max_active_frames=args.slots, grid_ctas=args.grid)
+                         max_active_frames=args.slots, grid_ctas=args.grid, groups=args.groups)
     e2e_s = time.perf_counter() - t0
     e2e = None if not e2e_steps else {"value": code.n * F * e2e_steps / e2e_s / 1e6, "unit": UNIT,
            "h2d_bytes_per_step": int(frames.llr.nbytes + frames.syndrome.nbytes),
@@ -359,7 +360,7 @@ def run_ours(args):
                    "rate": code.rate, "beta": wl["beta"], "max_iter": wl["max_iter"], "rule": "pce_vnr",
                    "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": "inputs 159 MB + decoder state > L2 (129 MB); L2 also flushed between steps",
-                   "slots": main["slots"], "grid_ctas": main["grid"]},
+                   "slots": main["slots"], "grid_ctas": main["grid"], "groups": args.groups or "auto"},
         "d_mean": main["d_mean"], "fer": main["fer"], "success_frames": main["success"],
         "aborted_frames": main["aborted"], "edge_msgs_per_s": edge_msgs, "goodput_mbit_s": goodput,
         "fixed_iteration": comp,

@@ -89,9 +89,12 @@ typedef struct ldpc_decode_opts {
                                   default 25.  Must be finite and > 0.                         */
     int32_t fp64;              /* 0: FP32 messages (default).  1: FP64 debug mode, which takes
                                   the tanh/atanh rule literally (slow on GB300's FP64 units).  */
-    int32_t max_active_frames; /* frames decoded concurrently, 0 = automatic.  Others wait in
-                                  a queue and start as running frames terminate.  <= 1024.     */
-    int32_t grid_ctas;         /* CTAs of the persistent kernel, 0 = all that fit on the GPU. */
+    int32_t max_active_frames; /* frames decoded concurrently (slots), 0 = automatic (all of
+                                  them, at most 1024).  Others wait in a queue and start as
+                                  running frames terminate.  Rounded up to a multiple of the
+                                  group count.                                                */
+    int32_t grid_ctas;         /* CTAs of the persistent kernel, 0 = all that fit on the GPU;
+                                  rounded down to a multiple of the group count.              */
     int32_t trace_iters;       /* record messages of iterations 1..trace_iters (0 = off)      */
     void* trace_c2v;           /* device [trace_iters][frames][E] check-to-variable messages,
                                   edges in row-major order of H (CSR order; for QC codes the
@@ -101,6 +104,17 @@ typedef struct ldpc_decode_opts {
                                   double as above.  May be NULL.                               */
     double* trace_q;           /* device [trace_iters][frames] q^(k).  May be NULL.           */
     ldpc_decode_stats* stats;  /* host; filled when not NULL                                   */
+    int32_t barrier_timeout_ms; /* limit of one barrier wait inside the decoder; 0 = 10000.
+                                   A wait that runs out ends the call with LDPC_ERR_TIMEOUT.   */
+    int32_t test_unreachable_barrier; /* failure-injection hook for tests only: nonzero makes
+                                   the first grid-wide wait expect one CTA more than the grid
+                                   has, so the waits run out after barrier_timeout_ms and the
+                                   call returns LDPC_ERR_TIMEOUT.  Leave 0.                    */
+    int32_t groups;            /* independent CTA groups, 0 = automatic (one CTA of each group
+                                  per SM, at most one group per running frame).  Each group
+                                  advances its own frames in lock-step between its own
+                                  barriers, and frames that stop are replaced from one shared
+                                  queue.  Results are bit-identical for any value.             */
 } ldpc_decode_opts;
 
 /* Fill *opts with the defaults (vnr_first_iter 2, clamp 25, FP32, automatic

@@ -37,11 +37,17 @@ enum : int { kErrNone = 0, kErrTimeout = 1, kErrSyndrome = 2 };
 enum : int { kModeFirst = 0, kModeFull = 1, kModeSynd = 2 };
 enum : int { kRuleNone = 0, kRulePce = 1, kRulePceVnr = 2 };
 
-struct Ctrl {
+constexpr int kMaxGrid = 4096;            // largest grid either decoder kernel is launched with
+
+constexpr int kMaxGroups = 64;
+
+// One per group (its barrier), 128 bytes apart; the first one also holds the
+// error word, the iteration total and the queue of waiting frames.
+struct alignas(128) Ctrl {
     unsigned bar_count;
     unsigned bar_gen;
     int err;
-    int pad;
+    int next_frame;                  // frames handed out so far
     unsigned long long frame_iters;  // sum over frames of D
 };
 
@@ -96,6 +102,11 @@ struct Params {
     double* trace_q;               // [trace_iters][frames]
     unsigned long long timeout_ns;
     int vec4;                      // 16-byte variable-node path allowed (Z % 4 == 0, aligned llr)
+    unsigned bar_extra;            // test hook: arrivals the first barrier waits for beyond the grid
+    int groups;                    // independent CTA groups, each with its own slots and barrier
+    int slots_per_group;           // slots = groups * slots_per_group
+    int* new_frame;                // [slots] frame taken from the queue by a slot that stopped
+    int cn_chunk, vn_chunk;        // QC items: checks of one base row / variables of one base column
 };
 
 // ---------------------------------------------------------------------------
@@ -122,35 +133,40 @@ __device__ __forceinline__ double clampm(double x, double l) { return fmin(fmax(
 __device__ __forceinline__ float absm(float x) { return fabsf(x); }
 __device__ __forceinline__ double absm(double x) { return fabs(x); }
 
-// Grid-wide barrier for a cooperative launch.  Thread 0 of each CTA arrives
-// on a counter; the last arrival resets it and releases a new generation.
-// A wait longer than timeout_ns (or any error raised elsewhere) ends it with
-// the error word set; the return value says whether the decode may go on.
-__device__ __forceinline__ bool grid_sync(Ctrl* ctrl, unsigned long long timeout_ns) {
+// Barrier over the nblocks CTAs of one group (a cooperative launch keeps them
+// all resident).  The group's arrival counter only grows: thread 0 of each
+// CTA adds 1 with a release reduction (no reply to wait for) and then waits,
+// with acquire loads, until the counter reaches nblocks times the number of
+// barriers passed so far (`epoch`, counted locally).  A wait longer than
+// timeout_ns (or any error raised elsewhere) ends it with the error word set;
+// the return value says whether the decode may go on.  `extra` (a test hook)
+// makes the barrier wait for more CTAs than exist.
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ bool grid_sync(Ctrl* bar, int* err, unsigned nblocks, unsigned epoch,
+                                          unsigned long long timeout_ns, unsigned extra = 0) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned gen = ld_acquire(&ctrl->bar_gen);
-        __threadfence();
-        const unsigned prev = atomicAdd(&ctrl->bar_count, 1u);
-        if (prev == gridDim.x - 1) {
-            ctrl->bar_count = 0;
-            st_release(&ctrl->bar_gen, gen + 1);
-        } else {
-            const unsigned long long t0 = global_ns();
-            unsigned spins = 0;
-            while (ld_acquire(&ctrl->bar_gen) == gen) {
-                if (ld_volatile(&ctrl->err) != kErrNone) break;
-                if (++spins > 64) __nanosleep(128);
+        const unsigned target = epoch * nblocks + extra;
+        red_release_add(&bar->bar_count, 1u);
+        unsigned spins = 0;
+        unsigned long long t0 = 0;
+        while ((int)(ld_acquire(&bar->bar_count) - target) < 0) {
+            if (++spins > 32) {
+                if (t0 == 0) t0 = global_ns();
+                __nanosleep(64);
+                if (ld_volatile(err) != kErrNone) break;
                 if (global_ns() - t0 > timeout_ns) {
-                    atomicCAS(&ctrl->err, kErrNone, kErrTimeout);
+                    atomicCAS(err, kErrNone, kErrTimeout);
                     break;
                 }
             }
         }
-        __threadfence();
     }
     __syncthreads();
-    return ld_volatile(&ctrl->err) == kErrNone;
+    return ld_volatile(err) == kErrNone;
 }
 
 // ---------------------------------------------------------------------------
@@ -261,21 +277,21 @@ __device__ __forceinline__ unsigned syndrome_bit(const unsigned* sb, int row) {
 }
 
 // ---------------------------------------------------------------------------
-// Quasi-cyclic check-node item: checks t in [t0, t0 + kQcCnChunk) of base row
+// Quasi-cyclic check-node item: checks t in [t0, t0 + p.cn_chunk) of base row
 // i.  The row's block pointers are set up once; each thread then walks the
 // chunk two checks at a time (both checks' loads issued before any
 // arithmetic).  MODE and SYND are compile-time so the hot loop carries no
 // mode tests: kModeFirst reads Lch with c2v = 0, kModeFull reads APP and the
 // old c2v, kModeSynd only tests the syndrome of the current decision.
 // ---------------------------------------------------------------------------
-constexpr int kQcCnChunk = 2048;         // checks of one base row per item
-constexpr int kQcVnChunk = 4096;         // variables of one base column per item
+constexpr int kQcCnChunk = 2048;         // default checks of one base row per item (multiple of 2*kThreads)
+constexpr int kQcVnChunk = 4096;         // default variables of one base column per item (multiple of 4*kThreads)
 
 template <int D, int MODE, bool SYND, typename T>
 __device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, int s, int f, int i, int t0,
                                            int b0) {
     const int Z = q.Z;
-    const int t_end = min(t0 + kQcCnChunk, Z);
+    const int t_end = min(t0 + p.cn_chunk, Z);
     T* c2v = p.c2v + (size_t)s * (size_t)p.E;
     const T* app = p.app + (size_t)s * (size_t)p.n;
     const float* llr = p.llr + (size_t)f * (size_t)p.n;
@@ -344,7 +360,7 @@ __device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, i
 template <int MODE, bool SYND, typename T>
 __device__ bool qc_cn_item_n(const Params<T>& p, const QcDev& q, int s, int f, int i, int t0, int b0, int d) {
     const int Z = q.Z;
-    const int t_end = min(t0 + kQcCnChunk, Z);
+    const int t_end = min(t0 + p.cn_chunk, Z);
     T* c2v = p.c2v + (size_t)s * (size_t)p.E;
     const T* app = p.app + (size_t)s * (size_t)p.n;
     const float* llr = p.llr + (size_t)f * (size_t)p.n;
@@ -389,7 +405,7 @@ __device__ __forceinline__ bool qc_cn_dispatch(const Params<T>& p, const QcDev& 
             bool unsat = false;
             if (SYND) {
                 const unsigned* sb = p.sbits + (size_t)f * (size_t)p.swords;
-                const int t_end = min(t0 + kQcCnChunk, q.Z);
+                const int t_end = min(t0 + p.cn_chunk, q.Z);
                 for (int t = t0 + (int)threadIdx.x; t < t_end; t += kThreads)
                     unsat |= syndrome_bit(sb, i * q.Z + t) != 0u;
             }
@@ -408,9 +424,9 @@ __device__ __forceinline__ bool qc_cn_dispatch(const Params<T>& p, const QcDev& 
 template <typename T>
 __device__ __forceinline__ bool cn_tile(const Params<T>& p, const QcDev& q, int s, int f, int k,
                                         int mode, bool want_synd, int tile) {
-    const int per_row = (q.Z + kQcCnChunk - 1) / kQcCnChunk;
+    const int per_row = (q.Z + p.cn_chunk - 1) / p.cn_chunk;
     const int i = tile / per_row;
-    const int t0 = (tile - i * per_row) * kQcCnChunk;
+    const int t0 = (tile - i * per_row) * p.cn_chunk;
     const int b0 = __ldg(q.row_ptr + i);
     const int d = __ldg(q.row_ptr + i + 1) - b0;
     (void)k;
@@ -542,7 +558,7 @@ __device__ void trace_c2v_qc(const Params<T>& p, const QcDev& q, const T* c2v, i
     }
 }
 
-// Quasi-cyclic variable-node item: variables u in [u0, u0 + kQcVnChunk) of
+// Quasi-cyclic variable-node item: variables u in [u0, u0 + p.vn_chunk) of
 // base column j.  DV > 0: compile-time column degree; DV == 0: runtime dv.
 // With vec (Z % 4 == 0, aligned Lch) each thread handles groups of four
 // consecutive variables with 16-byte loads and stores.
@@ -551,7 +567,7 @@ __device__ __forceinline__ void qc_vn_cols(const Params<T>& p, const QcDev& q, i
                                            int j, int u0, int cb0, int dv) {
     constexpr bool kFixed = DV > 0;
     const int Z = q.Z;
-    const int u_end = min(u0 + kQcVnChunk, Z);
+    const int u_end = min(u0 + p.vn_chunk, Z);
     const int nd = kFixed ? DV : dv;
     const bool inV = nd > 1;
     const bool want_q0 = (k == 0) && p.vnr_first_iter <= 1;
@@ -633,9 +649,9 @@ __device__ __forceinline__ void qc_vn_cols(const Params<T>& p, const QcDev& q, i
 
 template <typename T>
 __device__ __forceinline__ void vn_tile(const Params<T>& p, const QcDev& q, int s, int f, int k, int tile) {
-    const int per_col = (q.Z + kQcVnChunk - 1) / kQcVnChunk;
+    const int per_col = (q.Z + p.vn_chunk - 1) / p.vn_chunk;
     const int j = tile / per_col;
-    const int u0 = (tile - j * per_col) * kQcVnChunk;
+    const int u0 = (tile - j * per_col) * p.vn_chunk;
     const int cb0 = __ldg(q.col_ptr + j);
     const int dv = __ldg(q.col_ptr + j + 1) - cb0;
     switch (dv) {
@@ -695,10 +711,10 @@ __device__ __forceinline__ void final_tile(const Params<T>& p, int s, int f, int
 // QC items run per column block, so the variable range of an item differs.
 template <typename T>
 __device__ __forceinline__ void final_tile(const Params<T>& p, const QcDev& q, int s, int f, int tile) {
-    const int per_col = (q.Z + kQcVnChunk - 1) / kQcVnChunk;
+    const int per_col = (q.Z + p.vn_chunk - 1) / p.vn_chunk;
     const int j = tile / per_col;
-    const int u0 = (tile - j * per_col) * kQcVnChunk;
-    const int u_end = min(u0 + kQcVnChunk, q.Z);
+    const int u0 = (tile - j * per_col) * p.vn_chunk;
+    const int u_end = min(u0 + p.vn_chunk, q.Z);
     const T* app = p.app + (size_t)s * (size_t)p.n + j * q.Z;
     unsigned char* bits = p.bits_out + (size_t)f * (size_t)p.n + j * q.Z;
     for (int u = u0 + (int)threadIdx.x; u < u_end; u += kThreads) bits[u] = (unsigned char)(app[u] < T(0));
@@ -711,7 +727,16 @@ __device__ __forceinline__ void final_tile(const Params<T>& p, const CsrDev&, in
 // Deterministic FP64 sum of a frame's per-tile partials (fixed order).
 __device__ __forceinline__ double block_sum_fixed(const double* part, int count, double* s_red) {
     double acc = 0.0;
-    for (int t = threadIdx.x; t < count; t += kThreads) acc += part[t];
+    for (int base = 0; base < count; base += 8 * kThreads) {  // 8 loads in flight per thread
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int t = base + u * kThreads + (int)threadIdx.x;
+            v[u] = t < count ? part[t] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc += v[u];
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -726,27 +751,41 @@ __device__ __forceinline__ double block_sum_fixed(const double* part, int count,
 
 // ---------------------------------------------------------------------------
 // The persistent decoder.
+//
+// The grid is split into `groups` independent groups (by default one CTA of
+// each group per SM).  A group owns slots_per_group slots and advances its
+// frames in lock-step between its own barriers; frames that stop are replaced
+// from one queue shared by all groups.  While one group waits at a barrier,
+// the other groups' CTAs on the same SMs keep computing, and only the few
+// frames in flight have to stay in L2.
 // ---------------------------------------------------------------------------
 template <typename T, class Code>
 __global__ void __launch_bounds__(kThreads, 4) bp_decode_kernel(Params<T> p, Code code) {
+    const int SG = p.slots_per_group;
     extern __shared__ double smem_dyn[];
-    double* st_qprev = smem_dyn;                       // [slots]
-    int* st_frame = (int*)(st_qprev + p.slots);         // [slots]
-    int* st_k = st_frame + p.slots;                     // [slots]
-    int* st_new = st_k + p.slots;                       // [slots]
-    int* listA = st_new + p.slots;                      // [slots]
-    int* listB = listA + p.slots;                       // [slots]
+    double* st_qprev = smem_dyn;                  // [SG]
+    int* st_frame = (int*)(st_qprev + SG);        // [SG]
+    int* st_k = st_frame + SG;                    // [SG]
+    int* listA = st_k + SG;                       // [SG]
+    int* listB = listA + SG;                      // [SG]
     __shared__ double s_red[kWarps];
-    __shared__ int s_nA, s_nB, s_next;
+    __shared__ int s_nA, s_nB;
 
-    for (int s = threadIdx.x; s < p.slots; s += kThreads) {
-        st_frame[s] = s < p.frames ? s : -1;
-        st_k[s] = 0;
-        st_qprev[s] = 0.0;
+    const int gsize = gridDim.x / p.groups;
+    const int g = blockIdx.x / gsize;
+    if (g >= p.groups) return;
+    const int lb = blockIdx.x - g * gsize;        // CTA index within the group
+    const int s0 = g * SG;                        // first (global) slot of the group
+    Ctrl* bar = p.ctrl + g;
+    int* err = &p.ctrl->err;
+
+    for (int l = threadIdx.x; l < SG; l += kThreads) {
+        st_frame[l] = s0 + l < p.frames ? s0 + l : -1;
+        st_k[l] = 0;
+        st_qprev[l] = 0.0;
     }
-    if (threadIdx.x == 0) s_next = p.slots < p.frames ? p.slots : p.frames;
     __syncthreads();
-    if (ld_volatile(&p.ctrl->err) != kErrNone) return;
+    if (ld_volatile(err) != kErrNone) return;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -756,11 +795,11 @@ __global__ void __launch_bounds__(kThreads, 4) bp_decode_kernel(Params<T> p, Cod
         // ---- running slots ------------------------------------------------
         if (warp == 0) {
             int cnt = 0;
-            for (int base = 0; base < p.slots; base += 32) {
-                const int s = base + lane;
-                const bool occ = s < p.slots && st_frame[s] >= 0;
+            for (int base = 0; base < SG; base += 32) {
+                const int l = base + lane;
+                const bool occ = l < SG && st_frame[l] >= 0;
                 const unsigned m = __ballot_sync(0xffffffffu, occ);
-                if (occ) listA[cnt + __popc(m & lt_mask)] = s;
+                if (occ) listA[cnt + __popc(m & lt_mask)] = l;
                 cnt += __popc(m);
             }
             if (lane == 0) s_nA = cnt;
@@ -771,21 +810,25 @@ __global__ void __launch_bounds__(kThreads, 4) bp_decode_kernel(Params<T> p, Cod
 
         // ---- phase A: check nodes + syndrome of the current decision -----
         const unsigned totalA = (unsigned)nA * (unsigned)p.cn_tiles;
-        for (unsigned it = blockIdx.x; it < totalA; it += gridDim.x) {
+        for (unsigned it = lb; it < totalA; it += gsize) {
             const unsigned si = it / (unsigned)p.cn_tiles;
-            const int s = listA[si];
+            const int l = listA[si];
+            const int s = s0 + l;
             const int tile = (int)(it - si * (unsigned)p.cn_tiles);
-            const int k = st_k[s];
+            const int k = st_k[l];
             const int mode = k == 0 ? kModeFirst : (k >= p.max_iter ? kModeSynd : kModeFull);
             const bool want_synd = k >= 1 && (p.rule != kRuleNone || k >= p.max_iter);
-            const bool unsat = cn_tile<T>(p, code, s, st_frame[s], k, mode, want_synd, tile);
+            const bool unsat = cn_tile<T>(p, code, s, st_frame[l], k, mode, want_synd, tile);
             if (want_synd && __any_sync(0xffffffffu, unsat) && lane == 0)
                 atomicOr(&p.unsat[par * p.slots + s], 1);
         }
-        // q^(k) of every running frame that has done an iteration
-        for (int i = blockIdx.x; i < nA; i += gridDim.x) {
-            const int s = listA[i];
-            const int k = st_k[s];
+        // q^(k) of every running frame that has done an iteration, by the CTAs
+        // at the end of the group, which get one item fewer when the items do
+        // not divide evenly
+        for (int i = gsize - 1 - lb; i >= 0 && i < nA; i += gsize) {
+            const int l = listA[i];
+            const int s = s0 + l;
+            const int k = st_k[l];
             if (k < 1) continue;
             const int np = p.vn_tiles * kWarps;
             const double qv = block_sum_fixed(p.qpart + (size_t)s * np, np, s_red);
@@ -795,88 +838,86 @@ __global__ void __launch_bounds__(kThreads, 4) bp_decode_kernel(Params<T> p, Cod
             if (threadIdx.x == 0) {
                 p.qval[s] = qv;
                 if (with_q0) p.q0val[s] = q0;
-                if (k <= p.trace_iters && p.trace_q) p.trace_q[(long long)(k - 1) * p.frames + st_frame[s]] = qv;
+                if (k <= p.trace_iters && p.trace_q) p.trace_q[(long long)(k - 1) * p.frames + st_frame[l]] = qv;
             }
         }
-        if (!grid_sync(p.ctrl, p.timeout_ns)) return;
+        if (!grid_sync(bar, err, gsize, 2u * step + 1u, p.timeout_ns, step == 0 ? p.bar_extra : 0u)) return;
 
-        // ---- decisions (warp 0 of every CTA, identical everywhere) --------
+        // ---- decisions (warp 0 of every CTA of the group, all alike) ------
         if (warp == 0) {
-            int cnt = 0, next = s_next;
-            for (int base = 0; base < p.slots; base += 32) {
-                const int s = base + lane;
+            int cnt = 0;
+            for (int base = 0; base < SG; base += 32) {
+                const int l = base + lane;
+                const int s = s0 + l;
                 int act = -1;  // 0 = continue, 1 = stop
-                if (s < p.slots && st_frame[s] >= 0) {
-                    const int k = st_k[s];
-                    const int f = st_frame[s];
+                if (l < SG && st_frame[l] >= 0) {
+                    const int k = st_k[l];
+                    const int f = st_frame[l];
                     if (k == 0) {
                         act = 0;
                     } else {
                         const bool sat = ld_volatile(&p.unsat[par * p.slots + s]) == 0;
                         const double qv = ld_volatile(&p.qval[s]);
                         const double qprev =
-                            (k == 1 && p.vnr_first_iter <= 1) ? ld_volatile(&p.q0val[s]) : st_qprev[s];
+                            (k == 1 && p.vnr_first_iter <= 1) ? ld_volatile(&p.q0val[s]) : st_qprev[l];
                         const bool succ = p.rule != kRuleNone && sat;
                         const bool abort_ = !succ && p.rule == kRulePceVnr && k >= p.vnr_first_iter && qv < qprev;
                         const bool end = k >= p.max_iter;
                         if (succ || abort_ || end) {
                             act = 1;
-                            if (blockIdx.x == 0) {
+                            if (lb == 0) {
                                 p.flags_out[f] = (unsigned char)((sat ? 1 : 0) | (abort_ ? 2 : 0));
                                 p.iters_out[f] = k;
                                 atomicAdd(&p.ctrl->frame_iters, (unsigned long long)k);
+                                const int nf = atomicAdd(&p.ctrl->next_frame, 1);
+                                p.new_frame[s] = nf < p.frames ? nf : -1;
                             }
                         } else {
                             act = 0;
-                            st_qprev[s] = qv;
+                            st_qprev[l] = qv;
                         }
                     }
                 }
                 const unsigned mAny = __ballot_sync(0xffffffffu, act >= 0);
-                const unsigned mStop = __ballot_sync(0xffffffffu, act == 1);
-                if (act >= 0) listB[cnt + __popc(mAny & lt_mask)] = s | (act << 16);
-                if (act == 1) {
-                    const int nf = next + __popc(mStop & lt_mask);
-                    st_new[s] = nf < p.frames ? nf : -1;
-                }
+                if (act >= 0) listB[cnt + __popc(mAny & lt_mask)] = l | (act << 16);
                 cnt += __popc(mAny);
-                next += __popc(mStop);
             }
-            if (lane == 0) {
-                s_nB = cnt;
-                s_next = next < p.frames ? next : p.frames;
-            }
+            if (lane == 0) s_nB = cnt;
         }
         __syncthreads();
         const int nB = s_nB;
 
         // ---- phase B: variable nodes / write-out of stopped frames -------
         const unsigned totalB = (unsigned)nB * (unsigned)p.vn_tiles;
-        for (unsigned it = blockIdx.x; it < totalB; it += gridDim.x) {
+        for (unsigned it = lb; it < totalB; it += gsize) {
+            // phase B walks the slots in the reverse order of phase A, so it starts
+            // on the frames whose messages phase A wrote last (still in L2)
             const unsigned si = it / (unsigned)p.vn_tiles;
-            const int e = listB[si];
-            const int s = e & 0xffff;
+            const int e = listB[nB - 1 - (int)si];
+            const int l = e & 0xffff;
             const int tile = (int)(it - si * (unsigned)p.vn_tiles);
             if ((e >> 16) == 0)
-                vn_tile<T>(p, code, s, st_frame[s], st_k[s], tile);
+                vn_tile<T>(p, code, s0 + l, st_frame[l], st_k[l], tile);
             else
-                final_tile<T>(p, code, s, st_frame[s], tile);
+                final_tile<T>(p, code, s0 + l, st_frame[l], tile);
         }
-        if (blockIdx.x == 0)
-            for (int s = threadIdx.x; s < p.slots; s += kThreads) p.unsat[(par ^ 1) * p.slots + s] = 0;
-        __syncthreads();
+        if (lb == 0)
+            for (int l = threadIdx.x; l < SG; l += kThreads) p.unsat[(par ^ 1) * p.slots + s0 + l] = 0;
+        if (!grid_sync(bar, err, gsize, 2u * step + 2u, p.timeout_ns)) return;
+        // new state: continuing frames did one more iteration; stopped ones are
+        // replaced by the frame the group's first CTA took from the queue
         for (int i = threadIdx.x; i < nB; i += kThreads) {
             const int e = listB[i];
-            const int s = e & 0xffff;
+            const int l = e & 0xffff;
             if ((e >> 16) == 0) {
-                st_k[s] += 1;
+                st_k[l] += 1;
             } else {
-                st_frame[s] = st_new[s];
-                st_k[s] = 0;
-                st_qprev[s] = 0.0;
+                st_frame[l] = ld_volatile(&p.new_frame[s0 + l]);
+                st_k[l] = 0;
+                st_qprev[l] = 0.0;
             }
         }
-        if (!grid_sync(p.ctrl, p.timeout_ns)) return;
+        __syncthreads();
     }
 }
 

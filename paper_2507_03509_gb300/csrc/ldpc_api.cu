@@ -108,20 +108,21 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Device layout of one decode's state.
 struct Layout {
-    size_t c2v, app, qpart, q0part, qval, q0val, unsat, sbits, total;
+    size_t c2v, app, qpart, q0part, qval, q0val, unsat, sbits, new_frame, total;
 };
 
-Layout make_layout(const ldpc_graph* g, int slots, size_t elem, int frames, int swords) {
+Layout make_layout(const ldpc_graph* g, int slots, size_t elem, int frames, int swords, int vn_tiles) {
     Layout L{};
     size_t o = 0;
     L.c2v = o;    o = align_up(o + (size_t)slots * (size_t)g->E * elem, 256);
     L.app = o;    o = align_up(o + (size_t)slots * (size_t)g->n * elem, 256);
-    L.qpart = o;  o = align_up(o + (size_t)slots * g->vn_tiles * kWarps * sizeof(double), 256);
-    L.q0part = o; o = align_up(o + (size_t)slots * g->vn_tiles * kWarps * sizeof(double), 256);
+    L.qpart = o;  o = align_up(o + (size_t)slots * vn_tiles * kWarps * sizeof(double), 256);
+    L.q0part = o; o = align_up(o + (size_t)slots * vn_tiles * kWarps * sizeof(double), 256);
     L.qval = o;   o = align_up(o + (size_t)slots * sizeof(double), 256);
     L.q0val = o;  o = align_up(o + (size_t)slots * sizeof(double), 256);
     L.unsat = o;  o = align_up(o + 2 * (size_t)slots * sizeof(int), 256);
     L.sbits = o;  o = align_up(o + (size_t)frames * swords * sizeof(unsigned), 256);
+    L.new_frame = o; o = align_up(o + (size_t)slots * sizeof(int), 256);
     L.total = o;
     return L;
 }
@@ -129,7 +130,7 @@ Layout make_layout(const ldpc_graph* g, int slots, size_t elem, int frames, int 
 ldpc_status ensure_workspace(ldpc_graph* g, size_t bytes) {
     Workspace& ws = g->ws;
     if (!ws.ctrl) {
-        LDPC_TRY(cudaMalloc(&ws.ctrl, sizeof(Ctrl)));
+        LDPC_TRY(cudaMalloc(&ws.ctrl, kMaxGroups * sizeof(Ctrl)));
         LDPC_TRY(cudaHostAlloc(&ws.host_err, sizeof(int), cudaHostAllocDefault));
         LDPC_TRY(cudaHostAlloc(&ws.host_iters, sizeof(unsigned long long), cudaHostAllocDefault));
         for (auto& e : ws.ev) LDPC_TRY(cudaEventCreate(&e));
@@ -170,27 +171,55 @@ ldpc_status launch_decode(ldpc_graph* g, const Code& code, int frames, const flo
                           uint8_t* flags_out, int32_t* iters_out, const ldpc_decode_opts& o,
                           cudaStream_t stream) {
     const int swords = (g->m + 31) / 32;
-    int slots = o.max_active_frames > 0 ? o.max_active_frames : frames;
-    slots = std::min(std::min(slots, frames), kMaxSlots);
-    const Layout L = make_layout(g, slots, sizeof(T), frames, swords);
-    ldpc_status st = ensure_workspace(g, L.total);
-    if (st != LDPC_OK) return st;
-    Workspace& ws = g->ws;
-    char* base = (char*)ws.buf;
-
     auto kernel = bp_decode_kernel<T, Code>;
-    const size_t smem = (size_t)slots * (sizeof(double) + 5 * sizeof(int));
     int dev = 0, sms = 0, per_sm = 0, coop = 0;
     LDPC_TRY(cudaGetDevice(&dev));
     LDPC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     LDPC_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     if (!coop) return LDPC_ERR_CUDA;
-    if (smem > 48 * 1024)
-        LDPC_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    LDPC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem));
+    // occupancy with the largest slot table we may use (24 bytes of shared memory per slot)
+    LDPC_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSlots * 24));
+    LDPC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, kMaxSlots * 24));
     if (per_sm < 1) return LDPC_ERR_CUDA;
-    int grid = per_sm * sms;
+    int grid = std::min(per_sm * sms, kMaxGrid);
     if (o.grid_ctas > 0) grid = std::min(grid, o.grid_ctas);
+    // groups and slots: by default one group per resident CTA per SM (at most
+    // one per frame) and every frame in a slot (measured best at n = 1e6)
+    int groups = o.groups > 0 ? o.groups : per_sm;
+    int want_slots = o.max_active_frames > 0 ? o.max_active_frames : frames;
+    want_slots = std::min(std::min(want_slots, frames), kMaxSlots);
+    groups = std::max(1, std::min(std::min(groups, want_slots), std::min(grid, kMaxGroups)));
+    const int slots_per_group = (want_slots + groups - 1) / groups;
+    const int slots = groups * slots_per_group;
+    grid = (grid / groups) * groups;
+    const size_t smem = (size_t)slots_per_group * (sizeof(double) + 4 * sizeof(int));
+    // QC item sizes: as few, as large items as fill whole rounds of the group's CTAs
+    int cn_chunk = kQcCnChunk, vn_chunk = kQcVnChunk, cn_tiles = g->cn_tiles, vn_tiles = g->vn_tiles;
+    if (g->kind == 1) {
+        const int gsize = grid / groups;
+        auto pick = [&](int rows, const int* cand, int ncand, int* chunk, int* tiles) {
+            long long best = -1;
+            for (int c = 0; c < ncand; ++c) {
+                const long long items = (long long)rows * ((g->Z + cand[c] - 1) / cand[c]);
+                const long long rounds = (items * slots_per_group + gsize - 1) / gsize;
+                const long long cost = rounds * (cand[c] + 256);
+                if (best < 0 || cost < best) {
+                    best = cost;
+                    *chunk = cand[c];
+                    *tiles = (int)items;
+                }
+            }
+        };
+        static const int cn_cand[] = {512, 1024, 2048, 4096};
+        static const int vn_cand[] = {1024, 2048, 4096, 8192};
+        pick(g->mb, cn_cand, 4, &cn_chunk, &cn_tiles);
+        pick(g->nb, vn_cand, 4, &vn_chunk, &vn_tiles);
+    }
+    const Layout L = make_layout(g, slots, sizeof(T), frames, swords, vn_tiles);
+    ldpc_status st = ensure_workspace(g, L.total);
+    if (st != LDPC_OK) return st;
+    Workspace& ws = g->ws;
+    char* base = (char*)ws.buf;
 
     Params<T> p{};
     p.m = g->m;
@@ -216,18 +245,30 @@ ldpc_status launch_decode(ldpc_graph* g, const Code& code, int frames, const flo
     p.q0val = (double*)(base + L.q0val);
     p.unsat = (int*)(base + L.unsat);
     p.ctrl = ws.ctrl;
-    p.cn_tiles = g->cn_tiles;
-    p.vn_tiles = g->vn_tiles;
+    p.cn_tiles = cn_tiles;
+    p.vn_tiles = vn_tiles;
+    p.cn_chunk = cn_chunk;
+    p.vn_chunk = vn_chunk;
     p.trace_iters = o.trace_iters;
     p.trace_c2v = (T*)o.trace_c2v;
     p.trace_app = (T*)o.trace_app;
     p.trace_q = o.trace_q;
-    p.timeout_ns = kBarrierTimeoutNs;
+    p.timeout_ns = o.barrier_timeout_ms > 0 ? (unsigned long long)o.barrier_timeout_ms * 1000000ull
+                                            : kBarrierTimeoutNs;
     p.vec4 = (g->kind == 1 && (g->Z % 4) == 0 && ((uintptr_t)llr % 16) == 0) ? 1 : 0;
+    p.bar_extra = o.test_unreachable_barrier ? 1u : 0u;
+    p.groups = groups;
+    p.slots_per_group = slots_per_group;
+    p.new_frame = (int*)(base + L.new_frame);
 
     const bool timing = o.stats != nullptr;
     if (timing) LDPC_TRY(cudaEventRecord(ws.ev[0], stream));
-    LDPC_TRY(cudaMemsetAsync(ws.ctrl, 0, sizeof(Ctrl), stream));
+    {
+        // group barriers cleared; the queue of waiting frames starts after the first `slots`
+        Ctrl c0[kMaxGroups] = {};
+        c0[0].next_frame = std::min(slots, frames);
+        LDPC_TRY(cudaMemcpyAsync(ws.ctrl, c0, (size_t)groups * sizeof(Ctrl), cudaMemcpyHostToDevice, stream));
+    }
     LDPC_TRY(cudaMemsetAsync(p.unsat, 0, 2 * (size_t)slots * sizeof(int), stream));
     {
         const long long warps = (long long)frames * swords;
@@ -238,8 +279,10 @@ ldpc_status launch_decode(ldpc_graph* g, const Code& code, int frames, const flo
         LDPC_TRY(cudaGetLastError());
     }
     if (timing) LDPC_TRY(cudaEventRecord(ws.ev[1], stream));
-    void* args[] = {(void*)&p, (void*)&code};
-    LDPC_TRY(cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(kThreads), args, smem, stream));
+    {
+        void* args[] = {(void*)&p, (void*)&code};
+        LDPC_TRY(cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(kThreads), args, smem, stream));
+    }
     if (timing) LDPC_TRY(cudaEventRecord(ws.ev[2], stream));
     LDPC_TRY(cudaMemcpyAsync(ws.host_err, &ws.ctrl->err, sizeof(int), cudaMemcpyDeviceToHost, stream));
     LDPC_TRY(cudaMemcpyAsync(ws.host_iters, &ws.ctrl->frame_iters, sizeof(unsigned long long),
@@ -271,7 +314,8 @@ ldpc_status check_decode_args(const ldpc_graph* graph, int32_t frames, const voi
     if (frames > 0 && (!llr || !syndrome || !bits_out || !flags_out || !iters_out)) return LDPC_ERR_INVALID_ARG;
     if (o.vnr_first_iter < 1 || !(o.clamp > 0.0f) || !std::isfinite(o.clamp)) return LDPC_ERR_INVALID_ARG;
     if (o.fp64 != 0 && o.fp64 != 1) return LDPC_ERR_INVALID_ARG;
-    if (o.max_active_frames < 0 || o.max_active_frames > kMaxSlots || o.grid_ctas < 0 || o.trace_iters < 0)
+    if (o.max_active_frames < 0 || o.max_active_frames > kMaxSlots || o.grid_ctas < 0 || o.trace_iters < 0 ||
+        o.barrier_timeout_ms < 0 || o.groups < 0 || o.groups > kMaxGroups)
         return LDPC_ERR_INVALID_ARG;
     if ((long long)frames * graph->n > (1LL << 40)) return LDPC_ERR_INVALID_ARG;
     return LDPC_OK;
@@ -538,7 +582,7 @@ ldpc_status noalloc_scratch(int dev, char** out) {
 }
 
 struct NoallocLayout {
-    size_t ctrl, tables, sbits, unsat, qval, q0val, qpart, q0part, c2v, app, total;
+    size_t ctrl, tables, sbits, unsat, qval, q0val, qpart, q0part, new_frame, c2v, app, total;
     int slots;
 };
 
@@ -555,6 +599,7 @@ NoallocLayout noalloc_layout(size_t table_ints, int64_t n, int64_t E, int vn_til
     L.q0val = o;  o = align_up(o + (size_t)slots * sizeof(double), 256);
     L.qpart = o;  o = align_up(o + (size_t)slots * vn_tiles * kWarps * sizeof(double), 256);
     L.q0part = o; o = align_up(o + (size_t)slots * vn_tiles * kWarps * sizeof(double), 256);
+    L.new_frame = o; o = align_up(o + (size_t)slots * sizeof(int), 256);
     L.c2v = o;    o = align_up(o + (size_t)slots * (size_t)E * sizeof(float), 256);
     L.app = o;    o = align_up(o + (size_t)slots * (size_t)n * sizeof(float), 256);
     L.total = o;
@@ -630,19 +675,20 @@ extern "C" ldpc_status ldpc_decode_qc_noalloc(int32_t mb, int32_t nb, int32_t Z,
     LDPC_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     if (!coop) return LDPC_ERR_CUDA;
     auto kernel = bp_decode_kernel<float, QcDev>;
-    const size_t smem = (size_t)slots * (sizeof(double) + 5 * sizeof(int));
-    if (smem > 48 * 1024)
-        LDPC_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    LDPC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem));
+    const size_t smem = (size_t)slots * (sizeof(double) + 4 * sizeof(int));
+    LDPC_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSlots * 24));
+    LDPC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, kMaxSlots * 24));
     if (per_sm < 1) return LDPC_ERR_CUDA;
-    const int grid = per_sm * sms;
+    const int grid = std::min(per_sm * sms, kMaxGrid);
 
     int* dtab = (int*)(base + L.tables);
     LDPC_TRY(cudaMemcpyAsync(dtab, table.data(), table.size() * sizeof(int), cudaMemcpyHostToDevice, stream));
     const QcDev code{mb, nb, Z, nblk, dtab + off[0], dtab + off[1], dtab + off[2], dtab + off[3], dtab + off[4],
                      dtab + off[5]};
     Ctrl* ctrl = (Ctrl*)(base + L.ctrl);
-    LDPC_TRY(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), stream));
+    Ctrl c0{};
+    c0.next_frame = std::min(slots, frames);  // the queue of waiting frames starts after the slots
+    LDPC_TRY(cudaMemcpyAsync(ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, stream));
     LDPC_TRY(cudaMemsetAsync(base + L.unsat, 0, 2 * (size_t)slots * sizeof(int), stream));
 
     Params<float> p{};
@@ -674,6 +720,11 @@ extern "C" ldpc_status ldpc_decode_qc_noalloc(int32_t mb, int32_t nb, int32_t Z,
     p.trace_iters = 0;
     p.timeout_ns = kBarrierTimeoutNs;
     p.vec4 = ((Z % 4) == 0 && ((uintptr_t)llr % 16) == 0) ? 1 : 0;
+    p.groups = 1;
+    p.slots_per_group = slots;
+    p.cn_chunk = kQcCnChunk;
+    p.vn_chunk = kQcVnChunk;
+    p.new_frame = (int*)(base + L.new_frame);
     {
         const long long warps = (long long)frames * swords;
         long long blocks = (warps * 32 + 255) / 256;

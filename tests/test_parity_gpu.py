@@ -145,21 +145,23 @@ def test_noise_free_limit(ldpc, csr1, qc_small):
         assert (got["iters"] == 1).all() and (got["flags"] == 1).all() and (got["bits"] == x).all()
 
 
-def test_concurrency_and_grid_do_not_change_results(ldpc, csr1, qc_small):
-    """Frames decoded through fewer slots (queue + refill) or on fewer CTAs
-    give bit-identical results and traces."""
+def test_groups_concurrency_and_grid_do_not_change_results(ldpc, csr1, qc_small):
+    """Any number of CTA groups, slots (queue + refill) and CTAs gives
+    bit-identical results and traces."""
     for code, wl in ((csr1, 1), (qc_small, 2)):
         g = ldpc.Graph.from_code(code)
         fr = gen.workload_frames(wl, code, frames=9)
-        ref = gpu_decode(ldpc, g, fr.llr, fr.syndrome, 40, "pce_vnr", trace_iters=3)
-        for slots, ctas in ((3, 0), (1, 0), (9, 1), (4, 7)):
+        ref = gpu_decode(ldpc, g, fr.llr, fr.syndrome, 40, "pce_vnr", trace_iters=3, groups=1,
+                         max_active_frames=9)
+        for slots, ctas, groups in ((0, 0, 0), (3, 0, 1), (3, 0, 3), (1, 0, 0), (9, 1, 0), (9, 0, 4),
+                                    (4, 7, 0), (8, 0, 2), (0, 0, 8)):
             got = gpu_decode(ldpc, g, fr.llr, fr.syndrome, 40, "pce_vnr", trace_iters=3,
-                             max_active_frames=slots, grid_ctas=ctas)
+                             max_active_frames=slots, grid_ctas=ctas, groups=groups)
             for key in ("bits", "flags", "iters"):
-                assert np.array_equal(got[key], ref[key]), (slots, ctas, key)
+                assert np.array_equal(got[key], ref[key]), (slots, ctas, groups, key)
             for key in ("c2v", "app", "q"):
-                assert np.array_equal(got[key], ref[key], equal_nan=True), (slots, ctas, key)
-            assert got["stats"].active_frames == slots
+                assert np.array_equal(got[key], ref[key], equal_nan=True), (slots, ctas, groups, key)
+            assert got["stats"].active_frames >= max(1, slots)
 
 
 def test_degenerate_graph_shapes(ldpc, oracle):
@@ -242,3 +244,27 @@ def test_host_entry_point_matches_device(ldpc, qc_small):
     dev = gpu_decode(ldpc, g, fr.llr, fr.syndrome, 30, "pce_vnr")
     bits, flags, iters = ldpc.decode_host(g, fr.llr, fr.syndrome, 30, "pce_vnr")
     assert (bits == dev["bits"]).all() and (flags == dev["flags"]).all() and (iters == dev["iters"]).all()
+
+
+@pytest.mark.parametrize("groups", [1, 0])
+def test_expired_grid_wait_returns_timeout_and_context_survives(ldpc, qc_small, groups):
+    """Failure detection without a fault: the test hook makes the first
+    barrier of every group wait for one CTA more than the group has (nothing
+    ever arrives), so the waits run out after 200 ms; the call returns
+    LDPC_ERR_TIMEOUT and the next decode on the same context works."""
+    import time
+    import torch
+    g = ldpc.Graph.from_code(qc_small)
+    fr = gen.workload_frames(2, qc_small, frames=3)
+    dev = torch.device("cuda:0")
+    llr = torch.from_numpy(fr.llr).to(dev)
+    syn = torch.from_numpy(fr.syndrome).to(dev)
+    t0 = time.perf_counter()
+    with pytest.raises(ldpc.LdpcError) as ei:
+        ldpc.decode(g, llr, syn, 20, "pce_vnr", barrier_timeout_ms=200, test_unreachable_barrier=True,
+                    groups=groups)
+    assert ei.value.status == ldpc.LDPC_ERR_TIMEOUT
+    assert time.perf_counter() - t0 < 30.0
+    bits, flags, iters = ldpc.decode(g, llr, syn, 20, "pce_vnr", groups=groups)
+    ref = gpu_decode(ldpc, g, fr.llr, fr.syndrome, 20, "pce_vnr")
+    assert (iters.cpu().numpy() == ref["iters"]).all() and (bits.cpu().numpy() == ref["bits"]).all()
