@@ -89,10 +89,11 @@ struct Params {
     int slots;
     T* c2v;                        // [slots][E]
     T* app;                        // [slots][n]
-    double* qpart;                 // [slots][vn_tiles * kWarps] per-warp partial sums
-    double* q0part;                // [slots][vn_tiles * kWarps]
-    double* qval;                  // [slots]
-    double* q0val;                 // [slots]
+    double* qpart;                 // [slots][nqb * kWarps] per-warp partial sums of q
+    double* q0part;                // [slots][nqb * kWarps]
+    int nqb;                       // q-blocks per frame: fixed runs of kQBlock variables
+    double* qval;                  // [slots][kQParts] q^(k) summed over fixed ranges of partials
+    double* q0val;                 // [slots][kQParts] the same for q^(0)
     int* unsat;                    // [2][slots]
     Ctrl* ctrl;
     int cn_tiles, vn_tiles;        // tiles per frame
@@ -285,7 +286,9 @@ __device__ __forceinline__ unsigned syndrome_bit(const unsigned* sb, int row) {
 // old c2v, kModeSynd only tests the syndrome of the current decision.
 // ---------------------------------------------------------------------------
 constexpr int kQcCnChunk = 2048;         // default checks of one base row per item (multiple of 2*kThreads)
-constexpr int kQcVnChunk = 4096;         // default variables of one base column per item (multiple of 4*kThreads)
+constexpr int kQcVnChunk = 4096;         // default variables of one base column per item (multiple of kQBlock)
+constexpr int kQBlock = 4 * kThreads;    // variables per q partial sum (per warp: 128)
+constexpr int kQParts = 8;               // a frame's q is reduced in this many fixed ranges, by different CTAs
 
 template <int D, int MODE, bool SYND, typename T>
 __device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, int s, int f, int i, int t0,
@@ -560,11 +563,14 @@ __device__ void trace_c2v_qc(const Params<T>& p, const QcDev& q, const T* c2v, i
 
 // Quasi-cyclic variable-node item: variables u in [u0, u0 + p.vn_chunk) of
 // base column j.  DV > 0: compile-time column degree; DV == 0: runtime dv.
-// With vec (Z % 4 == 0, aligned Lch) each thread handles groups of four
-// consecutive variables with 16-byte loads and stores.
+// The item is walked in q-blocks of kQBlock variables (u0 is a multiple of
+// kQBlock); in each, thread t handles variables 4t .. 4t+3, so q's partial
+// sums -- one per q-block and warp, at a fixed position -- do not depend on
+// the item size or on the load path.  With vec (Z % 4 == 0, aligned Lch) the
+// four variables move as 16-byte loads and stores.
 template <int DV, typename T>
-__device__ __forceinline__ void qc_vn_cols(const Params<T>& p, const QcDev& q, int s, int f, int k, int tile,
-                                           int j, int u0, int cb0, int dv) {
+__device__ __forceinline__ void qc_vn_cols(const Params<T>& p, const QcDev& q, int s, int f, int k, int j, int u0,
+                                           int cb0, int dv) {
     constexpr bool kFixed = DV > 0;
     const int Z = q.Z;
     const int u_end = min(u0 + p.vn_chunk, Z);
@@ -580,71 +586,76 @@ __device__ __forceinline__ void qc_vn_cols(const Params<T>& p, const QcDev& q, i
 #pragma unroll
         for (int b = 0; b < DV; ++b) cb[b] = c2v + __ldg(q.col_blk + cb0 + b) * Z;
     }
-    T acc = T(0), acc0 = T(0);
     bool vec = false;
     if constexpr (sizeof(T) == 4) vec = p.vec4 != 0;
-    if (vec) {
-        for (int u = u0 + 4 * (int)threadIdx.x; u < u_end; u += 4 * kThreads) {
-            const float4 L = __ldg(reinterpret_cast<const float4*>(llr + u));
-            float4 sum = L;
-            if constexpr (kFixed) {
-                float4 m[DV];
+    const int qb_per_col = (Z + kQBlock - 1) / kQBlock;
+    for (int ub = u0; ub < u_end; ub += kQBlock) {
+        const int u = ub + 4 * (int)threadIdx.x;
+        T acc = T(0), acc0 = T(0);
+        if (u < u_end) {
+            T L[4], sum[4];
+            if (vec) {
+                const float4 l4 = __ldg(reinterpret_cast<const float4*>(llr + u));
+                float4 s4 = l4;
+                if constexpr (kFixed) {
+                    float4 m[DV];
 #pragma unroll
-                for (int b = 0; b < DV; ++b) m[b] = *reinterpret_cast<const float4*>(cb[b] + u);
+                    for (int b = 0; b < DV; ++b) m[b] = *reinterpret_cast<const float4*>(cb[b] + u);
 #pragma unroll
-                for (int b = 0; b < DV; ++b) {
-                    sum.x += m[b].x;
-                    sum.y += m[b].y;
-                    sum.z += m[b].z;
-                    sum.w += m[b].w;
+                    for (int b = 0; b < DV; ++b) {
+                        s4.x += m[b].x;
+                        s4.y += m[b].y;
+                        s4.z += m[b].z;
+                        s4.w += m[b].w;
+                    }
+                } else {
+                    for (int b = 0; b < nd; ++b) {
+                        const float4 m =
+                            *reinterpret_cast<const float4*>(c2v + __ldg(q.col_blk + cb0 + b) * Z + u);
+                        s4.x += m.x;
+                        s4.y += m.y;
+                        s4.z += m.z;
+                        s4.w += m.w;
+                    }
                 }
+                *reinterpret_cast<float4*>(reinterpret_cast<float*>(app) + u) = s4;
+                L[0] = T(l4.x), L[1] = T(l4.y), L[2] = T(l4.z), L[3] = T(l4.w);
+                sum[0] = T(s4.x), sum[1] = T(s4.y), sum[2] = T(s4.z), sum[3] = T(s4.w);
             } else {
-                for (int b = 0; b < nd; ++b) {
-                    const float4 m = *reinterpret_cast<const float4*>(c2v + __ldg(q.col_blk + cb0 + b) * Z + u);
-                    sum.x += m.x;
-                    sum.y += m.y;
-                    sum.z += m.z;
-                    sum.w += m.w;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    if (u + e < u_end) {
+                        L[e] = T(__ldg(llr + u + e));
+                        T t = L[e];
+                        if constexpr (kFixed) {
+#pragma unroll
+                            for (int b = 0; b < DV; ++b) t += cb[b][u + e];
+                        } else {
+                            for (int b = 0; b < nd; ++b) t += c2v[__ldg(q.col_blk + cb0 + b) * Z + u + e];
+                        }
+                        sum[e] = t;
+                        app[u + e] = t;
+                    } else {
+                        L[e] = T(0);
+                        sum[e] = T(0);
+                    }
                 }
             }
-            *reinterpret_cast<float4*>(reinterpret_cast<float*>(app) + u) = sum;
             if (inV) {
-                acc += T((fabsf(sum.x) + fabsf(sum.y)) + (fabsf(sum.z) + fabsf(sum.w)));
-                if (want_q0) acc0 += T((fabsf(L.x) + fabsf(L.y)) + (fabsf(L.z) + fabsf(L.w)));
+                acc = (absm(sum[0]) + absm(sum[1])) + (absm(sum[2]) + absm(sum[3]));
+                acc0 = (absm(L[0]) + absm(L[1])) + (absm(L[2]) + absm(L[3]));
             }
             if (tracing) {
-                const float sv[4] = {sum.x, sum.y, sum.z, sum.w};
-                for (int e = 0; e < 4; ++e) {
-                    if (p.trace_app)
-                        p.trace_app[((size_t)k * p.frames + f) * (size_t)p.n + j * Z + u + e] = T(sv[e]);
+                for (int e = 0; e < 4 && u + e < u_end; ++e) {
+                    if (p.trace_app) p.trace_app[((size_t)k * p.frames + f) * (size_t)p.n + j * Z + u + e] = sum[e];
                     if (p.trace_c2v) trace_c2v_qc(p, q, c2v, f, k, u + e, cb0, nd);
                 }
             }
         }
-    } else {
-        for (int u = u0 + (int)threadIdx.x; u < u_end; u += kThreads) {
-            const T L = T(__ldg(llr + u));
-            T sum = L;
-            if constexpr (kFixed) {
-#pragma unroll
-                for (int b = 0; b < DV; ++b) sum += cb[b][u];
-            } else {
-                for (int b = 0; b < nd; ++b) sum += c2v[__ldg(q.col_blk + cb0 + b) * Z + u];
-            }
-            app[u] = sum;
-            if (inV) {
-                acc += absm(sum);
-                acc0 += absm(L);
-            }
-            if (tracing) {
-                if (p.trace_app) p.trace_app[((size_t)k * p.frames + f) * (size_t)p.n + j * Z + u] = sum;
-                if (p.trace_c2v) trace_c2v_qc(p, q, c2v, f, k, u, cb0, nd);
-            }
-        }
+        const size_t part = ((size_t)s * p.nqb + (size_t)j * qb_per_col + ub / kQBlock) * kWarps;
+        warp_sum_store(acc, p.qpart + part);
+        if (want_q0) warp_sum_store(acc0, p.q0part + part);
     }
-    const size_t part = ((size_t)s * p.vn_tiles + tile) * kWarps;
-    warp_sum_store(acc, p.qpart + part);
-    if (want_q0) warp_sum_store(acc0, p.q0part + part);
 }
 
 template <typename T>
@@ -655,11 +666,11 @@ __device__ __forceinline__ void vn_tile(const Params<T>& p, const QcDev& q, int 
     const int cb0 = __ldg(q.col_ptr + j);
     const int dv = __ldg(q.col_ptr + j + 1) - cb0;
     switch (dv) {
-        case 1: qc_vn_cols<1, T>(p, q, s, f, k, tile, j, u0, cb0, dv); break;
-        case 2: qc_vn_cols<2, T>(p, q, s, f, k, tile, j, u0, cb0, dv); break;
-        case 3: qc_vn_cols<3, T>(p, q, s, f, k, tile, j, u0, cb0, dv); break;
-        case 4: qc_vn_cols<4, T>(p, q, s, f, k, tile, j, u0, cb0, dv); break;
-        default: qc_vn_cols<0, T>(p, q, s, f, k, tile, j, u0, cb0, dv); break;
+        case 1: qc_vn_cols<1, T>(p, q, s, f, k, j, u0, cb0, dv); break;
+        case 2: qc_vn_cols<2, T>(p, q, s, f, k, j, u0, cb0, dv); break;
+        case 3: qc_vn_cols<3, T>(p, q, s, f, k, j, u0, cb0, dv); break;
+        case 4: qc_vn_cols<4, T>(p, q, s, f, k, j, u0, cb0, dv); break;
+        default: qc_vn_cols<0, T>(p, q, s, f, k, j, u0, cb0, dv); break;
     }
 }
 
@@ -692,7 +703,7 @@ __device__ __forceinline__ void vn_tile(const Params<T>& p, const CsrDev& g, int
             }
         }
     }
-    const size_t part = ((size_t)s * p.vn_tiles + tile) * kWarps;
+    const size_t part = ((size_t)s * p.nqb + tile) * kWarps;
     warp_sum_store(acc, p.qpart + part);
     if (want_q0) warp_sum_store(acc0, p.q0part + part);
 }
@@ -822,23 +833,28 @@ __global__ void __launch_bounds__(kThreads, 4) bp_decode_kernel(Params<T> p, Cod
             if (want_synd && __any_sync(0xffffffffu, unsat) && lane == 0)
                 atomicOr(&p.unsat[par * p.slots + s], 1);
         }
-        // q^(k) of every running frame that has done an iteration, by the CTAs
-        // at the end of the group, which get one item fewer when the items do
-        // not divide evenly
-        for (int i = gsize - 1 - lb; i >= 0 && i < nA; i += gsize) {
-            const int l = listA[i];
-            const int s = s0 + l;
-            const int k = st_k[l];
-            if (k < 1) continue;
-            const int np = p.vn_tiles * kWarps;
-            const double qv = block_sum_fixed(p.qpart + (size_t)s * np, np, s_red);
-            const bool with_q0 = k == 1 && p.vnr_first_iter <= 1;
-            double q0 = 0.0;
-            if (with_q0) q0 = block_sum_fixed(p.q0part + (size_t)s * np, np, s_red);
-            if (threadIdx.x == 0) {
-                p.qval[s] = qv;
-                if (with_q0) p.q0val[s] = q0;
-                if (k <= p.trace_iters && p.trace_q) p.trace_q[(long long)(k - 1) * p.frames + st_frame[l]] = qv;
+        // q^(k) of every running frame that has done an iteration: the partials
+        // are summed in kQParts fixed ranges, each by its own CTA (counted from
+        // the end of the group, where CTAs get one item fewer when the items
+        // do not divide evenly); the decision adds the kQParts sums in order
+        {
+            const int np = p.nqb * kWarps;
+            const int per = (np + kQParts - 1) / kQParts;
+            for (int w = gsize - 1 - lb; w >= 0 && w < nA * kQParts; w += gsize) {
+                const int l = listA[w / kQParts];
+                const int r = w % kQParts;
+                const int s = s0 + l;
+                const int k = st_k[l];
+                if (k < 1) continue;
+                const int lo = r * per, cnt = max(0, min(np, lo + per) - lo);
+                const double qv = block_sum_fixed(p.qpart + (size_t)s * np + lo, cnt, s_red);
+                const bool with_q0 = k == 1 && p.vnr_first_iter <= 1;
+                double q0 = 0.0;
+                if (with_q0) q0 = block_sum_fixed(p.q0part + (size_t)s * np + lo, cnt, s_red);
+                if (threadIdx.x == 0) {
+                    p.qval[(size_t)s * kQParts + r] = qv;
+                    if (with_q0) p.q0val[(size_t)s * kQParts + r] = q0;
+                }
             }
         }
         if (!grid_sync(bar, err, gsize, 2u * step + 1u, p.timeout_ns, step == 0 ? p.bar_extra : 0u)) return;
@@ -857,9 +873,22 @@ __global__ void __launch_bounds__(kThreads, 4) bp_decode_kernel(Params<T> p, Cod
                         act = 0;
                     } else {
                         const bool sat = ld_volatile(&p.unsat[par * p.slots + s]) == 0;
-                        const double qv = ld_volatile(&p.qval[s]);
-                        const double qprev =
-                            (k == 1 && p.vnr_first_iter <= 1) ? ld_volatile(&p.q0val[s]) : st_qprev[l];
+                        double qr[kQParts], q0r[kQParts];
+                        const bool with_q0 = k == 1 && p.vnr_first_iter <= 1;
+#pragma unroll
+                        for (int r = 0; r < kQParts; ++r) {
+                            qr[r] = ld_volatile(&p.qval[(size_t)s * kQParts + r]);
+                            q0r[r] = with_q0 ? ld_volatile(&p.q0val[(size_t)s * kQParts + r]) : 0.0;
+                        }
+                        double qv = 0.0, q0 = 0.0;
+#pragma unroll
+                        for (int r = 0; r < kQParts; ++r) {
+                            qv += qr[r];
+                            q0 += q0r[r];
+                        }
+                        if (lb == 0 && k <= p.trace_iters && p.trace_q)
+                            p.trace_q[(long long)(k - 1) * p.frames + f] = qv;
+                        const double qprev = with_q0 ? q0 : st_qprev[l];
                         const bool succ = p.rule != kRuleNone && sat;
                         const bool abort_ = !succ && p.rule == kRulePceVnr && k >= p.vnr_first_iter && qv < qprev;
                         const bool end = k >= p.max_iter;

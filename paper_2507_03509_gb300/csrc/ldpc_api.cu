@@ -49,6 +49,7 @@ struct ldpc_graph {
     QcDev qc{};
     CsrDev csr{};
     int vn_tiles = 0, cn_tiles = 0;
+    std::vector<int> row_deg, col_deg;  // QC base-matrix row and column weights
     Workspace ws;
 };
 
@@ -111,15 +112,15 @@ struct Layout {
     size_t c2v, app, qpart, q0part, qval, q0val, unsat, sbits, new_frame, total;
 };
 
-Layout make_layout(const ldpc_graph* g, int slots, size_t elem, int frames, int swords, int vn_tiles) {
+Layout make_layout(const ldpc_graph* g, int slots, size_t elem, int frames, int swords, int nqb) {
     Layout L{};
     size_t o = 0;
     L.c2v = o;    o = align_up(o + (size_t)slots * (size_t)g->E * elem, 256);
     L.app = o;    o = align_up(o + (size_t)slots * (size_t)g->n * elem, 256);
-    L.qpart = o;  o = align_up(o + (size_t)slots * vn_tiles * kWarps * sizeof(double), 256);
-    L.q0part = o; o = align_up(o + (size_t)slots * vn_tiles * kWarps * sizeof(double), 256);
-    L.qval = o;   o = align_up(o + (size_t)slots * sizeof(double), 256);
-    L.q0val = o;  o = align_up(o + (size_t)slots * sizeof(double), 256);
+    L.qpart = o;  o = align_up(o + (size_t)slots * nqb * kWarps * sizeof(double), 256);
+    L.q0part = o; o = align_up(o + (size_t)slots * nqb * kWarps * sizeof(double), 256);
+    L.qval = o;   o = align_up(o + (size_t)slots * kQParts * sizeof(double), 256);
+    L.q0val = o;  o = align_up(o + (size_t)slots * kQParts * sizeof(double), 256);
     L.unsat = o;  o = align_up(o + 2 * (size_t)slots * sizeof(int), 256);
     L.sbits = o;  o = align_up(o + (size_t)frames * swords * sizeof(unsigned), 256);
     L.new_frame = o; o = align_up(o + (size_t)slots * sizeof(int), 256);
@@ -193,29 +194,41 @@ ldpc_status launch_decode(ldpc_graph* g, const Code& code, int frames, const flo
     const int slots = groups * slots_per_group;
     grid = (grid / groups) * groups;
     const size_t smem = (size_t)slots_per_group * (sizeof(double) + 4 * sizeof(int));
-    // QC item sizes: as few, as large items as fill whole rounds of the group's CTAs
+    // QC item sizes: simulate the static assignment (item it goes to CTA it mod
+    // gsize) of one step of the group's slots and take the size whose busiest
+    // CTA has the least work (checks or variables times (degree + 1), plus a
+    // fixed cost per item)
     int cn_chunk = kQcCnChunk, vn_chunk = kQcVnChunk, cn_tiles = g->cn_tiles, vn_tiles = g->vn_tiles;
     if (g->kind == 1) {
         const int gsize = grid / groups;
-        auto pick = [&](int rows, const int* cand, int ncand, int* chunk, int* tiles) {
+        std::vector<long long> load((size_t)gsize);
+        auto pick = [&](const std::vector<int>& deg, const int* cand, int ncand, int* chunk, int* tiles) {
             long long best = -1;
             for (int c = 0; c < ncand; ++c) {
-                const long long items = (long long)rows * ((g->Z + cand[c] - 1) / cand[c]);
-                const long long rounds = (items * slots_per_group + gsize - 1) / gsize;
-                const long long cost = rounds * (cand[c] + 256);
-                if (best < 0 || cost < best) {
-                    best = cost;
+                const int per = (g->Z + cand[c] - 1) / cand[c];
+                std::fill(load.begin(), load.end(), 0LL);
+                long long it = 0;
+                for (int sl = 0; sl < slots_per_group; ++sl)
+                    for (int r = 0; r < (int)deg.size(); ++r)
+                        for (int q = 0; q < per; ++q, ++it) {
+                            const int len = std::min(cand[c], g->Z - q * cand[c]);
+                            load[(size_t)(it % gsize)] += (long long)len * (deg[r] + 1) + 2048;
+                        }
+                const long long worst = *std::max_element(load.begin(), load.end());
+                if (best < 0 || worst < best) {
+                    best = worst;
                     *chunk = cand[c];
-                    *tiles = (int)items;
+                    *tiles = (int)deg.size() * per;
                 }
             }
         };
         static const int cn_cand[] = {512, 1024, 2048, 4096};
         static const int vn_cand[] = {1024, 2048, 4096, 8192};
-        pick(g->mb, cn_cand, 4, &cn_chunk, &cn_tiles);
-        pick(g->nb, vn_cand, 4, &vn_chunk, &vn_tiles);
+        pick(g->row_deg, cn_cand, 4, &cn_chunk, &cn_tiles);
+        pick(g->col_deg, vn_cand, 4, &vn_chunk, &vn_tiles);
     }
-    const Layout L = make_layout(g, slots, sizeof(T), frames, swords, vn_tiles);
+    const int nqb = g->kind == 1 ? g->nb * ((g->Z + kQBlock - 1) / kQBlock) : g->vn_tiles;
+    const Layout L = make_layout(g, slots, sizeof(T), frames, swords, nqb);
     ldpc_status st = ensure_workspace(g, L.total);
     if (st != LDPC_OK) return st;
     Workspace& ws = g->ws;
@@ -249,6 +262,7 @@ ldpc_status launch_decode(ldpc_graph* g, const Code& code, int frames, const flo
     p.vn_tiles = vn_tiles;
     p.cn_chunk = cn_chunk;
     p.vn_chunk = vn_chunk;
+    p.nqb = nqb;
     p.trace_iters = o.trace_iters;
     p.trace_c2v = (T*)o.trace_c2v;
     p.trace_app = (T*)o.trace_app;
@@ -446,6 +460,9 @@ ldpc_status ldpc_graph_create_qc(int32_t mb, int32_t nb, int32_t Z, const int32_
         return st;
     }
     g->qc = QcDev{mb, nb, Z, nblk, d[0], d[1], d[2], d[3], d[4], d[5]};
+    g->row_deg.resize(mb);
+    for (int i = 0; i < mb; ++i) g->row_deg[i] = row_ptr[i + 1] - row_ptr[i];
+    g->col_deg.assign(col_cnt.begin(), col_cnt.end());
     g->cn_tiles = mb * ((Z + kQcCnChunk - 1) / kQcCnChunk);
     g->vn_tiles = nb * ((Z + kQcVnChunk - 1) / kQcVnChunk);
     *out = g;
@@ -587,7 +604,7 @@ struct NoallocLayout {
 };
 
 // Carve the scratch for `slots` concurrent frames; total > kNoallocBytes means it does not fit.
-NoallocLayout noalloc_layout(size_t table_ints, int64_t n, int64_t E, int vn_tiles, int frames, int swords,
+NoallocLayout noalloc_layout(size_t table_ints, int64_t n, int64_t E, int nqb, int frames, int swords,
                              int slots) {
     NoallocLayout L{};
     size_t o = 0;
@@ -595,10 +612,10 @@ NoallocLayout noalloc_layout(size_t table_ints, int64_t n, int64_t E, int vn_til
     L.tables = o; o = align_up(o + table_ints * sizeof(int), 256);
     L.sbits = o;  o = align_up(o + (size_t)frames * swords * sizeof(unsigned), 256);
     L.unsat = o;  o = align_up(o + 2 * (size_t)slots * sizeof(int), 256);
-    L.qval = o;   o = align_up(o + (size_t)slots * sizeof(double), 256);
-    L.q0val = o;  o = align_up(o + (size_t)slots * sizeof(double), 256);
-    L.qpart = o;  o = align_up(o + (size_t)slots * vn_tiles * kWarps * sizeof(double), 256);
-    L.q0part = o; o = align_up(o + (size_t)slots * vn_tiles * kWarps * sizeof(double), 256);
+    L.qval = o;   o = align_up(o + (size_t)slots * kQParts * sizeof(double), 256);
+    L.q0val = o;  o = align_up(o + (size_t)slots * kQParts * sizeof(double), 256);
+    L.qpart = o;  o = align_up(o + (size_t)slots * nqb * kWarps * sizeof(double), 256);
+    L.q0part = o; o = align_up(o + (size_t)slots * nqb * kWarps * sizeof(double), 256);
     L.new_frame = o; o = align_up(o + (size_t)slots * sizeof(int), 256);
     L.c2v = o;    o = align_up(o + (size_t)slots * (size_t)E * sizeof(float), 256);
     L.app = o;    o = align_up(o + (size_t)slots * (size_t)n * sizeof(float), 256);
@@ -657,12 +674,13 @@ extern "C" ldpc_status ldpc_decode_qc_noalloc(int32_t mb, int32_t nb, int32_t Z,
     const int swords = (m + 31) / 32;
     const int vn_tiles = nb * ((Z + kQcVnChunk - 1) / kQcVnChunk);
     const int cn_tiles = mb * ((Z + kQcCnChunk - 1) / kQcCnChunk);
+    const int nqb = nb * ((Z + kQBlock - 1) / kQBlock);
     if (frames == 0) return LDPC_OK;
     int slots = std::min(frames, kMaxSlots);
-    while (slots > 0 && noalloc_layout(table.size(), n, E, vn_tiles, frames, swords, slots).total > kNoallocBytes)
+    while (slots > 0 && noalloc_layout(table.size(), n, E, nqb, frames, swords, slots).total > kNoallocBytes)
         --slots;
     if (slots < 1) return LDPC_ERR_TOO_LARGE;
-    const NoallocLayout L = noalloc_layout(table.size(), n, E, vn_tiles, frames, swords, slots);
+    const NoallocLayout L = noalloc_layout(table.size(), n, E, nqb, frames, swords, slots);
 
     // ---- device work, all inside the fixed scratch ----
     int dev = 0, sms = 0, per_sm = 0, coop = 0;
@@ -724,6 +742,7 @@ extern "C" ldpc_status ldpc_decode_qc_noalloc(int32_t mb, int32_t nb, int32_t Z,
     p.slots_per_group = slots;
     p.cn_chunk = kQcCnChunk;
     p.vn_chunk = kQcVnChunk;
+    p.nqb = nqb;
     p.new_frame = (int*)(base + L.new_frame);
     {
         const long long warps = (long long)frames * swords;
