@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--max-iter", type=int, default=None, help="override D_max (profiling runs)")
     ap.add_argument("--lean", action="store_true",
                     help="only the timed decodes: no fixed-iteration runs, no host-buffer runs, no CPU baseline")
+    ap.add_argument("--sweep", action="store_true",
+                    help="beta sweep (paper Figs. 1-2): FER, mean iterations and throughput K for PCE-ET with "
+                         "D_max in {100, 250, 500} against PCE+VNR-ET; prints one JSON line per beta")
+    ap.add_argument("--betas", default="0.84,0.85,0.86,0.87,0.88,0.89,0.90,0.92")
     return ap.parse_args()
 
 
@@ -342,6 +346,8 @@ def run_ours(args):
            "h2d_bytes_per_step": int(frames.llr.nbytes + frames.syndrome.nbytes),
            "d2h_bytes_per_step": int(F * code.n + F + 4 * F)}
 
+    et_regime = None if args.lean or world > 1 else et_paper_regime(ldpc, dev)
+
     if cpu_pending:
         d_mean_o = oracle_iters_mean(wl["name"], "pce_vnr")
         src = "oracle's own decisions on these frames"
@@ -367,6 +373,7 @@ def run_ours(args):
         "et_speedup": None if not comp else {
             "vs_pce": comp["pce"]["ms_per_step"] / (main["ms"] / args.steps),
             "vs_none": comp["none"]["ms_per_step"] / (main["ms"] / args.steps)},
+        "et_paper_regime": et_regime,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src,
                      "traffic": (traffic_fi * per_launch_fi) if traffic_fi else None,
@@ -383,10 +390,88 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def et_paper_regime(ldpc, dev, betas=(0.875, 0.8765), frames=64):
+    """Early termination where the paper measures it: the (3,6)-regular QC code
+    inside its waterfall; K ratios of PCE+VNR against the D_max baselines."""
+    import torch
+    number = 6
+    code = gen.workload_code(number)
+    graph = ldpc.Graph.from_code(code)
+    out = {"workload": gen.WORKLOADS[number]["name"], "frames": frames, "points": []}
+    for beta in betas:
+        fr = gen.workload_frames(number, code, frames=frames, beta=beta)
+        llr = torch.from_numpy(fr.llr).to(dev)
+        syn = torch.from_numpy(fr.syndrome).to(dev)
+        pt = {"beta": beta}
+        for rule, dmax in (("pce", 250), ("pce", 500), ("pce_vnr", 500)):
+            st = ldpc.ldpc_decode_stats()
+            bits, flags, iters = ldpc.decode(graph, llr, syn, dmax, rule, stats=st)
+            ok = ((flags.cpu().numpy() & 1) > 0) & (bits.cpu().numpy() == fr.x).all(1)
+            fer = float(1 - ok.mean())
+            d = float(iters.float().mean().item())
+            pt[f"{rule}_{dmax}"] = {"fer": fer, "d_mean": d, "ms": st.total_ms,
+                                    "K": code.n * code.rate * (1 - fer) / d}
+        kv = pt["pce_vnr_500"]["K"]
+        pt["K_vnr_over_pce500"] = kv / pt["pce_500"]["K"] if pt["pce_500"]["K"] > 0 else None
+        pt["K_vnr_over_pce250"] = kv / pt["pce_250"]["K"] if pt["pce_250"]["K"] > 0 else None
+        out["points"].append(pt)
+    graph.close()
+    return out
+
+
+def run_sweep(args):
+    """FER, mean iterations D and throughput against beta for the paper's
+    D_max baselines (PCE-ET on) and for PCE+VNR-ET, on the same frames.
+
+    K = N R (1 - FER) / D is the paper's Eq. 2 throughput in bits per iteration
+    latency; goodput is the measured rate of correctly decoded information bits."""
+    import torch
+    from paper_2507_03509_gb300 import build
+    build.build()
+    from paper_2507_03509_gb300 import ldpc
+    dev = torch.device("cuda", 0)
+    number = args.workload if args.workload != 2 else 6
+    wl = gen.WORKLOADS[number]
+    code = gen.workload_code(number)
+    graph = ldpc.Graph.from_code(code)
+    F = args.frames or wl["frames"]
+    runs = [("pce", 100), ("pce", 250), ("pce", 500), ("pce_vnr", 500)]
+    for beta in [float(b) for b in args.betas.split(",")]:
+        frames = gen.workload_frames(number, code, frames=F, beta=beta)
+        llr = torch.from_numpy(frames.llr).to(dev)
+        syn = torch.from_numpy(frames.syndrome).to(dev)
+        row = {"experiment": "beta_sweep", "workload": wl["name"], "n": code.n, "rate": code.rate, "frames": F,
+               "beta": beta, "sigma": float(frames.sigma[0]), "runs": {}}
+        for rule, dmax in runs:
+            ldpc.decode(graph, llr, syn, dmax, rule)  # warm-up
+            ms = []
+            for _ in range(max(1, args.steps)):
+                st = ldpc.ldpc_decode_stats()
+                bits, flags, iters = ldpc.decode(graph, llr, syn, dmax, rule, stats=st)
+                ms.append(st.total_ms)
+            t = float(np.median(ms)) * 1e-3
+            flags = flags.cpu().numpy()
+            iters = iters.cpu().numpy()
+            ok = ((flags & 1) > 0) & (bits.cpu().numpy() == frames.x).all(1)
+            fer = float(1.0 - ok.mean())
+            dmean = float(iters.mean())
+            row["runs"][f"{rule}_{dmax}"] = {
+                "fer": fer, "d_mean": dmean, "aborted": int(((flags & 2) > 0).sum()),
+                "ms": t * 1e3, "decoded_mbit_s": code.n * F / t / 1e6,
+                "goodput_mbit_s": float(ok.sum()) * code.n * code.rate / t / 1e6,
+                "K_bits_per_iteration": code.n * code.rate * (1.0 - fer) / dmean}
+        kv = row["runs"]["pce_vnr_500"]["K_bits_per_iteration"]
+        row["K_ratio_vnr_over"] = {k: (kv / v["K_bits_per_iteration"] if v["K_bits_per_iteration"] > 0 else None)
+                                   for k, v in row["runs"].items() if k != "pce_vnr_500"}
+        print(json.dumps(row), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.sweep:
+        run_sweep(args)
     else:
         run_ours(args)
 

@@ -289,6 +289,11 @@ WORKLOADS = {
             frames=32, beta=0.93, rate=0.02, max_iter=500),
     5: dict(name="qc_n1e6_r0.02_stream", kind="qc", mb=49, nb=50, Z=20000, n_w2=25,
             frames=512, beta=0.95, rate=0.02, max_iter=1000, code_from=2),
+    # a (3,6)-regular QC code of the same length class whose BP waterfall lies at
+    # beta ~ 0.86-0.89, where early termination changes FER and mean iterations
+    # (the regime of the paper's Figs. 1-2); used for the beta sweep
+    6: dict(name="qc_n960k_r0.5_reg36", kind="qc", mb=24, nb=48, Z=20000, col_weight=3,
+            frames=32, beta=0.87, rate=0.5, max_iter=500),
 }
 
 
@@ -299,7 +304,10 @@ def workload_code(number: int, Z: int | None = None):
     seed = 1000 + code_no
     if w["kind"] == "csr":
         return random_csr_code(w["n"], w["m"], w["var_degree"], w["check_degrees"], seed)
-    weights = _qc_weights_2_3(w["nb"], w["n_w2"], seed)
+    if "col_weight" in w:
+        weights = np.full(w["nb"], w["col_weight"], dtype=np.int64)
+    else:
+        weights = _qc_weights_2_3(w["nb"], w["n_w2"], seed)
     return random_qc_code(w["mb"], w["nb"], Z or w["Z"], weights, seed)
 
 

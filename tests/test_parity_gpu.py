@@ -268,3 +268,22 @@ def test_expired_grid_wait_returns_timeout_and_context_survives(ldpc, qc_small, 
     bits, flags, iters = ldpc.decode(g, llr, syn, 20, "pce_vnr", groups=groups)
     ref = gpu_decode(ldpc, g, fr.llr, fr.syndrome, 20, "pce_vnr")
     assert (iters.cpu().numpy() == ref["iters"]).all() and (bits.cpu().numpy() == ref["bits"]).all()
+
+
+def test_regular_36_qc_code_in_its_waterfall(ldpc, oracle):
+    """The (3,6)-regular QC family of the beta sweep (weight-6 rows, weight-3
+    columns), at a noise level inside its BP waterfall: successes, VNR aborts
+    and D_max all occur; decisions and messages follow the oracle."""
+    code = gen.workload_code(6, Z=200)
+    g = ldpc.Graph.from_code(code)
+    csr = code.to_csr()
+    fr = gen.workload_frames(6, code, frames=48, beta=0.87)
+    orc = oracle.decode(csr, fr.llr[:4], fr.syndrome[:4], 10, 0, trace_iters=10)
+    got = gpu_decode(ldpc, g, fr.llr[:4], fr.syndrome[:4], 10, "none", trace_iters=10)
+    assert_close_messages(got["c2v"], orc["c2v"], "c2v")
+    assert_close_messages(got["app"], orc["app"], "app")
+    seen = set()
+    for rule in ("pce_vnr", "pce"):
+        bad, res, _ = check_decisions(ldpc, g, csr, oracle, fr.llr, fr.syndrome, 200, rule)
+        seen |= {int(x) for x in res["flags"]}
+    assert {0, 1, 2} <= seen
