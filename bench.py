@@ -58,6 +58,27 @@ def parse():
     return ap.parse_args()
 
 
+def shard_first_frame(rank: int, frames_per_rank: int) -> int:
+    """Replicas only: rank r decodes frames r*F .. r*F + F - 1 of the workload
+    (weak scaling; frames are independent, so no data is exchanged)."""
+    return rank * frames_per_rank
+
+
+def job_time_ms(local_ms: float, dist=None, device=None) -> float:
+    """Whole-job time: the slowest rank's time (a MAX all-reduce)."""
+    if dist is None:
+        return local_ms
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value_mbit_s(n: int, frames_per_rank: int, steps: int, world: int, job_ms: float) -> float:
+    """Decoded Mbit/s of the whole job: every rank's frames over the slowest rank's time."""
+    return n * frames_per_rank * steps * world / (job_ms * 1e-3) / 1e6
+
+
 def algorithmic_bytes_per_frame_iter(code) -> int:
     """8E (c2v read + write) + 12n (Lch read, APP write, APP read once)."""
     return 8 * int(code.edges) + 12 * int(code.n)
@@ -239,7 +260,7 @@ def run_ours(args):
         wl["max_iter"] = args.max_iter
     code = gen.workload_code(args.workload)
     F = args.frames or wl["frames"]
-    frames = gen.workload_frames(args.workload, code, frames=F, first=rank * F)  # weak scaling by frames
+    frames = gen.workload_frames(args.workload, code, frames=F, first=shard_first_frame(rank, F))
 
     # CPU baseline first (rank 0, N = 1), before any GPU work in this process.
     cpu = None
@@ -299,13 +320,8 @@ def run_ours(args):
     main = timed("pce_vnr", args.steps, max(3, args.warmup))
     clk = clocks.stop()
 
-    ms_total = main["ms"]
-    if dist:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
-    bits_total = code.n * F * args.steps * world
-    value = bits_total / (ms_total * 1e-3) / 1e6
+    ms_total = job_time_ms(main["ms"], dist, dev)
+    value = job_value_mbit_s(code.n, F, args.steps, world, ms_total)
     edge_msgs = main["fi"] * 2 * code.edges / (main["ms"] * 1e-3)
     goodput = main["ok_frames"] * code.n * code.rate * args.steps / (main["ms"] * 1e-3) / 1e6
 
