@@ -178,6 +178,55 @@ LDPC_API ldpc_status ldpc_decode_host(const ldpc_graph* graph, int32_t frames, c
                              uint8_t* bits_out, uint8_t* flags_out, int32_t* iters_out,
                              const ldpc_decode_opts* opts, void* cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Batches of frames of several codes (different lengths, rates and noise
+ * levels) decoded by one persistent kernel: frames that stop early are
+ * replaced by waiting ones, whatever their code.  Not in the paper, whose
+ * decoder design is not given; built for streams of reconciliation frames.
+ * ------------------------------------------------------------------------- */
+typedef struct ldpc_batch ldpc_batch;
+
+/* Plan a batch: frame f is decoded with graphs[frame_graph[f]].
+ *   graphs      : 1..4 graphs of one kind (all QC or all CSR), same device
+ *   frame_graph : host int32 [frames], values in [0, n_graphs)
+ * The frames' values sit back to back in the batch buffers: frame f's LLRs
+ * and decided bits start at the sum of n over frames 0..f-1, its syndrome
+ * bytes at the sum of m (ldpc_batch_info gives the totals).  The plan copies
+ * these tables to the device and owns a workspace; the graphs must outlive
+ * it.  One decode at a time per plan. */
+LDPC_API ldpc_status ldpc_batch_create(const ldpc_graph* const* graphs, int32_t n_graphs, int32_t frames,
+                                       const int32_t* frame_graph, ldpc_batch** out);
+LDPC_API void ldpc_batch_destroy(ldpc_batch* batch);
+/* frames, and the lengths of the concatenated LLR (= bits) and syndrome buffers. */
+LDPC_API ldpc_status ldpc_batch_info(const ldpc_batch* batch, int32_t* frames, int64_t* llr_len,
+                                     int64_t* syndrome_len);
+/* As ldpc_decode, on the batch's buffers: llr float / bits_out uint8 [llr_len],
+ * syndrome uint8 [syndrome_len], flags_out uint8 / iters_out int32 [frames].
+ * Traces are not available for batches.  Returns when the results are ready. */
+LDPC_API ldpc_status ldpc_batch_decode(ldpc_batch* batch, const float* llr, const uint8_t* syndrome,
+                                       int32_t max_iter, ldpc_term_rule rule, uint8_t* bits_out,
+                                       uint8_t* flags_out, int32_t* iters_out, const ldpc_decode_opts* opts,
+                                       void* cuda_stream);
+/* The same, stream-ordered and without waiting for the GPU: the outcome is
+ * written to the device int32 *status_out as an ldpc_status code when the
+ * stream reaches it.  Nothing in it synchronises with the host, so it can be
+ * captured in a CUDA graph and replayed; run it (or ldpc_batch_decode) once
+ * with the same options before capturing, so that the workspace exists
+ * (LDPC_ERR_INVALID_ARG otherwise).  opts->stats is ignored. */
+LDPC_API ldpc_status ldpc_batch_decode_async(ldpc_batch* batch, const float* llr, const uint8_t* syndrome,
+                                             int32_t max_iter, ldpc_term_rule rule, uint8_t* bits_out,
+                                             uint8_t* flags_out, int32_t* iters_out, int32_t* status_out,
+                                             const ldpc_decode_opts* opts, void* cuda_stream);
+/* Autotuner: decodes the given inputs once per candidate schedule (CTA groups
+ * 1, 2, 4, 8 x frames in flight: all, 8 per group, 2 per group), keeps the
+ * fastest by kernel time, and uses it for this plan's later decodes whose
+ * opts leave groups / max_active_frames at 0.  The outputs hold the last
+ * candidate's (identical) results.  best_groups / best_slots may be NULL. */
+LDPC_API ldpc_status ldpc_batch_autotune(ldpc_batch* batch, const float* llr, const uint8_t* syndrome,
+                                         int32_t max_iter, ldpc_term_rule rule, uint8_t* bits_out,
+                                         uint8_t* flags_out, int32_t* iters_out, void* cuda_stream,
+                                         int32_t* best_groups, int32_t* best_slots);
+
 /* Device scratch that ldpc_decode_qc_noalloc works in: one fixed array of this
  * many bytes, reserved on every GPU that loads the library, for as long as the
  * library stays loaded. */

@@ -74,41 +74,100 @@ struct CsrDev {
     const int* var_edge;           // [E] edge ids of variable v, ascending
 };
 
+constexpr int kMaxCodes = 4;              // codes one decode call may mix
+
+// Sizes of one code as the decoder walks it.
+template <class Code>
+struct CodeInfo {
+    Code code;
+    int n, m;
+    long long E;
+    int swords;                    // packed syndrome words per frame
+    int cn_tiles, vn_tiles;        // check-node / variable-node items per frame
+    int cn_chunk, vn_chunk;        // QC items: checks of one base row / variables of one base column
+    int nqb;                       // q-blocks per frame: fixed runs of kQBlock variables
+    int vec4;                      // 16-byte variable-node path allowed (Z % 4 == 0, aligned Lch)
+};
+
+template <class Code>
+struct CodeSet {
+    CodeInfo<Code> c[kMaxCodes];
+    int count;
+};
+
 template <typename T>
 struct Params {
-    int m, n;
-    long long E;
     int frames, max_iter, rule, vnr_first_iter;
     T lmax;
-    const float* llr;              // [frames][n]
-    const unsigned* sbits;         // [frames][swords] packed syndrome
-    int swords;
-    unsigned char* bits_out;       // [frames][n]
+    // frames: code, and where its values start in the concatenated buffers
+    // (NULL arrays: one code, frame f at f*n and f*swords)
+    const int* frame_code;         // [frames]
+    const long long* var_off;      // [frames] offset of frame f in llr / bits_out
+    const long long* sb_off;       // [frames] offset of frame f in sbits (words)
+    const float* llr;              // channel LLRs of all frames
+    const unsigned* sbits;         // packed syndromes of all frames
+    unsigned char* bits_out;       // decisions of all frames
     unsigned char* flags_out;      // [frames]
     int* iters_out;                // [frames]
     int slots;
-    T* c2v;                        // [slots][E]
-    T* app;                        // [slots][n]
-    double* qpart;                 // [slots][nqb * kWarps] per-warp partial sums of q
-    double* q0part;                // [slots][nqb * kWarps]
-    int nqb;                       // q-blocks per frame: fixed runs of kQBlock variables
+    long long slot_E;              // per-slot strides (the largest code's sizes)
+    int slot_n, slot_nqb;
+    int cn_tiles_max, vn_tiles_max;
+    T* c2v;                        // [slots][slot_E]
+    T* app;                        // [slots][slot_n]
+    double* qpart;                 // [slots][slot_nqb * kWarps] per-warp partial sums of q
+    double* q0part;                // [slots][slot_nqb * kWarps]
     double* qval;                  // [slots][kQParts] q^(k) summed over fixed ranges of partials
     double* q0val;                 // [slots][kQParts] the same for q^(0)
     int* unsat;                    // [2][slots]
     Ctrl* ctrl;
-    int cn_tiles, vn_tiles;        // tiles per frame
     int trace_iters;
     T* trace_c2v;                  // [trace_iters][frames][E]
     T* trace_app;                  // [trace_iters][frames][n]
     double* trace_q;               // [trace_iters][frames]
     unsigned long long timeout_ns;
-    int vec4;                      // 16-byte variable-node path allowed (Z % 4 == 0, aligned llr)
     unsigned bar_extra;            // test hook: arrivals the first barrier waits for beyond the grid
     int groups;                    // independent CTA groups, each with its own slots and barrier
     int slots_per_group;           // slots = groups * slots_per_group
     int* new_frame;                // [slots] frame taken from the queue by a slot that stopped
-    int cn_chunk, vn_chunk;        // QC items: checks of one base row / variables of one base column
 };
+
+// Where one running frame's data lives (slot s decoding frame f of code ci).
+template <typename T>
+struct FrameCtx {
+    T* c2v;                        // the slot's messages
+    T* app;                        // the slot's APP values
+    const float* llr;              // the frame's channel LLRs
+    const unsigned* sbits;         // the frame's packed syndrome
+    unsigned char* bits;           // the frame's decision (output)
+    double* qpart;                 // the slot's partial sums of q
+    double* q0part;
+    int f, n;
+    long long E;
+    int cn_chunk, vn_chunk, nqb, vec4;
+};
+
+template <typename T, class Code>
+__device__ __forceinline__ FrameCtx<T> frame_ctx(const Params<T>& p, const CodeInfo<Code>& ci, int s, int f) {
+    FrameCtx<T> c;
+    c.c2v = p.c2v + (size_t)s * (size_t)p.slot_E;
+    c.app = p.app + (size_t)s * (size_t)p.slot_n;
+    const long long vo = p.var_off ? p.var_off[f] : (long long)f * ci.n;
+    const long long so = p.sb_off ? p.sb_off[f] : (long long)f * ci.swords;
+    c.llr = p.llr + vo;
+    c.bits = p.bits_out + vo;
+    c.sbits = p.sbits + so;
+    c.qpart = p.qpart + (size_t)s * p.slot_nqb * kWarps;
+    c.q0part = p.q0part + (size_t)s * p.slot_nqb * kWarps;
+    c.f = f;
+    c.n = ci.n;
+    c.E = ci.E;
+    c.cn_chunk = ci.cn_chunk;
+    c.vn_chunk = ci.vn_chunk;
+    c.nqb = ci.nqb;
+    c.vec4 = ci.vec4;
+    return c;
+}
 
 // ---------------------------------------------------------------------------
 // small helpers
@@ -278,7 +337,7 @@ __device__ __forceinline__ unsigned syndrome_bit(const unsigned* sb, int row) {
 }
 
 // ---------------------------------------------------------------------------
-// Quasi-cyclic check-node item: checks t in [t0, t0 + p.cn_chunk) of base row
+// Quasi-cyclic check-node item: checks t in [t0, t0 + cn_chunk) of base row
 // i.  The row's block pointers are set up once; each thread then walks the
 // chunk two checks at a time (both checks' loads issued before any
 // arithmetic).  MODE and SYND are compile-time so the hot loop carries no
@@ -291,14 +350,14 @@ constexpr int kQBlock = 4 * kThreads;    // variables per q partial sum (per war
 constexpr int kQParts = 8;               // a frame's q is reduced in this many fixed ranges, by different CTAs
 
 template <int D, int MODE, bool SYND, typename T>
-__device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, int s, int f, int i, int t0,
+__device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, const FrameCtx<T>& fc, int i, int t0,
                                            int b0) {
     const int Z = q.Z;
-    const int t_end = min(t0 + p.cn_chunk, Z);
-    T* c2v = p.c2v + (size_t)s * (size_t)p.E;
-    const T* app = p.app + (size_t)s * (size_t)p.n;
-    const float* llr = p.llr + (size_t)f * (size_t)p.n;
-    const unsigned* sb = p.sbits + (size_t)f * (size_t)p.swords + (size_t)i * Z / 32;
+    const int t_end = min(t0 + fc.cn_chunk, Z);
+    T* c2v = fc.c2v;
+    const T* app = fc.app;
+    const float* llr = fc.llr;
+    const unsigned* sb = fc.sbits + (size_t)i * Z / 32;
     const int sbit0 = (i * Z) & 31;  // bit offset of check (i, 0) in its word
     // per-block offsets: variable column (col*Z) and message block ((b0+j)*Z)
     int sh[D], vo[D], mo[D];
@@ -361,13 +420,14 @@ __device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, i
 
 // Rows of weight > 6: runtime degree, local arrays.
 template <int MODE, bool SYND, typename T>
-__device__ bool qc_cn_item_n(const Params<T>& p, const QcDev& q, int s, int f, int i, int t0, int b0, int d) {
+__device__ bool qc_cn_item_n(const Params<T>& p, const QcDev& q, const FrameCtx<T>& fc, int i, int t0, int b0,
+                             int d) {
     const int Z = q.Z;
-    const int t_end = min(t0 + p.cn_chunk, Z);
-    T* c2v = p.c2v + (size_t)s * (size_t)p.E;
-    const T* app = p.app + (size_t)s * (size_t)p.n;
-    const float* llr = p.llr + (size_t)f * (size_t)p.n;
-    const unsigned* sb = p.sbits + (size_t)f * (size_t)p.swords;
+    const int t_end = min(t0 + fc.cn_chunk, Z);
+    T* c2v = fc.c2v;
+    const T* app = fc.app;
+    const float* llr = fc.llr;
+    const unsigned* sb = fc.sbits;
     bool unsat = false;
     for (int t = t0 + (int)threadIdx.x; t < t_end; t += kThreads) {
         const unsigned sbit = syndrome_bit(sb, i * Z + t);
@@ -401,54 +461,53 @@ __device__ bool qc_cn_item_n(const Params<T>& p, const QcDev& q, int s, int f, i
 }
 
 template <int MODE, bool SYND, typename T>
-__device__ __forceinline__ bool qc_cn_dispatch(const Params<T>& p, const QcDev& q, int s, int f, int i, int t0,
-                                               int b0, int d) {
+__device__ __forceinline__ bool qc_cn_dispatch(const Params<T>& p, const QcDev& q, const FrameCtx<T>& fc, int i,
+                                               int t0, int b0, int d) {
     switch (d) {
         case 0: {
             bool unsat = false;
             if (SYND) {
-                const unsigned* sb = p.sbits + (size_t)f * (size_t)p.swords;
-                const int t_end = min(t0 + p.cn_chunk, q.Z);
+                const unsigned* sb = fc.sbits;
+                const int t_end = min(t0 + fc.cn_chunk, q.Z);
                 for (int t = t0 + (int)threadIdx.x; t < t_end; t += kThreads)
                     unsat |= syndrome_bit(sb, i * q.Z + t) != 0u;
             }
             return unsat;
         }
-        case 1: return qc_cn_item<1, MODE, SYND, T>(p, q, s, f, i, t0, b0);
-        case 2: return qc_cn_item<2, MODE, SYND, T>(p, q, s, f, i, t0, b0);
-        case 3: return qc_cn_item<3, MODE, SYND, T>(p, q, s, f, i, t0, b0);
-        case 4: return qc_cn_item<4, MODE, SYND, T>(p, q, s, f, i, t0, b0);
-        case 5: return qc_cn_item<5, MODE, SYND, T>(p, q, s, f, i, t0, b0);
-        case 6: return qc_cn_item<6, MODE, SYND, T>(p, q, s, f, i, t0, b0);
-        default: return qc_cn_item_n<MODE, SYND, T>(p, q, s, f, i, t0, b0, d);
+        case 1: return qc_cn_item<1, MODE, SYND, T>(p, q, fc, i, t0, b0);
+        case 2: return qc_cn_item<2, MODE, SYND, T>(p, q, fc, i, t0, b0);
+        case 3: return qc_cn_item<3, MODE, SYND, T>(p, q, fc, i, t0, b0);
+        case 4: return qc_cn_item<4, MODE, SYND, T>(p, q, fc, i, t0, b0);
+        case 5: return qc_cn_item<5, MODE, SYND, T>(p, q, fc, i, t0, b0);
+        case 6: return qc_cn_item<6, MODE, SYND, T>(p, q, fc, i, t0, b0);
+        default: return qc_cn_item_n<MODE, SYND, T>(p, q, fc, i, t0, b0, d);
     }
 }
 
 template <typename T>
-__device__ __forceinline__ bool cn_tile(const Params<T>& p, const QcDev& q, int s, int f, int k,
-                                        int mode, bool want_synd, int tile) {
-    const int per_row = (q.Z + p.cn_chunk - 1) / p.cn_chunk;
+__device__ __forceinline__ bool cn_tile(const Params<T>& p, const QcDev& q, const FrameCtx<T>& fc, int mode,
+                                        bool want_synd, int tile) {
+    const int per_row = (q.Z + fc.cn_chunk - 1) / fc.cn_chunk;
     const int i = tile / per_row;
-    const int t0 = (tile - i * per_row) * p.cn_chunk;
+    const int t0 = (tile - i * per_row) * fc.cn_chunk;
     const int b0 = __ldg(q.row_ptr + i);
     const int d = __ldg(q.row_ptr + i + 1) - b0;
-    (void)k;
-    if (mode == kModeFirst) return qc_cn_dispatch<kModeFirst, false, T>(p, q, s, f, i, t0, b0, d);
-    if (mode == kModeSynd) return qc_cn_dispatch<kModeSynd, true, T>(p, q, s, f, i, t0, b0, d);
-    if (want_synd) return qc_cn_dispatch<kModeFull, true, T>(p, q, s, f, i, t0, b0, d);
-    return qc_cn_dispatch<kModeFull, false, T>(p, q, s, f, i, t0, b0, d);
+    if (mode == kModeFirst) return qc_cn_dispatch<kModeFirst, false, T>(p, q, fc, i, t0, b0, d);
+    if (mode == kModeSynd) return qc_cn_dispatch<kModeSynd, true, T>(p, q, fc, i, t0, b0, d);
+    if (want_synd) return qc_cn_dispatch<kModeFull, true, T>(p, q, fc, i, t0, b0, d);
+    return qc_cn_dispatch<kModeFull, false, T>(p, q, fc, i, t0, b0, d);
 }
 
 // ---------------------------------------------------------------------------
 // CSR check-node tile: checks tile*kCnTile ...; one check per thread-slot.
 // ---------------------------------------------------------------------------
 template <int D, typename T>
-__device__ __forceinline__ bool csr_cn_check(const Params<T>& p, const CsrDev& g, int s, int f, int k,
-                                             int mode, bool want_synd, int row, int e0) {
-    T* c2v = p.c2v + (long long)s * p.E;
-    const T* app = p.app + (long long)s * p.n;
-    const float* llr = p.llr + (long long)f * p.n;
-    const unsigned sbit = syndrome_bit(p.sbits + (long long)f * p.swords, row);
+__device__ __forceinline__ bool csr_cn_check(const Params<T>& p, const CsrDev& g, const FrameCtx<T>& fc, int mode,
+                                             bool want_synd, int row, int e0) {
+    T* c2v = fc.c2v;
+    const T* app = fc.app;
+    const float* llr = fc.llr;
+    const unsigned sbit = syndrome_bit(fc.sbits, row);
     T a[D], o[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
@@ -479,12 +538,12 @@ __device__ __forceinline__ bool csr_cn_check(const Params<T>& p, const CsrDev& g
 }
 
 template <typename T>
-__device__ bool csr_cn_check_n(const Params<T>& p, const CsrDev& g, int s, int f, int k, int mode,
-                               bool want_synd, int row, int e0, int d) {
-    T* c2v = p.c2v + (long long)s * p.E;
-    const T* app = p.app + (long long)s * p.n;
-    const float* llr = p.llr + (long long)f * p.n;
-    const unsigned sbit = syndrome_bit(p.sbits + (long long)f * p.swords, row);
+__device__ bool csr_cn_check_n(const Params<T>& p, const CsrDev& g, const FrameCtx<T>& fc, int mode, bool want_synd,
+                               int row, int e0, int d) {
+    T* c2v = fc.c2v;
+    const T* app = fc.app;
+    const float* llr = fc.llr;
+    const unsigned sbit = syndrome_bit(fc.sbits, row);
     if (d == 0) return want_synd && sbit != 0u;
     T v[kMaxDeg], out[kMaxDeg];
     unsigned pr = sbit;
@@ -508,8 +567,8 @@ __device__ bool csr_cn_check_n(const Params<T>& p, const CsrDev& g, int s, int f
 }
 
 template <typename T>
-__device__ __forceinline__ bool cn_tile(const Params<T>& p, const CsrDev& g, int s, int f, int k,
-                                        int mode, bool want_synd, int tile) {
+__device__ __forceinline__ bool cn_tile(const Params<T>& p, const CsrDev& g, const FrameCtx<T>& fc, int mode,
+                                        bool want_synd, int tile) {
     bool unsat = false;
     for (int c = 0; c < kCPT; ++c) {
         const int row = tile * kCnTile + c * kThreads + (int)threadIdx.x;
@@ -517,13 +576,13 @@ __device__ __forceinline__ bool cn_tile(const Params<T>& p, const CsrDev& g, int
         const int e0 = __ldg(g.row_ptr + row);
         const int d = __ldg(g.row_ptr + row + 1) - e0;
         switch (d) {
-            case 1: unsat |= csr_cn_check<1, T>(p, g, s, f, k, mode, want_synd, row, e0); break;
-            case 2: unsat |= csr_cn_check<2, T>(p, g, s, f, k, mode, want_synd, row, e0); break;
-            case 3: unsat |= csr_cn_check<3, T>(p, g, s, f, k, mode, want_synd, row, e0); break;
-            case 4: unsat |= csr_cn_check<4, T>(p, g, s, f, k, mode, want_synd, row, e0); break;
-            case 5: unsat |= csr_cn_check<5, T>(p, g, s, f, k, mode, want_synd, row, e0); break;
-            case 6: unsat |= csr_cn_check<6, T>(p, g, s, f, k, mode, want_synd, row, e0); break;
-            default: unsat |= csr_cn_check_n<T>(p, g, s, f, k, mode, want_synd, row, e0, d); break;
+            case 1: unsat |= csr_cn_check<1, T>(p, g, fc, mode, want_synd, row, e0); break;
+            case 2: unsat |= csr_cn_check<2, T>(p, g, fc, mode, want_synd, row, e0); break;
+            case 3: unsat |= csr_cn_check<3, T>(p, g, fc, mode, want_synd, row, e0); break;
+            case 4: unsat |= csr_cn_check<4, T>(p, g, fc, mode, want_synd, row, e0); break;
+            case 5: unsat |= csr_cn_check<5, T>(p, g, fc, mode, want_synd, row, e0); break;
+            case 6: unsat |= csr_cn_check<6, T>(p, g, fc, mode, want_synd, row, e0); break;
+            default: unsat |= csr_cn_check_n<T>(p, g, fc, mode, want_synd, row, e0, d); break;
         }
     }
     return unsat;
@@ -546,10 +605,11 @@ __device__ __forceinline__ void warp_sum_store(T acc, double* dst) {
 // that only iterations a frame completes are recorded.  Edge order is the
 // lifted matrix's row-major order: row i*Z + t, blocks of row i in turn.
 template <typename T>
-__device__ void trace_c2v_qc(const Params<T>& p, const QcDev& q, const T* c2v, int f, int k, int u, int cb0,
+__device__ void trace_c2v_qc(const Params<T>& p, const QcDev& q, const FrameCtx<T>& fc, int k, int u, int cb0,
                              int dv) {
     const int Z = q.Z;
-    T* tr = p.trace_c2v + ((size_t)k * p.frames + f) * (size_t)p.E;
+    const T* c2v = fc.c2v;
+    T* tr = p.trace_c2v + ((size_t)k * p.frames + fc.f) * (size_t)fc.E;
     for (int b = 0; b < dv; ++b) {
         const int blk = __ldg(q.col_blk + cb0 + b);
         const int i = __ldg(q.blk_row + blk);
@@ -561,7 +621,7 @@ __device__ void trace_c2v_qc(const Params<T>& p, const QcDev& q, const T* c2v, i
     }
 }
 
-// Quasi-cyclic variable-node item: variables u in [u0, u0 + p.vn_chunk) of
+// Quasi-cyclic variable-node item: variables u in [u0, u0 + vn_chunk) of
 // base column j.  DV > 0: compile-time column degree; DV == 0: runtime dv.
 // The item is walked in q-blocks of kQBlock variables (u0 is a multiple of
 // kQBlock); in each, thread t handles variables 4t .. 4t+3, so q's partial
@@ -569,25 +629,25 @@ __device__ void trace_c2v_qc(const Params<T>& p, const QcDev& q, const T* c2v, i
 // the item size or on the load path.  With vec (Z % 4 == 0, aligned Lch) the
 // four variables move as 16-byte loads and stores.
 template <int DV, typename T>
-__device__ __forceinline__ void qc_vn_cols(const Params<T>& p, const QcDev& q, int s, int f, int k, int j, int u0,
-                                           int cb0, int dv) {
+__device__ __forceinline__ void qc_vn_cols(const Params<T>& p, const QcDev& q, const FrameCtx<T>& fc, int k, int j,
+                                           int u0, int cb0, int dv) {
     constexpr bool kFixed = DV > 0;
     const int Z = q.Z;
-    const int u_end = min(u0 + p.vn_chunk, Z);
+    const int u_end = min(u0 + fc.vn_chunk, Z);
     const int nd = kFixed ? DV : dv;
     const bool inV = nd > 1;
     const bool want_q0 = (k == 0) && p.vnr_first_iter <= 1;
     const bool tracing = k < p.trace_iters;
-    const T* c2v = p.c2v + (size_t)s * (size_t)p.E;
-    T* app = p.app + (size_t)s * (size_t)p.n + j * Z;
-    const float* llr = p.llr + (size_t)f * (size_t)p.n + j * Z;
+    const T* c2v = fc.c2v;
+    T* app = fc.app + j * Z;
+    const float* llr = fc.llr + j * Z;
     const T* cb[kFixed ? DV : 1];
     if constexpr (kFixed) {
 #pragma unroll
         for (int b = 0; b < DV; ++b) cb[b] = c2v + __ldg(q.col_blk + cb0 + b) * Z;
     }
     bool vec = false;
-    if constexpr (sizeof(T) == 4) vec = p.vec4 != 0;
+    if constexpr (sizeof(T) == 4) vec = fc.vec4 != 0;
     const int qb_per_col = (Z + kQBlock - 1) / kQBlock;
     for (int ub = u0; ub < u_end; ub += kQBlock) {
         const int u = ub + 4 * (int)threadIdx.x;
@@ -647,39 +707,39 @@ __device__ __forceinline__ void qc_vn_cols(const Params<T>& p, const QcDev& q, i
             }
             if (tracing) {
                 for (int e = 0; e < 4 && u + e < u_end; ++e) {
-                    if (p.trace_app) p.trace_app[((size_t)k * p.frames + f) * (size_t)p.n + j * Z + u + e] = sum[e];
-                    if (p.trace_c2v) trace_c2v_qc(p, q, c2v, f, k, u + e, cb0, nd);
+                    if (p.trace_app) p.trace_app[((size_t)k * p.frames + fc.f) * (size_t)fc.n + j * Z + u + e] = sum[e];
+                    if (p.trace_c2v) trace_c2v_qc(p, q, fc, k, u + e, cb0, nd);
                 }
             }
         }
-        const size_t part = ((size_t)s * p.nqb + (size_t)j * qb_per_col + ub / kQBlock) * kWarps;
-        warp_sum_store(acc, p.qpart + part);
-        if (want_q0) warp_sum_store(acc0, p.q0part + part);
+        const size_t part = ((size_t)j * qb_per_col + ub / kQBlock) * kWarps;
+        warp_sum_store(acc, fc.qpart + part);
+        if (want_q0) warp_sum_store(acc0, fc.q0part + part);
     }
 }
 
 template <typename T>
-__device__ __forceinline__ void vn_tile(const Params<T>& p, const QcDev& q, int s, int f, int k, int tile) {
-    const int per_col = (q.Z + p.vn_chunk - 1) / p.vn_chunk;
+__device__ __forceinline__ void vn_tile(const Params<T>& p, const QcDev& q, const FrameCtx<T>& fc, int k, int tile) {
+    const int per_col = (q.Z + fc.vn_chunk - 1) / fc.vn_chunk;
     const int j = tile / per_col;
-    const int u0 = (tile - j * per_col) * p.vn_chunk;
+    const int u0 = (tile - j * per_col) * fc.vn_chunk;
     const int cb0 = __ldg(q.col_ptr + j);
     const int dv = __ldg(q.col_ptr + j + 1) - cb0;
     switch (dv) {
-        case 1: qc_vn_cols<1, T>(p, q, s, f, k, j, u0, cb0, dv); break;
-        case 2: qc_vn_cols<2, T>(p, q, s, f, k, j, u0, cb0, dv); break;
-        case 3: qc_vn_cols<3, T>(p, q, s, f, k, j, u0, cb0, dv); break;
-        case 4: qc_vn_cols<4, T>(p, q, s, f, k, j, u0, cb0, dv); break;
-        default: qc_vn_cols<0, T>(p, q, s, f, k, j, u0, cb0, dv); break;
+        case 1: qc_vn_cols<1, T>(p, q, fc, k, j, u0, cb0, dv); break;
+        case 2: qc_vn_cols<2, T>(p, q, fc, k, j, u0, cb0, dv); break;
+        case 3: qc_vn_cols<3, T>(p, q, fc, k, j, u0, cb0, dv); break;
+        case 4: qc_vn_cols<4, T>(p, q, fc, k, j, u0, cb0, dv); break;
+        default: qc_vn_cols<0, T>(p, q, fc, k, j, u0, cb0, dv); break;
     }
 }
 
 template <typename T>
-__device__ __forceinline__ void vn_tile(const Params<T>& p, const CsrDev& g, int s, int f, int k, int tile) {
+__device__ __forceinline__ void vn_tile(const Params<T>& p, const CsrDev& g, const FrameCtx<T>& fc, int k, int tile) {
     const bool want_q0 = (k == 0) && p.vnr_first_iter <= 1;
-    const T* c2v = p.c2v + (size_t)s * (size_t)p.E;
-    T* app = p.app + (size_t)s * (size_t)p.n;
-    const float* llr = p.llr + (size_t)f * (size_t)p.n;
+    const T* c2v = fc.c2v;
+    T* app = fc.app;
+    const float* llr = fc.llr;
     T acc = T(0), acc0 = T(0);
 #pragma unroll
     for (int c = 0; c < kVPT; ++c) {
@@ -695,44 +755,42 @@ __device__ __forceinline__ void vn_tile(const Params<T>& p, const CsrDev& g, int
                 acc0 += absm(L);
             }
             if (k < p.trace_iters) {
-                if (p.trace_app) p.trace_app[((size_t)k * p.frames + f) * (size_t)p.n + v] = sum;
+                if (p.trace_app) p.trace_app[((size_t)k * p.frames + fc.f) * (size_t)fc.n + v] = sum;
                 if (p.trace_c2v) {
-                    T* tr = p.trace_c2v + ((size_t)k * p.frames + f) * (size_t)p.E;
+                    T* tr = p.trace_c2v + ((size_t)k * p.frames + fc.f) * (size_t)fc.E;
                     for (int a = a0; a < a1; ++a) tr[__ldg(g.var_edge + a)] = c2v[__ldg(g.var_edge + a)];
                 }
             }
         }
     }
-    const size_t part = ((size_t)s * p.nqb + tile) * kWarps;
-    warp_sum_store(acc, p.qpart + part);
-    if (want_q0) warp_sum_store(acc0, p.q0part + part);
+    const size_t part = (size_t)tile * kWarps;
+    warp_sum_store(acc, fc.qpart + part);
+    if (want_q0) warp_sum_store(acc0, fc.q0part + part);
 }
 
 // Hard decision of a stopped frame: bits = [APP < 0] over the tile's variables.
 template <typename T>
-__device__ __forceinline__ void final_tile(const Params<T>& p, int s, int f, int tile) {
-    const T* app = p.app + (long long)s * p.n;
-    unsigned char* bits = p.bits_out + (long long)f * p.n;
+__device__ __forceinline__ void final_tile(const FrameCtx<T>& fc, int tile) {
     for (int c = 0; c < kVPT; ++c) {
         const long long v = (long long)tile * kVnTile + c * kThreads + threadIdx.x;
-        if (v < p.n) bits[v] = (unsigned char)(app[v] < T(0));
+        if (v < fc.n) fc.bits[v] = (unsigned char)(fc.app[v] < T(0));
     }
 }
 
 // QC items run per column block, so the variable range of an item differs.
 template <typename T>
-__device__ __forceinline__ void final_tile(const Params<T>& p, const QcDev& q, int s, int f, int tile) {
-    const int per_col = (q.Z + p.vn_chunk - 1) / p.vn_chunk;
+__device__ __forceinline__ void final_tile(const QcDev& q, const FrameCtx<T>& fc, int tile) {
+    const int per_col = (q.Z + fc.vn_chunk - 1) / fc.vn_chunk;
     const int j = tile / per_col;
-    const int u0 = (tile - j * per_col) * p.vn_chunk;
-    const int u_end = min(u0 + p.vn_chunk, q.Z);
-    const T* app = p.app + (size_t)s * (size_t)p.n + j * q.Z;
-    unsigned char* bits = p.bits_out + (size_t)f * (size_t)p.n + j * q.Z;
+    const int u0 = (tile - j * per_col) * fc.vn_chunk;
+    const int u_end = min(u0 + fc.vn_chunk, q.Z);
+    const T* app = fc.app + j * q.Z;
+    unsigned char* bits = fc.bits + j * q.Z;
     for (int u = u0 + (int)threadIdx.x; u < u_end; u += kThreads) bits[u] = (unsigned char)(app[u] < T(0));
 }
 template <typename T>
-__device__ __forceinline__ void final_tile(const Params<T>& p, const CsrDev&, int s, int f, int tile) {
-    final_tile(p, s, f, tile);
+__device__ __forceinline__ void final_tile(const CsrDev&, const FrameCtx<T>& fc, int tile) {
+    final_tile(fc, tile);
 }
 
 // Deterministic FP64 sum of a frame's per-tile partials (fixed order).
@@ -771,13 +829,14 @@ __device__ __forceinline__ double block_sum_fixed(const double* part, int count,
 // frames in flight have to stay in L2.
 // ---------------------------------------------------------------------------
 template <typename T, class Code>
-__global__ void __launch_bounds__(kThreads, 4) bp_decode_kernel(Params<T> p, Code code) {
+__global__ void __launch_bounds__(kThreads, 4) bp_decode_kernel(Params<T> p, CodeSet<Code> cs) {
     const int SG = p.slots_per_group;
     extern __shared__ double smem_dyn[];
     double* st_qprev = smem_dyn;                  // [SG]
     int* st_frame = (int*)(st_qprev + SG);        // [SG]
     int* st_k = st_frame + SG;                    // [SG]
-    int* listA = st_k + SG;                       // [SG]
+    int* st_code = st_k + SG;                     // [SG]
+    int* listA = st_code + SG;                    // [SG]
     int* listB = listA + SG;                      // [SG]
     __shared__ double s_red[kWarps];
     __shared__ int s_nA, s_nB;
@@ -791,7 +850,9 @@ __global__ void __launch_bounds__(kThreads, 4) bp_decode_kernel(Params<T> p, Cod
     int* err = &p.ctrl->err;
 
     for (int l = threadIdx.x; l < SG; l += kThreads) {
-        st_frame[l] = s0 + l < p.frames ? s0 + l : -1;
+        const int f = s0 + l < p.frames ? s0 + l : -1;
+        st_frame[l] = f;
+        st_code[l] = (f >= 0 && p.frame_code) ? p.frame_code[f] : 0;
         st_k[l] = 0;
         st_qprev[l] = 0.0;
     }
@@ -820,16 +881,20 @@ __global__ void __launch_bounds__(kThreads, 4) bp_decode_kernel(Params<T> p, Cod
         if (nA == 0) break;
 
         // ---- phase A: check nodes + syndrome of the current decision -----
-        const unsigned totalA = (unsigned)nA * (unsigned)p.cn_tiles;
+        // (every slot owns cn_tiles_max items; a frame of a smaller code skips the rest)
+        const unsigned totalA = (unsigned)nA * (unsigned)p.cn_tiles_max;
         for (unsigned it = lb; it < totalA; it += gsize) {
-            const unsigned si = it / (unsigned)p.cn_tiles;
+            const unsigned si = it / (unsigned)p.cn_tiles_max;
             const int l = listA[si];
+            const int tile = (int)(it - si * (unsigned)p.cn_tiles_max);
+            const CodeInfo<Code>& ci = cs.c[st_code[l]];
+            if (tile >= ci.cn_tiles) continue;
             const int s = s0 + l;
-            const int tile = (int)(it - si * (unsigned)p.cn_tiles);
             const int k = st_k[l];
             const int mode = k == 0 ? kModeFirst : (k >= p.max_iter ? kModeSynd : kModeFull);
             const bool want_synd = k >= 1 && (p.rule != kRuleNone || k >= p.max_iter);
-            const bool unsat = cn_tile<T>(p, code, s, st_frame[l], k, mode, want_synd, tile);
+            const FrameCtx<T> fc = frame_ctx(p, ci, s, st_frame[l]);
+            const bool unsat = cn_tile<T>(p, ci.code, fc, mode, want_synd, tile);
             if (want_synd && __any_sync(0xffffffffu, unsat) && lane == 0)
                 atomicOr(&p.unsat[par * p.slots + s], 1);
         }
@@ -837,24 +902,24 @@ __global__ void __launch_bounds__(kThreads, 4) bp_decode_kernel(Params<T> p, Cod
         // are summed in kQParts fixed ranges, each by its own CTA (counted from
         // the end of the group, where CTAs get one item fewer when the items
         // do not divide evenly); the decision adds the kQParts sums in order
-        {
-            const int np = p.nqb * kWarps;
+        for (int w = gsize - 1 - lb; w >= 0 && w < nA * kQParts; w += gsize) {
+            const int l = listA[w / kQParts];
+            const int r = w % kQParts;
+            const int s = s0 + l;
+            const int k = st_k[l];
+            if (k < 1) continue;
+            const int np = cs.c[st_code[l]].nqb * kWarps;
             const int per = (np + kQParts - 1) / kQParts;
-            for (int w = gsize - 1 - lb; w >= 0 && w < nA * kQParts; w += gsize) {
-                const int l = listA[w / kQParts];
-                const int r = w % kQParts;
-                const int s = s0 + l;
-                const int k = st_k[l];
-                if (k < 1) continue;
-                const int lo = r * per, cnt = max(0, min(np, lo + per) - lo);
-                const double qv = block_sum_fixed(p.qpart + (size_t)s * np + lo, cnt, s_red);
-                const bool with_q0 = k == 1 && p.vnr_first_iter <= 1;
-                double q0 = 0.0;
-                if (with_q0) q0 = block_sum_fixed(p.q0part + (size_t)s * np + lo, cnt, s_red);
-                if (threadIdx.x == 0) {
-                    p.qval[(size_t)s * kQParts + r] = qv;
-                    if (with_q0) p.q0val[(size_t)s * kQParts + r] = q0;
-                }
+            const int lo = r * per, cnt = max(0, min(np, lo + per) - lo);
+            const double* qp = p.qpart + (size_t)s * p.slot_nqb * kWarps;
+            const double* q0p = p.q0part + (size_t)s * p.slot_nqb * kWarps;
+            const double qv = block_sum_fixed(qp + lo, cnt, s_red);
+            const bool with_q0 = k == 1 && p.vnr_first_iter <= 1;
+            double q0 = 0.0;
+            if (with_q0) q0 = block_sum_fixed(q0p + lo, cnt, s_red);
+            if (threadIdx.x == 0) {
+                p.qval[(size_t)s * kQParts + r] = qv;
+                if (with_q0) p.q0val[(size_t)s * kQParts + r] = q0;
             }
         }
         if (!grid_sync(bar, err, gsize, 2u * step + 1u, p.timeout_ns, step == 0 ? p.bar_extra : 0u)) return;
@@ -917,18 +982,21 @@ __global__ void __launch_bounds__(kThreads, 4) bp_decode_kernel(Params<T> p, Cod
         const int nB = s_nB;
 
         // ---- phase B: variable nodes / write-out of stopped frames -------
-        const unsigned totalB = (unsigned)nB * (unsigned)p.vn_tiles;
+        const unsigned totalB = (unsigned)nB * (unsigned)p.vn_tiles_max;
         for (unsigned it = lb; it < totalB; it += gsize) {
             // phase B walks the slots in the reverse order of phase A, so it starts
             // on the frames whose messages phase A wrote last (still in L2)
-            const unsigned si = it / (unsigned)p.vn_tiles;
+            const unsigned si = it / (unsigned)p.vn_tiles_max;
             const int e = listB[nB - 1 - (int)si];
             const int l = e & 0xffff;
-            const int tile = (int)(it - si * (unsigned)p.vn_tiles);
+            const int tile = (int)(it - si * (unsigned)p.vn_tiles_max);
+            const CodeInfo<Code>& ci = cs.c[st_code[l]];
+            if (tile >= ci.vn_tiles) continue;
+            const FrameCtx<T> fc = frame_ctx(p, ci, s0 + l, st_frame[l]);
             if ((e >> 16) == 0)
-                vn_tile<T>(p, code, s0 + l, st_frame[l], st_k[l], tile);
+                vn_tile<T>(p, ci.code, fc, st_k[l], tile);
             else
-                final_tile<T>(p, code, s0 + l, st_frame[l], tile);
+                final_tile<T>(ci.code, fc, tile);
         }
         if (lb == 0)
             for (int l = threadIdx.x; l < SG; l += kThreads) p.unsat[(par ^ 1) * p.slots + s0 + l] = 0;
@@ -941,7 +1009,9 @@ __global__ void __launch_bounds__(kThreads, 4) bp_decode_kernel(Params<T> p, Cod
             if ((e >> 16) == 0) {
                 st_k[l] += 1;
             } else {
-                st_frame[l] = ld_volatile(&p.new_frame[s0 + l]);
+                const int nf = ld_volatile(&p.new_frame[s0 + l]);
+                st_frame[l] = nf;
+                st_code[l] = (nf >= 0 && p.frame_code) ? p.frame_code[nf] : 0;
                 st_k[l] = 0;
                 st_qprev[l] = 0.0;
             }
@@ -950,26 +1020,57 @@ __global__ void __launch_bounds__(kThreads, 4) bp_decode_kernel(Params<T> p, Cod
     }
 }
 
-// Pack the syndrome bytes into bits, 32 checks per word; any byte other than
-// 0/1 raises kErrSyndrome (the decode kernel then returns at once).
-__global__ void pack_syndrome_kernel(const unsigned char* __restrict__ s, int frames, int m, int swords,
+// Where each frame's syndrome bytes are and where its packed words go.
+struct PackInfo {
+    int m[kMaxCodes];              // checks per frame of each code
+    int swords[kMaxCodes];
+    const int* frame_code;         // [frames], NULL = all code 0
+    const long long* syn_off;      // [frames] byte offset, NULL = f * m
+    const long long* sb_off;       // [frames] word offset, NULL = f * swords
+};
+
+// Pack the syndrome bytes into bits, 32 checks per word, one frame per CTA
+// (grid-stride over frames, one warp per word); any byte other than 0/1
+// raises kErrSyndrome (the decode kernel then returns at once).
+__global__ void pack_syndrome_kernel(const unsigned char* __restrict__ syn, int frames, PackInfo pi,
                                      unsigned* __restrict__ out, Ctrl* ctrl) {
-    const long long nwarps_total = (long long)frames * swords;
-    const int lane = threadIdx.x & 31;
-    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const long long stride = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long w = gw; w < nwarps_total; w += stride) {
-        const long long f = w / swords;
-        const int word = (int)(w - f * swords);
-        const int c = word * 32 + lane;
-        const unsigned char b = c < m ? s[f * m + c] : (unsigned char)0;
-        const unsigned bits = __ballot_sync(0xffffffffu, (b & 1u) != 0u);
-        const bool bad = __any_sync(0xffffffffu, b > 1u);
-        if (lane == 0) {
-            out[w] = bits;
-            if (bad) atomicCAS(&ctrl->err, kErrNone, kErrSyndrome);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int f = blockIdx.x; f < frames; f += gridDim.x) {
+        const int c = pi.frame_code ? pi.frame_code[f] : 0;
+        const int m = pi.m[c], swords = pi.swords[c];
+        const unsigned char* s = syn + (pi.syn_off ? pi.syn_off[f] : (long long)f * m);
+        unsigned* o = out + (pi.sb_off ? pi.sb_off[f] : (long long)f * swords);
+        bool bad = false;
+        for (int w = warp; w < swords; w += nw) {
+            const int i = w * 32 + lane;
+            const unsigned char b = i < m ? s[i] : (unsigned char)0;
+            const unsigned bits = __ballot_sync(0xffffffffu, (b & 1u) != 0u);
+            bad |= __any_sync(0xffffffffu, b > 1u);
+            if (lane == 0) o[w] = bits;
         }
+        if (bad && lane == 0) atomicCAS(&ctrl->err, kErrNone, kErrSyndrome);
     }
+}
+
+// Start-of-decode control words: every group's barrier cleared, the error word
+// and totals zeroed, the queue of waiting frames starting at `next_frame`.
+// (A kernel rather than a host copy, so a whole decode can be captured in a
+// CUDA graph.)
+__global__ void init_ctrl_kernel(Ctrl* ctrl, int groups, int next_frame, int* unsat, int unsat_words) {
+    for (int i = threadIdx.x; i < groups; i += blockDim.x) {
+        ctrl[i].bar_count = 0u;
+        ctrl[i].bar_gen = 0u;
+        ctrl[i].err = kErrNone;
+        ctrl[i].next_frame = i == 0 ? next_frame : 0;
+        ctrl[i].frame_iters = 0ull;
+    }
+    for (int i = threadIdx.x; i < unsat_words; i += blockDim.x) unsat[i] = 0;
+}
+
+// The decode's outcome as an ldpc_status code (0 ok, 1 bad syndrome byte, 5 timeout).
+__global__ void status_kernel(const Ctrl* ctrl, int* out) {
+    const int e = ctrl->err;
+    *out = e == kErrNone ? 0 : (e == kErrSyndrome ? 1 : (e == kErrTimeout ? 5 : 4));
 }
 
 }  // namespace ldpcgb

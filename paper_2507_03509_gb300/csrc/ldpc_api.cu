@@ -112,24 +112,23 @@ struct Layout {
     size_t c2v, app, qpart, q0part, qval, q0val, unsat, sbits, new_frame, total;
 };
 
-Layout make_layout(const ldpc_graph* g, int slots, size_t elem, int frames, int swords, int nqb) {
+Layout make_layout(int slots, size_t elem, long long slot_E, int slot_n, int slot_nqb, long long sbits_words) {
     Layout L{};
     size_t o = 0;
-    L.c2v = o;    o = align_up(o + (size_t)slots * (size_t)g->E * elem, 256);
-    L.app = o;    o = align_up(o + (size_t)slots * (size_t)g->n * elem, 256);
-    L.qpart = o;  o = align_up(o + (size_t)slots * nqb * kWarps * sizeof(double), 256);
-    L.q0part = o; o = align_up(o + (size_t)slots * nqb * kWarps * sizeof(double), 256);
+    L.c2v = o;    o = align_up(o + (size_t)slots * (size_t)slot_E * elem, 256);
+    L.app = o;    o = align_up(o + (size_t)slots * (size_t)slot_n * elem, 256);
+    L.qpart = o;  o = align_up(o + (size_t)slots * slot_nqb * kWarps * sizeof(double), 256);
+    L.q0part = o; o = align_up(o + (size_t)slots * slot_nqb * kWarps * sizeof(double), 256);
     L.qval = o;   o = align_up(o + (size_t)slots * kQParts * sizeof(double), 256);
     L.q0val = o;  o = align_up(o + (size_t)slots * kQParts * sizeof(double), 256);
     L.unsat = o;  o = align_up(o + 2 * (size_t)slots * sizeof(int), 256);
-    L.sbits = o;  o = align_up(o + (size_t)frames * swords * sizeof(unsigned), 256);
+    L.sbits = o;  o = align_up(o + (size_t)sbits_words * sizeof(unsigned), 256);
     L.new_frame = o; o = align_up(o + (size_t)slots * sizeof(int), 256);
     L.total = o;
     return L;
 }
 
-ldpc_status ensure_workspace(ldpc_graph* g, size_t bytes) {
-    Workspace& ws = g->ws;
+ldpc_status ensure_workspace(Workspace& ws, size_t bytes) {
     if (!ws.ctrl) {
         LDPC_TRY(cudaMalloc(&ws.ctrl, kMaxGroups * sizeof(Ctrl)));
         LDPC_TRY(cudaHostAlloc(&ws.host_err, sizeof(int), cudaHostAllocDefault));
@@ -166,21 +165,83 @@ struct DeviceGuard {
     }
 };
 
+const QcDev& code_of(const ldpc_graph* g, QcDev*) { return g->qc; }
+const CsrDev& code_of(const ldpc_graph* g, CsrDev*) { return g->csr; }
+
+// One decode launch: frames of 1..kMaxCodes codes (graphs of one kind), with
+// optional per-frame device arrays (code index, offsets into the concatenated
+// buffers; NULL = one code, frames back to back).
+struct Job {
+    const ldpc_graph* const* graphs;
+    int ngraphs;
+    int frames;
+    const int* frame_code;       // device [frames] or NULL
+    const long long* var_off;    // device [frames] or NULL
+    const long long* syn_off;    // device [frames] or NULL (syndrome bytes)
+    const long long* sb_off;     // device [frames] or NULL (packed words)
+    long long sbits_words;       // packed syndrome words of all frames
+    int max_slot_frames;         // frames that may run at once (min(frames, ...))
+    const float* llr;
+    const uint8_t* syndrome;
+    uint8_t* bits_out;
+    uint8_t* flags_out;
+    int32_t* iters_out;
+    int max_iter, rule;
+    bool var_unaligned[kMaxCodes];  // some frame of code c starts at an offset not a multiple of 4
+};
+
+// QC item sizes: simulate the static assignment (item it goes to CTA it mod
+// gsize) of one step of the group's slots and take the size whose busiest CTA
+// has the least work (checks or variables times (degree + 1), plus a fixed
+// cost per item).
+void pick_chunks(const ldpc_graph* g, int gsize, int slots_per_group, int* cn_chunk, int* cn_tiles, int* vn_chunk,
+                 int* vn_tiles) {
+    std::vector<long long> load((size_t)gsize);
+    auto pick = [&](const std::vector<int>& deg, const int* cand, int ncand, int* chunk, int* tiles) {
+        long long best = -1;
+        for (int c = 0; c < ncand; ++c) {
+            const int per = (g->Z + cand[c] - 1) / cand[c];
+            std::fill(load.begin(), load.end(), 0LL);
+            long long it = 0;
+            for (int sl = 0; sl < slots_per_group; ++sl)
+                for (int r = 0; r < (int)deg.size(); ++r)
+                    for (int q = 0; q < per; ++q, ++it) {
+                        const int len = std::min(cand[c], g->Z - q * cand[c]);
+                        load[(size_t)(it % gsize)] += (long long)len * (deg[r] + 1) + 2048;
+                    }
+            const long long worst = *std::max_element(load.begin(), load.end());
+            if (best < 0 || worst < best) {
+                best = worst;
+                *chunk = cand[c];
+                *tiles = (int)deg.size() * per;
+            }
+        }
+    };
+    static const int cn_cand[] = {512, 1024, 2048, 4096};
+    static const int vn_cand[] = {1024, 2048, 4096, 8192};
+    pick(g->row_deg, cn_cand, 4, cn_chunk, cn_tiles);
+    pick(g->col_deg, vn_cand, 4, vn_chunk, vn_tiles);
+}
+
+// Synchronous (status_out == NULL): reads the status back and fills stats.
+// Asynchronous: copies the device status word to status_out and returns at
+// once; nothing in it waits for the host, so it can be captured in a graph
+// (the workspace must already be large enough: no allocation while capturing).
 template <typename T, class Code>
-ldpc_status launch_decode(ldpc_graph* g, const Code& code, int frames, const float* llr,
-                          const uint8_t* syndrome, int max_iter, int rule, uint8_t* bits_out,
-                          uint8_t* flags_out, int32_t* iters_out, const ldpc_decode_opts& o,
-                          cudaStream_t stream) {
-    const int swords = (g->m + 31) / 32;
+ldpc_status launch_decode(Workspace& ws, const Job& job, const ldpc_decode_opts& o, cudaStream_t stream,
+                          int32_t* status_out = nullptr) {
+    const int frames = job.frames;
     auto kernel = bp_decode_kernel<T, Code>;
     int dev = 0, sms = 0, per_sm = 0, coop = 0;
     LDPC_TRY(cudaGetDevice(&dev));
     LDPC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     LDPC_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     if (!coop) return LDPC_ERR_CUDA;
-    // occupancy with the largest slot table we may use (24 bytes of shared memory per slot)
-    LDPC_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSlots * 24));
-    LDPC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, kMaxSlots * 24));
+    // occupancy with the largest slot table we may use (28 bytes of shared memory per slot)
+    const auto smem_for = [](int sg) { return (size_t)((sg * 28 + 127) / 128) * 128; };
+    LDPC_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_for(kMaxSlots)));
+    LDPC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads,
+                                                           smem_for(std::min(frames, kMaxSlots))));
     if (per_sm < 1) return LDPC_ERR_CUDA;
     int grid = std::min(per_sm * sms, kMaxGrid);
     if (o.grid_ctas > 0) grid = std::min(grid, o.grid_ctas);
@@ -188,68 +249,84 @@ ldpc_status launch_decode(ldpc_graph* g, const Code& code, int frames, const flo
     // one per frame) and every frame in a slot (measured best at n = 1e6)
     int groups = o.groups > 0 ? o.groups : per_sm;
     int want_slots = o.max_active_frames > 0 ? o.max_active_frames : frames;
-    want_slots = std::min(std::min(want_slots, frames), kMaxSlots);
+    want_slots = std::min(std::min(want_slots, job.max_slot_frames), kMaxSlots);
     groups = std::max(1, std::min(std::min(groups, want_slots), std::min(grid, kMaxGroups)));
     const int slots_per_group = (want_slots + groups - 1) / groups;
     const int slots = groups * slots_per_group;
     grid = (grid / groups) * groups;
-    const size_t smem = (size_t)slots_per_group * (sizeof(double) + 4 * sizeof(int));
-    // QC item sizes: simulate the static assignment (item it goes to CTA it mod
-    // gsize) of one step of the group's slots and take the size whose busiest
-    // CTA has the least work (checks or variables times (degree + 1), plus a
-    // fixed cost per item)
-    int cn_chunk = kQcCnChunk, vn_chunk = kQcVnChunk, cn_tiles = g->cn_tiles, vn_tiles = g->vn_tiles;
-    if (g->kind == 1) {
-        const int gsize = grid / groups;
-        std::vector<long long> load((size_t)gsize);
-        auto pick = [&](const std::vector<int>& deg, const int* cand, int ncand, int* chunk, int* tiles) {
-            long long best = -1;
-            for (int c = 0; c < ncand; ++c) {
-                const int per = (g->Z + cand[c] - 1) / cand[c];
-                std::fill(load.begin(), load.end(), 0LL);
-                long long it = 0;
-                for (int sl = 0; sl < slots_per_group; ++sl)
-                    for (int r = 0; r < (int)deg.size(); ++r)
-                        for (int q = 0; q < per; ++q, ++it) {
-                            const int len = std::min(cand[c], g->Z - q * cand[c]);
-                            load[(size_t)(it % gsize)] += (long long)len * (deg[r] + 1) + 2048;
-                        }
-                const long long worst = *std::max_element(load.begin(), load.end());
-                if (best < 0 || worst < best) {
-                    best = worst;
-                    *chunk = cand[c];
-                    *tiles = (int)deg.size() * per;
-                }
-            }
-        };
-        static const int cn_cand[] = {512, 1024, 2048, 4096};
-        static const int vn_cand[] = {1024, 2048, 4096, 8192};
-        pick(g->row_deg, cn_cand, 4, &cn_chunk, &cn_tiles);
-        pick(g->col_deg, vn_cand, 4, &vn_chunk, &vn_tiles);
+    const size_t smem = smem_for(slots_per_group);
+
+    // per-code sizes; slots are sized for the largest code
+    CodeSet<Code> cs{};
+    cs.count = job.ngraphs;
+    long long slot_E = 0;
+    int slot_n = 0, slot_nqb = 0, cn_max = 0, vn_max = 0;
+    PackInfo pi{};
+    for (int c = 0; c < job.ngraphs; ++c) {
+        const ldpc_graph* g = job.graphs[c];
+        CodeInfo<Code>& ci = cs.c[c];
+        ci.code = code_of(g, (Code*)nullptr);
+        ci.n = g->n;
+        ci.m = g->m;
+        ci.E = g->E;
+        ci.swords = (g->m + 31) / 32;
+        ci.cn_tiles = g->cn_tiles;
+        ci.vn_tiles = g->vn_tiles;
+        ci.cn_chunk = kQcCnChunk;
+        ci.vn_chunk = kQcVnChunk;
+        ci.nqb = g->vn_tiles;
+        ci.vec4 = 0;
+        if (g->kind == 1) {
+            pick_chunks(g, grid / groups, slots_per_group, &ci.cn_chunk, &ci.cn_tiles, &ci.vn_chunk, &ci.vn_tiles);
+            ci.nqb = g->nb * ((g->Z + kQBlock - 1) / kQBlock);
+            // 16-byte variable-side loads: Z % 4 == 0 and every frame's Lch and
+            // decisions 16-byte aligned (the buffer aligned, every frame of the
+            // code at an offset that is a multiple of 4)
+            ci.vec4 = ((g->Z % 4) == 0 && ((uintptr_t)job.llr % 16) == 0 && !job.var_unaligned[c]) ? 1 : 0;
+        }
+        // slot strides rounded up to 64 elements, so every slot's messages and
+        // APP values start 256-byte aligned whatever the codes' sizes
+        slot_E = std::max(slot_E, (long long)align_up((size_t)ci.E, 64));
+        slot_n = std::max(slot_n, (int)align_up((size_t)ci.n, 64));
+        slot_nqb = std::max(slot_nqb, ci.nqb);
+        cn_max = std::max(cn_max, ci.cn_tiles);
+        vn_max = std::max(vn_max, ci.vn_tiles);
+        pi.m[c] = ci.m;
+        pi.swords[c] = ci.swords;
     }
-    const int nqb = g->kind == 1 ? g->nb * ((g->Z + kQBlock - 1) / kQBlock) : g->vn_tiles;
-    const Layout L = make_layout(g, slots, sizeof(T), frames, swords, nqb);
-    ldpc_status st = ensure_workspace(g, L.total);
+    pi.frame_code = job.frame_code;
+    pi.syn_off = job.syn_off;
+    pi.sb_off = job.sb_off;
+
+    const Layout L = make_layout(slots, sizeof(T), slot_E, slot_n, slot_nqb, job.sbits_words);
+    cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+    LDPC_TRY(cudaStreamIsCapturing(stream, &capturing));
+    if (capturing != cudaStreamCaptureStatusNone && (ws.cap < L.total || !ws.ctrl))
+        return LDPC_ERR_INVALID_ARG;  // run one decode of this size before capturing it
+    ldpc_status st = ensure_workspace(ws, L.total);
     if (st != LDPC_OK) return st;
-    Workspace& ws = g->ws;
     char* base = (char*)ws.buf;
 
     Params<T> p{};
-    p.m = g->m;
-    p.n = g->n;
-    p.E = g->E;
     p.frames = frames;
-    p.max_iter = max_iter;
-    p.rule = rule;
+    p.max_iter = job.max_iter;
+    p.rule = job.rule;
     p.vnr_first_iter = o.vnr_first_iter;
     p.lmax = T(o.clamp);
-    p.llr = llr;
+    p.frame_code = job.frame_code;
+    p.var_off = job.var_off;
+    p.sb_off = job.sb_off;
+    p.llr = job.llr;
     p.sbits = (const unsigned*)(base + L.sbits);
-    p.swords = swords;
-    p.bits_out = bits_out;
-    p.flags_out = flags_out;
-    p.iters_out = iters_out;
+    p.bits_out = job.bits_out;
+    p.flags_out = job.flags_out;
+    p.iters_out = job.iters_out;
     p.slots = slots;
+    p.slot_E = slot_E;
+    p.slot_n = slot_n;
+    p.slot_nqb = slot_nqb;
+    p.cn_tiles_max = cn_max;
+    p.vn_tiles_max = vn_max;
     p.c2v = (T*)(base + L.c2v);
     p.app = (T*)(base + L.app);
     p.qpart = (double*)(base + L.qpart);
@@ -258,46 +335,45 @@ ldpc_status launch_decode(ldpc_graph* g, const Code& code, int frames, const flo
     p.q0val = (double*)(base + L.q0val);
     p.unsat = (int*)(base + L.unsat);
     p.ctrl = ws.ctrl;
-    p.cn_tiles = cn_tiles;
-    p.vn_tiles = vn_tiles;
-    p.cn_chunk = cn_chunk;
-    p.vn_chunk = vn_chunk;
-    p.nqb = nqb;
     p.trace_iters = o.trace_iters;
     p.trace_c2v = (T*)o.trace_c2v;
     p.trace_app = (T*)o.trace_app;
     p.trace_q = o.trace_q;
     p.timeout_ns = o.barrier_timeout_ms > 0 ? (unsigned long long)o.barrier_timeout_ms * 1000000ull
                                             : kBarrierTimeoutNs;
-    p.vec4 = (g->kind == 1 && (g->Z % 4) == 0 && ((uintptr_t)llr % 16) == 0) ? 1 : 0;
     p.bar_extra = o.test_unreachable_barrier ? 1u : 0u;
     p.groups = groups;
     p.slots_per_group = slots_per_group;
     p.new_frame = (int*)(base + L.new_frame);
 
-    const bool timing = o.stats != nullptr;
+    const bool timing = o.stats != nullptr && status_out == nullptr;
     if (timing) LDPC_TRY(cudaEventRecord(ws.ev[0], stream));
-    {
-        // group barriers cleared; the queue of waiting frames starts after the first `slots`
-        Ctrl c0[kMaxGroups] = {};
-        c0[0].next_frame = std::min(slots, frames);
-        LDPC_TRY(cudaMemcpyAsync(ws.ctrl, c0, (size_t)groups * sizeof(Ctrl), cudaMemcpyHostToDevice, stream));
-    }
-    LDPC_TRY(cudaMemsetAsync(p.unsat, 0, 2 * (size_t)slots * sizeof(int), stream));
-    {
-        const long long warps = (long long)frames * swords;
-        long long blocks = (warps * 32 + 255) / 256;
-        blocks = std::max(1LL, std::min(blocks, (long long)sms * 8));
-        pack_syndrome_kernel<<<(unsigned)blocks, 256, 0, stream>>>(syndrome, frames, g->m, swords,
-                                                                   (unsigned*)(base + L.sbits), ws.ctrl);
-        LDPC_TRY(cudaGetLastError());
-    }
+    // group barriers cleared; the queue of waiting frames starts after the first `slots`
+    init_ctrl_kernel<<<1, 256, 0, stream>>>(ws.ctrl, groups, std::min(slots, frames), p.unsat, 2 * slots);
+    LDPC_TRY(cudaGetLastError());
+    pack_syndrome_kernel<<<(unsigned)std::max(1, std::min(frames, sms * 8)), 256, 0, stream>>>(
+        job.syndrome, frames, pi, (unsigned*)(base + L.sbits), ws.ctrl);
+    LDPC_TRY(cudaGetLastError());
     if (timing) LDPC_TRY(cudaEventRecord(ws.ev[1], stream));
     {
-        void* args[] = {(void*)&p, (void*)&code};
-        LDPC_TRY(cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(kThreads), args, smem, stream));
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs resident: the group barriers need it
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        LDPC_TRY(cudaLaunchKernelEx(&cfg, kernel, p, cs));
     }
     if (timing) LDPC_TRY(cudaEventRecord(ws.ev[2], stream));
+    if (status_out) {
+        status_kernel<<<1, 1, 0, stream>>>(ws.ctrl, status_out);
+        LDPC_TRY(cudaGetLastError());
+        return LDPC_OK;
+    }
     LDPC_TRY(cudaMemcpyAsync(ws.host_err, &ws.ctrl->err, sizeof(int), cudaMemcpyDeviceToHost, stream));
     LDPC_TRY(cudaMemcpyAsync(ws.host_iters, &ws.ctrl->frame_iters, sizeof(unsigned long long),
                              cudaMemcpyDeviceToHost, stream));
@@ -305,19 +381,40 @@ ldpc_status launch_decode(ldpc_graph* g, const Code& code, int frames, const flo
     LDPC_TRY(cudaStreamSynchronize(stream));
     const int err = *ws.host_err;
     if (timing) {
-        ldpc_decode_stats* s = o.stats;
-        cudaEventElapsedTime(&s->kernel_ms, ws.ev[1], ws.ev[2]);
-        cudaEventElapsedTime(&s->total_ms, ws.ev[0], ws.ev[3]);
-        s->kernel_launches = 2;
-        s->grid_ctas = grid;
-        s->threads_per_cta = kThreads;
-        s->active_frames = slots;
-        s->frame_iterations = (int64_t)*ws.host_iters;
+        ldpc_decode_stats* sst = o.stats;
+        cudaEventElapsedTime(&sst->kernel_ms, ws.ev[1], ws.ev[2]);
+        cudaEventElapsedTime(&sst->total_ms, ws.ev[0], ws.ev[3]);
+        sst->kernel_launches = 3;
+        sst->grid_ctas = grid;
+        sst->threads_per_cta = kThreads;
+        sst->active_frames = slots;
+        sst->frame_iterations = (int64_t)*ws.host_iters;
     }
     if (err == kErrSyndrome) return LDPC_ERR_INVALID_ARG;
     if (err == kErrTimeout) return LDPC_ERR_TIMEOUT;
     if (err != kErrNone) return LDPC_ERR_CUDA;
     return LDPC_OK;
+}
+
+template <typename T, class Code>
+ldpc_status launch_single(ldpc_graph* g, int frames, const float* llr, const uint8_t* syndrome, int max_iter,
+                          int rule, uint8_t* bits_out, uint8_t* flags_out, int32_t* iters_out,
+                          const ldpc_decode_opts& o, cudaStream_t stream) {
+    const ldpc_graph* gs[1] = {g};
+    Job job{};
+    job.graphs = gs;
+    job.ngraphs = 1;
+    job.frames = frames;
+    job.sbits_words = (long long)frames * ((g->m + 31) / 32);
+    job.max_slot_frames = frames;
+    job.llr = llr;
+    job.syndrome = syndrome;
+    job.bits_out = bits_out;
+    job.flags_out = flags_out;
+    job.iters_out = iters_out;
+    job.max_iter = max_iter;
+    job.rule = rule;
+    return launch_decode<T, Code>(g->ws, job, o, stream);
 }
 
 ldpc_status check_decode_args(const ldpc_graph* graph, int32_t frames, const void* llr, const void* syndrome,
@@ -506,16 +603,16 @@ ldpc_status ldpc_decode(const ldpc_graph* graph, int32_t frames, const float* ll
     cudaStream_t stream = (cudaStream_t)cuda_stream;
     if (g->kind == 1) {
         if (o.fp64)
-            return launch_decode<double>(g, g->qc, frames, llr, syndrome, max_iter, (int)rule, bits_out, flags_out,
-                                         iters_out, o, stream);
-        return launch_decode<float>(g, g->qc, frames, llr, syndrome, max_iter, (int)rule, bits_out, flags_out,
-                                    iters_out, o, stream);
+            return launch_single<double, QcDev>(g, frames, llr, syndrome, max_iter, (int)rule, bits_out, flags_out,
+                                                iters_out, o, stream);
+        return launch_single<float, QcDev>(g, frames, llr, syndrome, max_iter, (int)rule, bits_out, flags_out,
+                                           iters_out, o, stream);
     }
     if (o.fp64)
-        return launch_decode<double>(g, g->csr, frames, llr, syndrome, max_iter, (int)rule, bits_out, flags_out,
-                                     iters_out, o, stream);
-    return launch_decode<float>(g, g->csr, frames, llr, syndrome, max_iter, (int)rule, bits_out, flags_out,
-                                iters_out, o, stream);
+        return launch_single<double, CsrDev>(g, frames, llr, syndrome, max_iter, (int)rule, bits_out, flags_out,
+                                             iters_out, o, stream);
+    return launch_single<float, CsrDev>(g, frames, llr, syndrome, max_iter, (int)rule, bits_out, flags_out,
+                                        iters_out, o, stream);
 }
 
 ldpc_status ldpc_decode_host(const ldpc_graph* graph, int32_t frames, const float* llr, const uint8_t* syndrome,
@@ -558,6 +655,235 @@ ldpc_status ldpc_decode_host(const ldpc_graph* graph, int32_t frames, const floa
     LDPC_TRY(cudaMemcpyAsync(iters_out, d + o_iters, (size_t)frames * sizeof(int32_t), cudaMemcpyDeviceToHost,
                              stream));
     LDPC_TRY(cudaStreamSynchronize(stream));
+    return LDPC_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of frames of several codes (ldpc_batch_*).
+// ---------------------------------------------------------------------------
+struct ldpc_batch {
+    std::vector<const ldpc_graph*> graphs;
+    int kind = 0, device = 0, frames = 0, max_slot_frames = 0;
+    void* dmem = nullptr;            // frame_code | var_off | syn_off | sb_off
+    const int* frame_code = nullptr;
+    const long long* var_off = nullptr;
+    const long long* syn_off = nullptr;
+    const long long* sb_off = nullptr;
+    long long llr_len = 0, syn_len = 0, sb_words = 0;
+    bool var_unaligned[kMaxCodes] = {};     // a frame of code c starts at an offset not a multiple of 4
+    int tuned_groups = 0, tuned_slots = 0;  // from ldpc_batch_autotune (0 = none)
+    Workspace ws;
+};
+
+namespace {
+
+ldpc_decode_opts batch_opts(const ldpc_batch* b, const ldpc_decode_opts* opts) {
+    ldpc_decode_opts o;
+    ldpc_decode_opts_init(&o);
+    if (opts) o = *opts;
+    if (o.groups == 0) o.groups = b->tuned_groups;
+    if (o.max_active_frames == 0) o.max_active_frames = b->tuned_slots;
+    return o;
+}
+
+ldpc_status batch_launch(ldpc_batch* b, const float* llr, const uint8_t* syndrome, int32_t max_iter,
+                         ldpc_term_rule rule, uint8_t* bits_out, uint8_t* flags_out, int32_t* iters_out,
+                         const ldpc_decode_opts& o, cudaStream_t stream, int32_t* status_out) {
+    Job job{};
+    job.graphs = b->graphs.data();
+    job.ngraphs = (int)b->graphs.size();
+    job.frames = b->frames;
+    job.frame_code = b->frame_code;
+    job.var_off = b->var_off;
+    job.syn_off = b->syn_off;
+    job.sb_off = b->sb_off;
+    job.sbits_words = b->sb_words;
+    job.max_slot_frames = b->max_slot_frames;
+    job.llr = llr;
+    job.syndrome = syndrome;
+    job.bits_out = bits_out;
+    job.flags_out = flags_out;
+    job.iters_out = iters_out;
+    job.max_iter = max_iter;
+    job.rule = (int)rule;
+    for (int c = 0; c < kMaxCodes; ++c) job.var_unaligned[c] = b->var_unaligned[c];
+    if (b->kind == 1) {
+        if (o.fp64) return launch_decode<double, QcDev>(b->ws, job, o, stream, status_out);
+        return launch_decode<float, QcDev>(b->ws, job, o, stream, status_out);
+    }
+    if (o.fp64) return launch_decode<double, CsrDev>(b->ws, job, o, stream, status_out);
+    return launch_decode<float, CsrDev>(b->ws, job, o, stream, status_out);
+}
+
+ldpc_status check_batch_args(const ldpc_batch* b, const void* llr, const void* syndrome, int32_t max_iter,
+                             int rule, const void* bits, const void* flags, const void* iters,
+                             const ldpc_decode_opts& o) {
+    if (!b) return LDPC_ERR_INVALID_ARG;
+    if (o.trace_iters > 0 || o.trace_c2v || o.trace_app || o.trace_q) return LDPC_ERR_INVALID_ARG;
+    return check_decode_args(b->graphs[0], b->frames, llr, syndrome, max_iter, rule, bits, flags, iters, o);
+}
+
+}  // namespace
+
+extern "C" {
+
+ldpc_status ldpc_batch_create(const ldpc_graph* const* graphs, int32_t n_graphs, int32_t frames,
+                              const int32_t* frame_graph, ldpc_batch** out) {
+    if (!out) return LDPC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!graphs || n_graphs < 1 || n_graphs > kMaxCodes || frames < 1 || !frame_graph) return LDPC_ERR_INVALID_ARG;
+    for (int c = 0; c < n_graphs; ++c) {
+        if (!graphs[c] || graphs[c]->kind != graphs[0]->kind || graphs[c]->device != graphs[0]->device)
+            return LDPC_ERR_INVALID_ARG;
+    }
+    std::vector<int> code(frames);
+    std::vector<long long> var_off(frames), syn_off(frames), sb_off(frames);
+    long long vo = 0, so = 0, wo = 0;
+    for (int f = 0; f < frames; ++f) {
+        const int c = frame_graph[f];
+        if (c < 0 || c >= n_graphs) return LDPC_ERR_INVALID_ARG;
+        code[f] = c;
+        var_off[f] = vo;
+        syn_off[f] = so;
+        sb_off[f] = wo;
+        vo += graphs[c]->n;
+        so += graphs[c]->m;
+        wo += (graphs[c]->m + 31) / 32;
+    }
+    ldpc_batch* b = new (std::nothrow) ldpc_batch();
+    if (!b) return LDPC_ERR_OOM;
+    b->graphs.assign(graphs, graphs + n_graphs);
+    b->kind = graphs[0]->kind;
+    b->device = graphs[0]->device;
+    b->frames = frames;
+    b->max_slot_frames = frames;
+    b->llr_len = vo;
+    b->syn_len = so;
+    b->sb_words = wo;
+    for (int f = 0; f < frames; ++f)
+        if (var_off[f] % 4 != 0) b->var_unaligned[code[f]] = true;
+    DeviceGuard guard;
+    cudaError_t ce = guard.enter(b->device);
+    const size_t bytes = align_up((size_t)frames * sizeof(int), 256) + 3 * align_up((size_t)frames * 8, 256);
+    if (ce == cudaSuccess) ce = cudaMalloc(&b->dmem, bytes);
+    if (ce != cudaSuccess) {
+        delete b;
+        return cuda_status(ce);
+    }
+    char* d = (char*)b->dmem;
+    const size_t o1 = align_up((size_t)frames * sizeof(int), 256), ob = align_up((size_t)frames * 8, 256);
+    b->frame_code = (const int*)d;
+    b->var_off = (const long long*)(d + o1);
+    b->syn_off = (const long long*)(d + o1 + ob);
+    b->sb_off = (const long long*)(d + o1 + 2 * ob);
+    ce = cudaMemcpy(d, code.data(), (size_t)frames * sizeof(int), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(d + o1, var_off.data(), (size_t)frames * 8, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(d + o1 + ob, syn_off.data(), (size_t)frames * 8, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpy(d + o1 + 2 * ob, sb_off.data(), (size_t)frames * 8, cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) {
+        cudaFree(b->dmem);
+        delete b;
+        return cuda_status(ce);
+    }
+    *out = b;
+    return LDPC_OK;
+}
+
+void ldpc_batch_destroy(ldpc_batch* b) {
+    if (!b) return;
+    DeviceGuard guard;
+    guard.enter(b->device);
+    free_workspace(b->ws);
+    if (b->dmem) cudaFree(b->dmem);
+    delete b;
+}
+
+ldpc_status ldpc_batch_info(const ldpc_batch* b, int32_t* frames, int64_t* llr_len, int64_t* syndrome_len) {
+    if (!b) return LDPC_ERR_INVALID_ARG;
+    if (frames) *frames = b->frames;
+    if (llr_len) *llr_len = b->llr_len;
+    if (syndrome_len) *syndrome_len = b->syn_len;
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_batch_decode(ldpc_batch* b, const float* llr, const uint8_t* syndrome, int32_t max_iter,
+                              ldpc_term_rule rule, uint8_t* bits_out, uint8_t* flags_out, int32_t* iters_out,
+                              const ldpc_decode_opts* opts, void* cuda_stream) {
+    if (!b) return LDPC_ERR_INVALID_ARG;
+    const ldpc_decode_opts o = batch_opts(b, opts);
+    ldpc_status st = check_batch_args(b, llr, syndrome, max_iter, (int)rule, bits_out, flags_out, iters_out, o);
+    if (st != LDPC_OK) return st;
+    DeviceGuard guard;
+    LDPC_TRY(guard.enter(b->device));
+    return batch_launch(b, llr, syndrome, max_iter, rule, bits_out, flags_out, iters_out, o,
+                        (cudaStream_t)cuda_stream, nullptr);
+}
+
+ldpc_status ldpc_batch_decode_async(ldpc_batch* b, const float* llr, const uint8_t* syndrome, int32_t max_iter,
+                                    ldpc_term_rule rule, uint8_t* bits_out, uint8_t* flags_out, int32_t* iters_out,
+                                    int32_t* status_out, const ldpc_decode_opts* opts, void* cuda_stream) {
+    if (!b || !status_out) return LDPC_ERR_INVALID_ARG;
+    ldpc_decode_opts o = batch_opts(b, opts);
+    o.stats = nullptr;
+    ldpc_status st = check_batch_args(b, llr, syndrome, max_iter, (int)rule, bits_out, flags_out, iters_out, o);
+    if (st != LDPC_OK) return st;
+    DeviceGuard guard;
+    LDPC_TRY(guard.enter(b->device));
+    return batch_launch(b, llr, syndrome, max_iter, rule, bits_out, flags_out, iters_out, o,
+                        (cudaStream_t)cuda_stream, status_out);
+}
+
+ldpc_status ldpc_batch_autotune(ldpc_batch* b, const float* llr, const uint8_t* syndrome, int32_t max_iter,
+                                ldpc_term_rule rule, uint8_t* bits_out, uint8_t* flags_out, int32_t* iters_out,
+                                void* cuda_stream, int32_t* best_groups, int32_t* best_slots) {
+    if (!b) return LDPC_ERR_INVALID_ARG;
+    ldpc_decode_opts o;
+    ldpc_decode_opts_init(&o);
+    ldpc_status st = check_batch_args(b, llr, syndrome, max_iter, (int)rule, bits_out, flags_out, iters_out, o);
+    if (st != LDPC_OK) return st;
+    DeviceGuard guard;
+    LDPC_TRY(guard.enter(b->device));
+    int dev = 0, per_sm = 0;
+    LDPC_TRY(cudaGetDevice(&dev));
+    LDPC_TRY(cudaDeviceGetAttribute(&per_sm, cudaDevAttrMultiProcessorCount, dev));
+    // candidates: groups in {1, 2, 4, 8}; slots in {all frames, 8 per group, 2 per group}
+    const int F = std::min(b->frames, kMaxSlots);
+    float best_ms = -1.0f;
+    int bg = 0, bs = 0;
+    // one untimed decode at the largest slot count first: sizes the workspace
+    // and warms caches and clocks, so the first candidate is not timed cold
+    o.groups = 1;
+    o.max_active_frames = F;
+    st = batch_launch(b, llr, syndrome, max_iter, rule, bits_out, flags_out, iters_out, o, (cudaStream_t)cuda_stream,
+                      nullptr);
+    if (st != LDPC_OK) return st;
+    const int gcand[] = {1, 2, 4, 8};
+    for (int gi = 0; gi < 4; ++gi) {
+        const int gcount = gcand[gi];
+        const int scand[] = {F, std::min(F, 8 * gcount), std::min(F, 2 * gcount)};
+        for (int si = 0; si < 3; ++si) {
+            if (si > 0 && scand[si] == scand[si - 1]) continue;
+            ldpc_decode_stats stats{};
+            o.groups = gcount;
+            o.max_active_frames = scand[si];
+            o.stats = &stats;
+            st = batch_launch(b, llr, syndrome, max_iter, rule, bits_out, flags_out, iters_out, o,
+                              (cudaStream_t)cuda_stream, nullptr);
+            if (st != LDPC_OK) return st;
+            if (best_ms < 0.0f || stats.kernel_ms < best_ms) {
+                best_ms = stats.kernel_ms;
+                bg = gcount;
+                bs = scand[si];
+            }
+        }
+    }
+    b->tuned_groups = bg;
+    b->tuned_slots = bs;
+    if (best_groups) *best_groups = bg;
+    if (best_slots) *best_slots = bs;
     return LDPC_OK;
 }
 
@@ -709,10 +1035,22 @@ extern "C" ldpc_status ldpc_decode_qc_noalloc(int32_t mb, int32_t nb, int32_t Z,
     LDPC_TRY(cudaMemcpyAsync(ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, stream));
     LDPC_TRY(cudaMemsetAsync(base + L.unsat, 0, 2 * (size_t)slots * sizeof(int), stream));
 
+    CodeSet<QcDev> cs{};
+    cs.count = 1;
+    CodeInfo<QcDev>& ci = cs.c[0];
+    ci.code = code;
+    ci.n = n;
+    ci.m = m;
+    ci.E = E;
+    ci.swords = swords;
+    ci.cn_tiles = cn_tiles;
+    ci.vn_tiles = vn_tiles;
+    ci.cn_chunk = kQcCnChunk;
+    ci.vn_chunk = kQcVnChunk;
+    ci.nqb = nqb;
+    ci.vec4 = ((Z % 4) == 0 && ((uintptr_t)llr % 16) == 0) ? 1 : 0;
+
     Params<float> p{};
-    p.m = m;
-    p.n = n;
-    p.E = E;
     p.frames = frames;
     p.max_iter = max_iter;
     p.rule = (int)rule;
@@ -720,11 +1058,15 @@ extern "C" ldpc_status ldpc_decode_qc_noalloc(int32_t mb, int32_t nb, int32_t Z,
     p.lmax = 25.0f;
     p.llr = llr;
     p.sbits = (const unsigned*)(base + L.sbits);
-    p.swords = swords;
     p.bits_out = bits_out;
     p.flags_out = flags_out;
     p.iters_out = iters_out;
     p.slots = slots;
+    p.slot_E = E;
+    p.slot_n = n;
+    p.slot_nqb = nqb;
+    p.cn_tiles_max = cn_tiles;
+    p.vn_tiles_max = vn_tiles;
     p.c2v = (float*)(base + L.c2v);
     p.app = (float*)(base + L.app);
     p.qpart = (double*)(base + L.qpart);
@@ -733,26 +1075,20 @@ extern "C" ldpc_status ldpc_decode_qc_noalloc(int32_t mb, int32_t nb, int32_t Z,
     p.q0val = (double*)(base + L.q0val);
     p.unsat = (int*)(base + L.unsat);
     p.ctrl = ctrl;
-    p.cn_tiles = cn_tiles;
-    p.vn_tiles = vn_tiles;
     p.trace_iters = 0;
     p.timeout_ns = kBarrierTimeoutNs;
-    p.vec4 = ((Z % 4) == 0 && ((uintptr_t)llr % 16) == 0) ? 1 : 0;
     p.groups = 1;
     p.slots_per_group = slots;
-    p.cn_chunk = kQcCnChunk;
-    p.vn_chunk = kQcVnChunk;
-    p.nqb = nqb;
     p.new_frame = (int*)(base + L.new_frame);
     {
-        const long long warps = (long long)frames * swords;
-        long long blocks = (warps * 32 + 255) / 256;
-        blocks = std::max(1LL, std::min(blocks, (long long)sms * 8));
-        pack_syndrome_kernel<<<(unsigned)blocks, 256, 0, stream>>>(syndrome, frames, m, swords,
-                                                                   (unsigned*)(base + L.sbits), ctrl);
+        PackInfo pi{};
+        pi.m[0] = m;
+        pi.swords[0] = swords;
+        pack_syndrome_kernel<<<(unsigned)std::max(1, std::min(frames, sms * 8)), 256, 0, stream>>>(
+            syndrome, frames, pi, (unsigned*)(base + L.sbits), ctrl);
         LDPC_TRY(cudaGetLastError());
     }
-    void* args[] = {(void*)&p, (void*)&code};
+    void* args[] = {(void*)&p, (void*)&cs};
     LDPC_TRY(cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(kThreads), args, smem, stream));
     int err = 0;
     LDPC_TRY(cudaMemcpyAsync(&err, &ctrl->err, sizeof(int), cudaMemcpyDeviceToHost, stream));

@@ -38,7 +38,8 @@ RULES = {"none": LDPC_TERM_NONE, "pce": LDPC_TERM_PCE, "pce_vnr": LDPC_TERM_PCE_
 
 EXPORTED = ("ldpc_decode_opts_init", "ldpc_graph_create_csr", "ldpc_graph_create_qc",
             "ldpc_graph_destroy", "ldpc_graph_info", "ldpc_decode", "ldpc_decode_host",
-            "ldpc_status_str", "ldpc_decode_qc_noalloc")
+            "ldpc_status_str", "ldpc_decode_qc_noalloc", "ldpc_batch_create", "ldpc_batch_destroy",
+            "ldpc_batch_info", "ldpc_batch_decode", "ldpc_batch_decode_async", "ldpc_batch_autotune")
 
 NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 
@@ -86,6 +87,20 @@ def _load():
     lib.ldpc_status_str.restype = ctypes.c_char_p
     lib.ldpc_decode_qc_noalloc.argtypes = [i32, i32, i32, P, i32, P, P, i32, ctypes.c_int, P, P, P, P]
     lib.ldpc_decode_qc_noalloc.restype = ctypes.c_int
+    lib.ldpc_batch_create.argtypes = [P, i32, i32, P, pg]
+    lib.ldpc_batch_create.restype = ctypes.c_int
+    lib.ldpc_batch_destroy.argtypes = [P]
+    lib.ldpc_batch_destroy.restype = None
+    lib.ldpc_batch_info.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    lib.ldpc_batch_info.restype = ctypes.c_int
+    lib.ldpc_batch_decode.argtypes = [P, P, P, i32, ctypes.c_int, P, P, P, ctypes.POINTER(ldpc_decode_opts), P]
+    lib.ldpc_batch_decode.restype = ctypes.c_int
+    lib.ldpc_batch_decode_async.argtypes = [P, P, P, i32, ctypes.c_int, P, P, P, P,
+                                            ctypes.POINTER(ldpc_decode_opts), P]
+    lib.ldpc_batch_decode_async.restype = ctypes.c_int
+    lib.ldpc_batch_autotune.argtypes = [P, P, P, i32, ctypes.c_int, P, P, P, P, ctypes.POINTER(i32),
+                                        ctypes.POINTER(i32)]
+    lib.ldpc_batch_autotune.restype = ctypes.c_int
     return lib
 
 
@@ -278,3 +293,100 @@ def decode_host(graph: Graph, llr: np.ndarray, syndrome: np.ndarray, max_iter: i
                           bits.ctypes.data, flags.ctypes.data, iters.ctypes.data, o, stream)
     _check(st, "ldpc_decode_host")
     return bits, flags, iters
+
+
+# --------------------------------------------------------------------------
+# Batches of frames of several codes
+# --------------------------------------------------------------------------
+def ldpc_batch_create(graph_handles, frame_graph) -> int:
+    arr = (ctypes.c_void_p * len(graph_handles))(*graph_handles)
+    fg = np.ascontiguousarray(frame_graph, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(_lib.ldpc_batch_create(arr, len(graph_handles), fg.size, fg.ctypes.data, ctypes.byref(h)),
+           "ldpc_batch_create")
+    return h.value
+
+
+def ldpc_batch_destroy(handle: int) -> None:
+    _lib.ldpc_batch_destroy(handle)
+
+
+def ldpc_batch_info(handle: int):
+    f, a, b = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+    _check(_lib.ldpc_batch_info(handle, ctypes.byref(f), ctypes.byref(a), ctypes.byref(b)), "ldpc_batch_info")
+    return f.value, a.value, b.value
+
+
+def ldpc_batch_decode(handle, llr_ptr, syndrome_ptr, max_iter, rule, bits_ptr, flags_ptr, iters_ptr, opts,
+                      stream) -> int:
+    return _lib.ldpc_batch_decode(handle, llr_ptr, syndrome_ptr, int(max_iter), int(rule), bits_ptr, flags_ptr,
+                                  iters_ptr, ctypes.byref(opts) if opts is not None else None, stream)
+
+
+def ldpc_batch_decode_async(handle, llr_ptr, syndrome_ptr, max_iter, rule, bits_ptr, flags_ptr, iters_ptr,
+                            status_ptr, opts, stream) -> int:
+    return _lib.ldpc_batch_decode_async(handle, llr_ptr, syndrome_ptr, int(max_iter), int(rule), bits_ptr,
+                                        flags_ptr, iters_ptr, status_ptr,
+                                        ctypes.byref(opts) if opts is not None else None, stream)
+
+
+def ldpc_batch_autotune(handle, llr_ptr, syndrome_ptr, max_iter, rule, bits_ptr, flags_ptr, iters_ptr, stream):
+    g, s = ctypes.c_int32(), ctypes.c_int32()
+    _check(_lib.ldpc_batch_autotune(handle, llr_ptr, syndrome_ptr, int(max_iter), int(rule), bits_ptr, flags_ptr,
+                                    iters_ptr, stream, ctypes.byref(g), ctypes.byref(s)), "ldpc_batch_autotune")
+    return g.value, s.value
+
+
+class Batch:
+    """Frames of up to four codes decoded together (owns an ldpc_batch plan).
+    Buffers hold the frames back to back: llr / bits [llr_len], syndrome
+    [syndrome_len], flags / iters [frames]."""
+
+    def __init__(self, graphs, frame_graph):
+        self.graphs = list(graphs)  # keep the graphs alive
+        self.handle = ldpc_batch_create([g.handle for g in self.graphs], frame_graph)
+        self.frames, self.llr_len, self.syndrome_len = ldpc_batch_info(self.handle)
+
+    def _out(self, device):
+        import torch
+        return (torch.empty(self.llr_len, dtype=torch.uint8, device=device),
+                torch.empty(self.frames, dtype=torch.uint8, device=device),
+                torch.empty(self.frames, dtype=torch.int32, device=device))
+
+    def decode(self, llr, syndrome, max_iter, rule="pce_vnr", out=None, stream=None, **opt):
+        import torch
+        rule = RULES[rule] if isinstance(rule, str) else int(rule)
+        out = out or self._out(llr.device)
+        s = stream if stream is not None else torch.cuda.current_stream(llr.device)
+        _check(ldpc_batch_decode(self.handle, llr.data_ptr(), syndrome.data_ptr(), max_iter, rule,
+                                 out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr(), make_opts(**opt),
+                                 s.cuda_stream), "ldpc_batch_decode")
+        return out
+
+    def decode_async(self, llr, syndrome, max_iter, rule, out, status, stream=None, **opt):
+        """Stream-ordered; writes the ldpc_status code to the device int32 tensor `status`."""
+        import torch
+        rule = RULES[rule] if isinstance(rule, str) else int(rule)
+        s = stream if stream is not None else torch.cuda.current_stream(llr.device)
+        _check(ldpc_batch_decode_async(self.handle, llr.data_ptr(), syndrome.data_ptr(), max_iter, rule,
+                                       out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr(), status.data_ptr(),
+                                       make_opts(**opt), s.cuda_stream), "ldpc_batch_decode_async")
+
+    def autotune(self, llr, syndrome, max_iter, rule="pce_vnr", out=None, stream=None):
+        import torch
+        rule = RULES[rule] if isinstance(rule, str) else int(rule)
+        out = out or self._out(llr.device)
+        s = stream if stream is not None else torch.cuda.current_stream(llr.device)
+        return ldpc_batch_autotune(self.handle, llr.data_ptr(), syndrome.data_ptr(), max_iter, rule,
+                                   out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr(), s.cuda_stream)
+
+    def close(self):
+        if self.handle:
+            ldpc_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
