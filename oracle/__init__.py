@@ -8,13 +8,23 @@ nothing from the product package.
 The arithmetic lives in ``bp_oracle.c`` (plain C, FP64, OpenMP over frames);
 this module compiles it with gcc on first use and marshals arguments.
 
-Parity status of each function (what pins it, tests/test_oracle_pins.py):
+The weighted-BP reference (weights per iteration and edge class, T unrolled
+iterations, binary cross-entropy loss and its exact reverse-mode gradient)
+lives in ``wbp_oracle.c`` and is built the same way into its own library.
+
+Parity status of each function (what pins it, tests/test_oracle_pins.py and
+tests/test_wbp_oracle_pins.py):
   decode  -- pinned: brute-force bitwise MAP marginals on cycle-free graphs,
              closed forms of degree-1 and degree-2 checks, a hand-solved
              3-cycle with an unsatisfiable syndrome (APP values, q sequence,
              VNR abort iteration), channel/syndrome sign symmetry, zero
              syndrome on every success (independent GF(2) product), the
              noise-free limit.
+  wbp     -- pinned: unit weights reproduce decode()'s APP after T
+             iterations; the gradient equals central finite differences of the
+             loss (eps 1e-6) for every weight and for sampled channel values;
+             all-zero weights give APP = Lch and a gradient written out by hand
+             in the test; sign symmetry of loss and gradient (bit-exact).
 """
 from __future__ import annotations
 
@@ -35,16 +45,27 @@ RULE_NONE, RULE_PCE, RULE_PCE_VNR = 0, 1, 2
 FLAG_SUCCESS, FLAG_ABORTED = 1, 2
 
 
-def build(force: bool = False) -> str:
-    """Compile bp_oracle.c into _bp_oracle.so (gcc, OpenMP, no FP contraction)."""
-    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-        return _LIB
-    tmp = _LIB + f".{os.getpid()}.tmp"
+_WSRC = os.path.join(_HERE, "wbp_oracle.c")
+_WLIB = os.path.join(_HERE, "_wbp_oracle.so")
+_wlib = None
+
+
+def _compile(src: str, lib: str, force: bool) -> str:
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= os.path.getmtime(src):
+        return lib
+    tmp = lib + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+           "-fno-fast-math", src, "-o", tmp, "-lm"]
     subprocess.run(cmd, check=True)
-    os.replace(tmp, _LIB)
-    return _LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+def build(force: bool = False) -> str:
+    """Compile bp_oracle.c and wbp_oracle.c into their libraries (gcc, OpenMP,
+    no FP contraction); returns the decoder library's path."""
+    _compile(_WSRC, _WLIB, force)
+    return _compile(_SRC, _LIB, force)
 
 
 def _load():
@@ -116,4 +137,62 @@ def decode(code, llr, syndrome, max_iter: int, rule: int = RULE_PCE_VNR,
     for key, arr in (("c2v", tc), ("app", ta), ("q", tq)):
         if arr is not None:
             out[key] = arr
+    return out
+
+
+def _load_wbp():
+    global _wlib
+    with _lock:
+        if _wlib is None:
+            _wlib = _bind_wbp(ctypes.CDLL(_compile(_WSRC, _WLIB, False)))
+    return _wlib
+
+
+def _bind_wbp(lib):
+    P = ctypes.c_void_p
+    i64, i32, dbl = ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    lib.oracle_wbp.argtypes = [i64, i64, P, P, i64, P, P, P, i32, i32, P, P, dbl, P, P, P, P, i32]
+    lib.oracle_wbp.restype = ctypes.c_int
+    return lib
+
+
+def wbp(code, llr, syndrome, x, iters: int, edge_class, weights, lmax: float = 25.0, grad: bool = True,
+        threads: int = 0, lib=None):
+    """Weighted BP over T = iters unrolled iterations, loss and gradient (FP64).
+
+    code: m, n, rowptr, colidx (check-major CSR); llr float32 [F, n];
+    syndrome uint8 [F, m]; x uint8 [F, n] (the bits the loss compares with);
+    edge_class int [E] in CSR edge order; weights float [T, C].
+    Returns dict(app [F, n], loss float, and with grad: grad_w [T, C],
+    grad_llr [F, n]).
+    """
+    lib = lib or _load_wbp()
+    llr = np.ascontiguousarray(llr, dtype=np.float32)
+    syndrome = np.ascontiguousarray(syndrome, dtype=np.uint8)
+    x = np.ascontiguousarray(x, dtype=np.uint8)
+    if llr.ndim == 1:
+        llr, syndrome, x = llr[None], syndrome[None], x[None]
+    F = llr.shape[0]
+    m, n = int(code.m), int(code.n)
+    w = np.ascontiguousarray(weights, dtype=np.float64)
+    T, C = int(iters), int(w.shape[1])
+    if w.shape != (T, C) or llr.shape != (F, n) or syndrome.shape != (F, m) or x.shape != (F, n):
+        raise ValueError("shapes do not match the code / iterations")
+    rowptr = np.ascontiguousarray(code.rowptr, dtype=np.int64)
+    colidx = np.ascontiguousarray(code.colidx, dtype=np.int32)
+    cls = np.ascontiguousarray(edge_class, dtype=np.int32)
+    if cls.shape != (int(rowptr[-1]),):
+        raise ValueError("edge_class must hold one class per edge")
+    app = np.zeros((F, n))
+    loss = np.zeros(1)
+    gw = np.zeros((T, C)) if grad else None
+    gl = np.zeros((F, n)) if grad else None
+    rc = lib.oracle_wbp(m, n, _ptr(rowptr), _ptr(colidx), F, _ptr(llr), _ptr(syndrome), _ptr(x), T, C,
+                        _ptr(cls), _ptr(w), float(lmax), _ptr(app), _ptr(loss), _ptr(gw), _ptr(gl),
+                        int(threads))
+    if rc != 0:
+        raise RuntimeError("oracle_wbp failed (bad arguments or out of memory)")
+    out = dict(app=app, loss=float(loss[0]))
+    if grad:
+        out.update(grad_w=gw, grad_llr=gl)
     return out

@@ -289,6 +289,18 @@ WORKLOADS = {
             frames=32, beta=0.93, rate=0.02, max_iter=500),
     5: dict(name="qc_n1e6_r0.02_stream", kind="qc", mb=49, nb=50, Z=20000, n_w2=25,
             frames=512, beta=0.95, rate=0.02, max_iter=1000, code_from=2),
+    # frames of three codes of different length and rate, decoded together; each
+    # frame draws its code and its efficiency beta ~ U[beta_lo, beta_hi]
+    3: dict(name="qc_mix3_n64k-1e6_256f", kind="batch", frames=256, beta_lo=0.85, beta_hi=0.97, max_iter=500,
+            codes=[dict(name="qc_n65536_r0.1", mb=115, nb=128, Z=512, n_w2=64, seed=1031),
+                   dict(name="qc_n262144_r0.05", mb=243, nb=256, Z=1024, n_w2=128, seed=1032),
+                   dict(name="qc_n1e6_r0.02", code_from=2)]),
+    # weighted BP trained by gradient descent: T unrolled iterations, one weight
+    # per (iteration, base block); gradients checked against finite differences
+    # on the small random code `fd` (one weight per (iteration, check degree))
+    4: dict(name="wbp_qc_n65536_r0.1_T20", kind="wbp", mb=115, nb=128, Z=512, n_w2=64, frames=128, beta=0.9,
+            rate=0.1, iters=20, checkpoint=5,
+            fd=dict(n=256, m=230, var_degree=3, check_degrees={3: 152, 4: 78}, seed=1404)),
     # a (3,6)-regular QC code of the same length class whose BP waterfall lies at
     # beta ~ 0.86-0.89, where early termination changes FER and mean iterations
     # (the regime of the paper's Figs. 1-2); used for the beta sweep
@@ -304,11 +316,96 @@ def workload_code(number: int, Z: int | None = None):
     seed = 1000 + code_no
     if w["kind"] == "csr":
         return random_csr_code(w["n"], w["m"], w["var_degree"], w["check_degrees"], seed)
+    if w["kind"] == "batch":
+        raise ValueError("a batch workload has several codes: use batch_codes()")
     if "col_weight" in w:
         weights = np.full(w["nb"], w["col_weight"], dtype=np.int64)
     else:
         weights = _qc_weights_2_3(w["nb"], w["n_w2"], seed)
     return random_qc_code(w["mb"], w["nb"], Z or w["Z"], weights, seed)
+
+
+def edge_classes_by_check_degree(code: CSRCode):
+    """Edge classes of a CSR code: the class of edge (c, v) is the rank of
+    deg(c) among the code's distinct check degrees.  Returns (class per edge
+    in CSR order, number of classes, the degrees in class order)."""
+    deg = code.check_degrees()
+    degrees = np.unique(deg[deg > 0])
+    rank = np.searchsorted(degrees, deg)
+    return rank[code.row_of_edge()].astype(np.int32), int(degrees.size), degrees
+
+
+def qc_block_index(code: QCCode) -> np.ndarray:
+    """[mb, nb] -> index of each nonzero base block in row-major order (-1 elsewhere)."""
+    nz = code.shifts >= 0
+    idx = np.full(code.shifts.shape, -1, dtype=np.int64)
+    idx[nz] = np.arange(int(nz.sum()))
+    return idx
+
+
+def qc_csr_edge_blocks(code: QCCode) -> np.ndarray:
+    """Base block of every edge of code.to_csr(), in CSR edge order."""
+    csr = code.to_csr()
+    rows = csr.row_of_edge() // code.Z
+    cols = csr.colidx.astype(np.int64) // code.Z
+    return qc_block_index(code)[rows, cols]
+
+
+def wbp_fd_code(number: int = 4) -> CSRCode:
+    """The small random code of a weighted-BP workload's finite-difference check."""
+    d = WORKLOADS[number]["fd"]
+    return random_csr_code(d["n"], d["m"], d["var_degree"], d["check_degrees"], d["seed"])
+
+
+def batch_codes(number: int):
+    """The codes of a batch workload, in the order frames index them."""
+    codes = []
+    for c in WORKLOADS[number]["codes"]:
+        if "code_from" in c:
+            codes.append(workload_code(c["code_from"]))
+        else:
+            codes.append(random_qc_code(c["mb"], c["nb"], c["Z"], _qc_weights_2_3(c["nb"], c["n_w2"], c["seed"]),
+                                        c["seed"]))
+    return codes
+
+
+@dataclass
+class BatchFrames:
+    frame_code: np.ndarray  # int32 [F]  code of each frame
+    beta: np.ndarray        # float64 [F]
+    sigma: np.ndarray       # float64 [F]
+    var_off: np.ndarray     # int64 [F + 1]  frame f's bits / LLRs at var_off[f] .. var_off[f + 1]
+    syn_off: np.ndarray     # int64 [F + 1]
+    x: np.ndarray           # uint8 [sum n]  all frames' bits, back to back
+    llr: np.ndarray         # float32 [sum n]
+    syndrome: np.ndarray    # uint8 [sum m]
+
+
+def workload_batch(number: int, codes, frames: int | None = None, first: int = 0) -> BatchFrames:
+    """Frames first..first+frames-1 of a batch workload.  Frame f draws its code
+    and beta from its own seeded generator, so a frame does not depend on how
+    many frames are drawn; then x, Lch and s as make_frames makes them, with
+    sigma such that capacity = R_code / beta."""
+    w = WORKLOADS[number]
+    F = w["frames"] if frames is None else frames
+    fc = np.empty(F, dtype=np.int32)
+    beta = np.empty(F)
+    for i in range(F):
+        rng = np.random.Generator(np.random.PCG64([number, first + i]))
+        fc[i] = rng.integers(0, len(codes))
+        beta[i] = rng.uniform(w["beta_lo"], w["beta_hi"])
+    sigma = np.array([sigma_for_capacity(codes[c].rate / b) for c, b in zip(fc, beta)])
+    var_off = np.concatenate([[0], np.cumsum([codes[c].n for c in fc])]).astype(np.int64)
+    syn_off = np.concatenate([[0], np.cumsum([codes[c].m for c in fc])]).astype(np.int64)
+    x = np.empty(var_off[-1], dtype=np.uint8)
+    llr = np.empty(var_off[-1], dtype=np.float32)
+    syn = np.empty(syn_off[-1], dtype=np.uint8)
+    for i in range(F):
+        fr = make_frames(codes[fc[i]], [sigma[i]], [2000 * number + first + i])
+        x[var_off[i]:var_off[i + 1]] = fr.x[0]
+        llr[var_off[i]:var_off[i + 1]] = fr.llr[0]
+        syn[syn_off[i]:syn_off[i + 1]] = fr.syndrome[0]
+    return BatchFrames(fc, beta, sigma, var_off, syn_off, x, llr, syn)
 
 
 def workload_frames(number: int, code, frames: int | None = None, first: int = 0,

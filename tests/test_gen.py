@@ -95,3 +95,20 @@ def test_frames_reproducible_and_llr_convention():
     agree = ((a.llr > 0) == (a.x == 0)).mean()
     assert 0.6 < agree < 0.8
     assert a.sigma[0] == pytest.approx(2.449867, abs=2e-6)
+
+
+def test_batch_workload_layout_and_reproducibility():
+    codes = gen.batch_codes(3)
+    assert [c.n for c in codes] == [65536, 262144, 1000000]
+    assert [round(c.rate, 2) for c in codes] == [0.1, 0.05, 0.02]
+    a = gen.workload_batch(3, codes, frames=6)
+    b = gen.workload_batch(3, codes, frames=3, first=3)
+    assert (a.frame_code[3:] == b.frame_code).all() and (a.beta[3:] == b.beta).all()
+    assert (a.llr[a.var_off[3]:] == b.llr).all() and (a.syndrome[a.syn_off[3]:] == b.syndrome).all()
+    for f in range(6):
+        c = codes[a.frame_code[f]]
+        assert a.var_off[f + 1] - a.var_off[f] == c.n and a.syn_off[f + 1] - a.syn_off[f] == c.m
+        x = a.x[a.var_off[f]:a.var_off[f + 1]]
+        assert (gen.syndrome(c, x) == a.syndrome[a.syn_off[f]:a.syn_off[f + 1]]).all()
+        assert 0.85 <= a.beta[f] <= 0.97
+        assert gen.biawgn_capacity(a.sigma[f]) == pytest.approx(c.rate / a.beta[f], rel=1e-9)
