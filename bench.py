@@ -482,12 +482,484 @@ def run_sweep(args):
         print(json.dumps(row), flush=True)
 
 
+# ---------------------------------------------------------------------------
+# Batched frames of several codes (one persistent kernel in a CUDA graph)
+# ---------------------------------------------------------------------------
+BATCH_METRIC = "decoded Mbit/s (PCE+VNR early termination), 256 frames of 3 QC codes n=64k..1e6"
+
+
+def batch_oracle_rate(codes, bf, d_per_frame, target_s, d_src):
+    """CPU rate of the oracle on the batch: seconds per frame-iteration of each
+    code from a bounded sample, times each frame's D."""
+    s_fi = {}
+    cores = 1
+    parts = []
+    for c, code in enumerate(codes):
+        idx = np.nonzero(bf.frame_code == c)[0]
+        if idx.size == 0:
+            continue
+        fr = gen.Frames(None, np.stack([bf.llr[bf.var_off[f]:bf.var_off[f + 1]] for f in idx[:16]]),
+                        np.stack([bf.syndrome[bf.syn_off[f]:bf.syn_off[f + 1]] for f in idx[:16]]), None)
+        t, cores, F, iters, dt = time_oracle_sample(code.to_csr(), fr, 500, target_s / len(codes))
+        s_fi[c] = t
+        parts.append(f"code {c}: {F} frames x {iters} iterations ({dt:.1f} s)")
+    cpu_s = sum(d_per_frame[f] * s_fi[int(bf.frame_code[f])] for f in range(bf.frame_code.size))
+    mbps = float(bf.var_off[-1]) / cpu_s / 1e6
+    sample = ("FP64 oracle, " + "; ".join(parts) + f"; {cores} threads; per-frame-iteration times of each "
+              f"code scaled to every frame's D ({d_src})")
+    return mbps, cores, sample
+
+
+def batch_oracle_iters(wl_name):
+    path = os.path.join(ROOT, "tests", "golden", f"oracle_{wl_name}_pce_vnr.txt")
+    if not os.path.exists(path):
+        return None
+    its = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            f, it = line.split()[:2]
+            its[int(f)] = int(it)
+    return its
+
+
+def run_batch_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = gen.WORKLOADS[args.workload]
+    codes = gen.batch_codes(args.workload)
+    bf = gen.workload_batch(args.workload, codes, frames=args.frames)
+    F = bf.frame_code.size
+    its = batch_oracle_iters(wl["name"])
+    if its is not None and all(f in its for f in range(F)):
+        d, src = [its[f] for f in range(F)], "oracle's own decisions on these frames"
+    else:
+        d, src = [wl["max_iter"]] * F, "max_iter (no stored oracle decisions)"
+    target = max(1.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        mbps, cores, sample = batch_oracle_rate(codes, bf, d, target, src)
+        if i >= args.warmup:
+            vals.append(mbps)
+    v = float(np.mean(vals))
+    line = {"metric": BATCH_METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": float(bf.var_off[-1]) / (v * 1e6) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "frames": F, "bits_per_step": int(bf.var_off[-1]),
+                       "max_iter": wl["max_iter"], "rule": "pce_vnr"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_batch(args):
+    """One step = one replay of a CUDA graph holding a whole batch decode
+    (control init, syndrome packing, the persistent decoder, status word) of
+    the workload's frames, inputs resident in HBM; schedule from the autotuner."""
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2507_03509_gb300 import build
+    build.build()
+    from paper_2507_03509_gb300 import ldpc
+
+    wl = gen.WORKLOADS[args.workload]
+    max_iter = args.max_iter or wl["max_iter"]
+    codes = gen.batch_codes(args.workload)
+    F = args.frames or wl["frames"]
+    bf = gen.workload_batch(args.workload, codes, frames=F, first=shard_first_frame(rank, F))
+    bits_per_step = int(bf.var_off[-1])
+    graphs = [ldpc.Graph.from_code(c) for c in codes]
+    batch = ldpc.Batch(graphs, bf.frame_code)
+    llr = torch.from_numpy(bf.llr).to(dev)
+    syn = torch.from_numpy(bf.syndrome).to(dev)
+    out = batch.outputs(dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    # schedule: the autotuner's pick unless given on the command line (untimed)
+    t0 = time.perf_counter()
+    if args.groups or args.slots:
+        tuned = None
+        opt = dict(groups=args.groups, max_active_frames=args.slots)
+    else:
+        tuned = batch.autotune(llr, syn, max_iter, "pce_vnr", out=out)
+        opt = {}
+    tune_s = time.perf_counter() - t0
+    batch.decode(llr, syn, max_iter, "pce_vnr", out=out, **opt)  # sizes the workspace for this schedule
+
+    # capture one decode in a CUDA graph (warmed up on a side stream first)
+    side = torch.cuda.Stream(dev)
+    side.wait_stream(stream)
+    with torch.cuda.stream(side):
+        batch.decode_async(llr, syn, max_iter, "pce_vnr", out, status, **opt)
+    stream.wait_stream(side)
+    torch.cuda.synchronize()
+    cg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(cg):
+        batch.decode_async(llr, syn, max_iter, "pce_vnr", out, status, **opt)
+    for _ in range(max(3, args.warmup)):
+        cg.replay()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # evict the previous step's data from L2 (outside the timed events)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cg.replay()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    if int(status.item()) != 0:
+        raise RuntimeError(f"batch decode failed: {ldpc.ldpc_status_str(int(status.item()))}")
+    ms_total = job_time_ms(sum(ms), dist, dev)
+    value = bits_per_step * args.steps * world / (ms_total * 1e-3) / 1e6
+
+    iters = out[2].cpu().numpy()
+    flags = out[1].cpu().numpy()
+    bits = out[0].cpu().numpy()
+    errs = np.array([(bits[bf.var_off[f]:bf.var_off[f + 1]] != bf.x[bf.var_off[f]:bf.var_off[f + 1]]).any()
+                     for f in range(F)])
+    ok = ~errs & ((flags & 1) > 0)
+    B = [algorithmic_bytes_per_frame_iter(c) for c in codes]
+    bytes_per_step = float(sum(int(iters[f]) * B[int(bf.frame_code[f])] for f in range(F)))
+    peak, peak_src = hbm_peak()
+    achieved = bytes_per_step / (statistics.mean(ms) * 1e-3) / 1e9
+    per_code = {}
+    for c, code in enumerate(codes):
+        idx = bf.frame_code == c
+        per_code[gen.WORKLOADS[args.workload]["codes"][c]["name"]] = {
+            "frames": int(idx.sum()), "d_mean": float(iters[idx].mean()) if idx.any() else None,
+            "fer": float(1 - ok[idx].mean()) if idx.any() else None,
+            "aborted": int(((flags[idx] & 2) > 0).sum())}
+
+    # fixed-iteration baselines (synchronous decodes of the same batch)
+    comp = {}
+    for rule in (() if args.lean else ("pce", "none")):
+        batch.decode(llr, syn, max_iter, rule, out=out, **opt)
+        t = []
+        for _ in range(args.compare_steps):
+            flush.fill_(1.0)
+            st = ldpc.ldpc_decode_stats()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            batch.decode(llr, syn, max_iter, rule, out=out, stats=st, **opt)
+            e1.record(stream)
+            e1.synchronize()
+            t.append(e0.elapsed_time(e1))
+        comp[rule] = {"mbit_s": bits_per_step / (statistics.mean(t) * 1e-3) / 1e6,
+                      "ms_per_step": statistics.mean(t), "d_mean": float(out[2].float().mean().item())}
+
+    # end to end: pinned host buffers copied in, graph replayed, results copied out, every step
+    e2e = None
+    if not args.lean:
+        h_llr = torch.from_numpy(bf.llr).pin_memory()
+        h_syn = torch.from_numpy(bf.syndrome).pin_memory()
+        h_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in out]
+        e2e_steps = max(1, min(args.steps, 5))
+        def e2e_step():
+            llr.copy_(h_llr, non_blocking=True)
+            syn.copy_(h_syn, non_blocking=True)
+            cg.replay()
+            for h, d in zip(h_out, out):
+                h.copy_(d, non_blocking=True)
+            stream.synchronize()
+        e2e_step()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": bits_per_step * e2e_steps / e2e_s / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(bf.llr.nbytes + bf.syndrome.nbytes),
+               "d2h_bytes_per_step": int(sum(t.numel() * t.element_size() for t in out))}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.lean:
+        mbps, cores, sample = batch_oracle_rate(codes, bf, [int(i) for i in iters], args.cpu_seconds,
+                                                "D of this run")
+        cpu = {"value": mbps, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    if rank != 0:
+        return
+    line = {
+        "metric": BATCH_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["name"], "frames_per_gpu": F, "bits_per_step": bits_per_step,
+                   "codes": [{"n": c.n, "m": c.m, "edges": int(c.edges), "rate": c.rate} for c in codes],
+                   "beta": [wl["beta_lo"], wl["beta_hi"]], "max_iter": max_iter, "rule": "pce_vnr",
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "inputs > L2 (129 MB); L2 also flushed between steps",
+                   "schedule": {"autotuned": tuned is not None, "groups": tuned[0] if tuned else args.groups,
+                                "slots": tuned[1] if tuned else args.slots, "autotune_s": tune_s},
+                   "cuda_graph": "init + pack + persistent decoder + status kernels, replayed once per step"},
+        "d_mean": float(iters.mean()), "fer": float(1 - ok.mean()), "per_code": per_code,
+        "fixed_iteration": comp,
+        "et_speedup": None if not comp else {"vs_pce": comp["pce"]["ms_per_step"] / (ms_total / args.steps),
+                                             "vs_none": comp["none"]["ms_per_step"] / (ms_total / args.steps)},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": peak_src, "traffic": None, "algorithmic_bytes_per_launch": bytes_per_step,
+                     "kernel": "bp_decode_kernel<float,QcDev>",
+                     "timed": "whole graph replay (the decoder plus three one-CTA kernels)"},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": 4 * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    batch.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# Weighted BP training (forward, loss, adjoint, gradient step in one CUDA graph)
+# ---------------------------------------------------------------------------
+WBP_METRIC = "trained Mbit/s (weighted BP, 20 unrolled iterations, forward + adjoint + step), QC n=65536"
+
+
+def wbp_bytes_per_frame_iter(code) -> int:
+    """Forward 8E + 12n (as the decoder) plus adjoint 12E + 12n: c2v^(k-1) and
+    G read, G^(k-1) written, APP^(k-1) read, dloss/dLch read and written."""
+    return 20 * int(code.edges) + 24 * int(code.n)
+
+
+def wbp_setup(number):
+    wl = gen.WORKLOADS[number]
+    code = gen.workload_code(number)
+    nblk = int((code.shifts >= 0).sum())
+    cls_blk = np.arange(nblk, dtype=np.int32)
+    return wl, code, nblk, cls_blk
+
+
+def wbp_oracle_rate(code, cls_csr, C, fr, T, target_s):
+    """Oracle training throughput (forward, loss and gradient, FP64) on a
+    bounded sample: one frame per core, frames decoded together."""
+    import oracle
+    oracle.build()
+    cores = oracle.max_threads()
+    csr = code.to_csr()
+    w = np.ones((T, C))
+    F = min(cores, fr.llr.shape[0])
+    done, calls = 0, 0
+    t0 = time.perf_counter()
+    while True:  # groups of one frame per core until the target time is used
+        lo = (calls * F) % fr.llr.shape[0]
+        sel = slice(lo, min(lo + F, fr.llr.shape[0]))
+        oracle.wbp(csr, fr.llr[sel], fr.syndrome[sel], fr.x[sel], T, cls_csr, w)
+        done += sel.stop - sel.start
+        calls += 1
+        dt = time.perf_counter() - t0
+        if dt >= target_s:
+            break
+    return code.n * done / dt / 1e6, cores, (f"{done} frames ({calls} calls of {F}) x {T} iterations, forward + "
+                                             f"loss + gradient of the FP64 oracle ({dt:.1f} s, {cores} threads)")
+
+
+def run_wbp_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl, code, nblk, cls_blk = wbp_setup(args.workload)
+    cls_csr = cls_blk[gen.qc_csr_edge_blocks(code)]
+    fr = gen.workload_frames(args.workload, code, frames=min(wl["frames"], 64))
+    target = max(1.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, cores, sample = wbp_oracle_rate(code, cls_csr, nblk, fr, wl["iters"], target)
+        if i >= args.warmup:
+            vals.append(v)
+    v = float(np.mean(vals))
+    F = wl["frames"]
+    line = {"metric": WBP_METRIC, "value": v, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": code.n * F / (v * 1e6) * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl["name"], "frames": F, "n": code.n, "iters": wl["iters"], "classes": nblk},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_wbp(args):
+    """One step = one replay of a CUDA graph holding a whole training step of
+    the weighted decoder on the workload's frames (inputs resident in HBM):
+    forward over T iterations with checkpoints, BCE loss, adjoint with
+    recomputation, SGD update of the weights."""
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2507_03509_gb300 import build
+    build.build()
+    from paper_2507_03509_gb300 import ldpc
+
+    wl, code, nblk, cls_blk = wbp_setup(args.workload)
+    F = args.frames or wl["frames"]
+    T = wl["iters"]
+    fr = gen.workload_frames(args.workload, code, frames=F, first=shard_first_frame(rank, F))
+    graph = ldpc.Graph.from_code(code)
+    plan = ldpc.WeightedBP(graph, F, T, cls_blk, nblk, checkpoint_every=wl["checkpoint"])
+    llr = torch.from_numpy(fr.llr).to(dev)
+    syn = torch.from_numpy(fr.syndrome).to(dev)
+    x = torch.from_numpy(fr.x).to(dev)
+    w = torch.ones((T, nblk), dtype=torch.float32, device=dev)
+    app = torch.empty((F, code.n), dtype=torch.float32, device=dev)
+    gw = torch.empty_like(w)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    lr = 20.0
+
+    def step():
+        plan.forward(llr, syn, w, app=app)
+        loss, gapp = plan.loss(app, x)
+        plan.backward(llr, syn, w, gapp, grad_w=gw)
+        plan.sgd_step(w, gw, lr)
+        return loss
+
+    first_loss = float(step().item())
+    torch.cuda.synchronize()
+    cg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(cg):
+        loss_g = step()
+    cgf = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(cgf):
+        plan.forward(llr, syn, w, app=app, save=False)
+    for _ in range(max(3, args.warmup)):
+        cg.replay()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cg.replay()
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clk = clocks.stop()
+    last_loss = float(loss_g.item())
+    fwd_ms = []
+    for _ in range(max(3, args.steps)):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cgf.replay()
+        e1.record(stream)
+        e1.synchronize()
+        fwd_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms_total = job_time_ms(sum(ms), dist, dev)
+    value = code.n * F * args.steps * world / (ms_total * 1e-3) / 1e6
+    peak, peak_src = hbm_peak()
+    B = wbp_bytes_per_frame_iter(code) * F * T
+    achieved = B / (statistics.mean(ms) * 1e-3) / 1e9
+    Bf = algorithmic_bytes_per_frame_iter(code) * F * T
+    fwd_achieved = Bf / (statistics.mean(fwd_ms) * 1e-3) / 1e9
+    every = wl["checkpoint"]
+    n_launch = (2 * T + 2) + (1 + 3 * T + 2 * (T - (T + every - 1) // every)) + 1
+
+    # end to end: inputs copied in from pinned host memory, the step replayed,
+    # loss and weights read back, every step
+    e2e = None
+    if not args.lean:
+        h_llr = torch.from_numpy(fr.llr).pin_memory()
+        h_syn = torch.from_numpy(fr.syndrome).pin_memory()
+        h_x = torch.from_numpy(fr.x).pin_memory()
+        h_w = torch.empty_like(w, device="cpu").pin_memory()
+        h_loss = torch.empty(1, dtype=torch.float32).pin_memory()
+        e2e_steps = max(1, min(args.steps, 5))
+        def e2e_step():
+            llr.copy_(h_llr, non_blocking=True)
+            syn.copy_(h_syn, non_blocking=True)
+            x.copy_(h_x, non_blocking=True)
+            cg.replay()
+            h_loss.copy_(loss_g, non_blocking=True)
+            h_w.copy_(w, non_blocking=True)
+            stream.synchronize()
+        e2e_step()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": code.n * F * e2e_steps / e2e_s / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(fr.llr.nbytes + fr.syndrome.nbytes + fr.x.nbytes),
+               "d2h_bytes_per_step": int(4 + w.numel() * 4)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.lean:
+        cls_csr = cls_blk[gen.qc_csr_edge_blocks(code)]
+        v, cores, sample = wbp_oracle_rate(code, cls_csr, nblk, fr, T, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    if rank != 0:
+        return
+    line = {
+        "metric": WBP_METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["name"], "frames_per_gpu": F, "n": code.n, "m": code.m, "edges": int(code.edges),
+                   "rate": code.rate, "beta": wl["beta"], "iters": T, "classes": nblk,
+                   "checkpoint_every": every, "lr": lr,
+                   "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": "decoder state (~1 GB) > L2 (129 MB); L2 also flushed between steps",
+                   "cuda_graph": "forward + loss + adjoint + SGD step, replayed once per step"},
+        "loss_first_step": first_loss, "loss_after_steps": last_loss,
+        "forward_only": {"mbit_s": code.n * F / (statistics.mean(fwd_ms) * 1e-3) / 1e6,
+                         "ms": statistics.mean(fwd_ms), "achieved_gbs": fwd_achieved,
+                         "frac": fwd_achieved / peak},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": peak_src, "traffic": None, "algorithmic_bytes_per_launch": B,
+                     "kernel": "training step (wbp::cn_kernel / vn_*_kernel / wgrad_kernel)",
+                     "timed": "whole graph replay"},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": n_launch * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    plan.close()
+    if dist:
+        dist.destroy_process_group()
+
+
 def main():
     args = parse()
+    kind = gen.WORKLOADS.get(args.workload, {}).get("kind")
+    if kind == "wbp":
+        return run_wbp_reference(args) if args.impl == "reference" else run_wbp(args)
+    batch = kind == "batch"
     if args.impl == "reference":
-        run_reference(args)
+        run_batch_reference(args) if batch else run_reference(args)
     elif args.sweep:
         run_sweep(args)
+    elif batch:
+        run_batch(args)
     else:
         run_ours(args)
 

@@ -261,6 +261,67 @@ LDPC_API ldpc_status ldpc_decode_qc_noalloc(int32_t mb, int32_t nb, int32_t Z, c
                                             int32_t max_iter, ldpc_term_rule rule, uint8_t* bits_out,
                                             uint8_t* flags_out, int32_t* iters_out, void* cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Weighted belief propagation (trainable decoder)
+ *
+ * The sum-product decoder of ldpc_decode (paper, section "Early Termination":
+ * tanh/atanh check rule with the syndrome sign, l_out the a-posteriori value)
+ * unrolled for exactly `iters` flooding iterations, without early
+ * termination, with one weight per (iteration k, edge class cl) that scales
+ * every check-to-variable message of that class:
+ *     c2v_e^(k) = w[k][class(e)] * clamp((1 - 2 s_c) * boxplus of the other
+ *                 clamped v2c messages of check c, +-25)
+ * (a degree-1 check sends (1 - 2 s_c) * 25).  The calls below run it forward,
+ * evaluate a binary cross-entropy loss on its soft output, run its adjoint
+ * (the exact reverse-mode gradient w.r.t. the weights and the channel LLRs)
+ * with recomputation from checkpoints, and take a plain gradient step.
+ *
+ * Element type: the plan's arithmetic type -- float, or double when the plan
+ * is created with fp64 = 1.  Every buffer typed `void*` below holds that type.
+ * All buffers are device buffers owned by the caller; the plan owns its
+ * workspace (allocated at creation).  No call allocates or waits for the GPU:
+ * each is stream-ordered and can be captured in a CUDA graph.  Syndrome and
+ * bit bytes count as 1 when nonzero.
+ * ------------------------------------------------------------------------- */
+typedef struct ldpc_wbp ldpc_wbp;
+
+/* Plan for `frames` frames of `graph`, `iters` iterations, `n_classes` weight
+ * classes.  edge_class (host, copied): for a QC graph one class per nonzero
+ * base block, in row-major block order (length = nonzero blocks); for a CSR
+ * graph one class per edge in CSR order (length = edges); values in
+ * [0, n_classes).  checkpoint_every (>= 1): the forward pass keeps the
+ * messages of every checkpoint_every-th iteration and the backward pass
+ * recomputes the iterations in between (1 = keep all; >= iters = keep none).
+ * The graph must outlive the plan.  LDPC_ERR_INVALID_ARG on bad sizes or
+ * classes. */
+LDPC_API ldpc_status ldpc_wbp_create(const ldpc_graph* graph, int32_t frames, int32_t iters, int32_t n_classes,
+                                     const int32_t* edge_class, int32_t checkpoint_every, int32_t fp64,
+                                     ldpc_wbp** out);
+LDPC_API void ldpc_wbp_destroy(ldpc_wbp* plan);
+/* Forward pass: llr float [frames][n], syndrome uint8 [frames][m], weights
+ * [iters][n_classes]; writes app_out [frames][n] = APP after the last
+ * iteration.  With save_for_backward the checkpoints a later ldpc_wbp_backward
+ * needs are kept in the plan (the next forward with it set replaces them). */
+LDPC_API ldpc_status ldpc_wbp_forward(ldpc_wbp* plan, const float* llr, const uint8_t* syndrome,
+                                      const void* weights, void* app_out, int32_t save_for_backward,
+                                      void* cuda_stream);
+/* Loss: loss_out[0] = mean over frames*n bits of softplus(-(1 - 2 x) APP),
+ * the binary cross-entropy of P(x = 1) = 1 / (1 + e^APP) against x uint8
+ * [frames][n]; if grad_app is not NULL it receives dloss/dAPP [frames][n]. */
+LDPC_API ldpc_status ldpc_wbp_loss(ldpc_wbp* plan, const void* app, const uint8_t* x, void* loss_out,
+                                   void* grad_app, void* cuda_stream);
+/* Backward pass for the last forward with save_for_backward (same llr,
+ * syndrome and weights, unchanged since): from grad_app = dloss/dAPP
+ * [frames][n] writes grad_weights [iters][n_classes] and, if not NULL,
+ * grad_llr [frames][n] = dloss/dLch.  LDPC_ERR_INVALID_ARG if the plan keeps
+ * checkpoints and no forward has saved them. */
+LDPC_API ldpc_status ldpc_wbp_backward(ldpc_wbp* plan, const float* llr, const uint8_t* syndrome,
+                                       const void* weights, const void* grad_app, void* grad_weights,
+                                       void* grad_llr, void* cuda_stream);
+/* weights -= lr * grad over [iters][n_classes] (a plain gradient step). */
+LDPC_API ldpc_status ldpc_wbp_sgd_step(ldpc_wbp* plan, void* weights, const void* grad, double lr,
+                                       void* cuda_stream);
+
 /* Static, human-readable name of a status code. */
 LDPC_API const char* ldpc_status_str(ldpc_status status);
 

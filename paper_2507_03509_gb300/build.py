@@ -36,15 +36,30 @@ def nvcc_flags() -> list[str]:
             "-fvisibility=hidden", "-I" + os.path.join(ROOT, "include")]
 
 
+UNITS = ("ldpc_api.cu", "wbp_api.cu")  # translation units, compiled in parallel
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     newest = max(os.path.getmtime(s) for s in sources())
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= newest:
         return LIB
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc_path(), *nvcc_flags(), "-shared", "-o", tmp, os.path.join(CSRC, "ldpc_api.cu")]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.run(cmd, check=True)
+    out = os.path.join(PKG, "_build")
+    os.makedirs(out, exist_ok=True)
+    tag = f"{os.getpid()}"
+    objs = [os.path.join(out, f"{os.path.splitext(u)[0]}.{tag}.o") for u in UNITS]
+    procs = []
+    for unit, obj in zip(UNITS, objs):
+        cmd = [nvcc_path(), *nvcc_flags(), "-c", "-o", obj, os.path.join(CSRC, unit)]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        procs.append(subprocess.Popen(cmd))
+    failed = [u for u, pr in zip(UNITS, procs) if pr.wait() != 0]
+    if failed:
+        raise RuntimeError(f"nvcc failed on {', '.join(failed)}")
+    tmp = LIB + f".{tag}.tmp"
+    subprocess.run([nvcc_path(), ARCH, "-shared", "-o", tmp, *objs], check=True)
+    for obj in objs:
+        os.remove(obj)
     os.replace(tmp, LIB)
     return LIB
 

@@ -22,6 +22,9 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "cn_math.cuh"
+#include "device_types.h"
+
 namespace ldpcgb {
 
 constexpr int kThreads = 256;
@@ -30,7 +33,6 @@ constexpr int kCPT = 2;                  // checks per thread in a check-node ti
 constexpr int kVPT = 4;                  // variables per thread in a variable-node tile
 constexpr int kCnTile = kThreads * kCPT;
 constexpr int kVnTile = kThreads * kVPT;
-constexpr int kMaxDeg = 64;              // largest check degree supported
 constexpr int kMaxSlots = 1024;
 
 enum : int { kErrNone = 0, kErrTimeout = 1, kErrSyndrome = 2 };
@@ -40,39 +42,6 @@ enum : int { kRuleNone = 0, kRulePce = 1, kRulePceVnr = 2 };
 constexpr int kMaxGrid = 4096;            // largest grid either decoder kernel is launched with
 
 constexpr int kMaxGroups = 64;
-
-// One per group (its barrier), 128 bytes apart; the first one also holds the
-// error word, the iteration total and the queue of waiting frames.
-struct alignas(128) Ctrl {
-    unsigned bar_count;
-    unsigned bar_gen;
-    int err;
-    int next_frame;                  // frames handed out so far
-    unsigned long long frame_iters;  // sum over frames of D
-};
-
-// Quasi-cyclic code: nonzero base blocks in row-major order (block id b).
-// Check i*Z + t meets variable col[b]*Z + (t + shift[b]) mod Z.
-// Messages of block b live at c2v[b*Z + p], p the variable's offset in its
-// column block, so the variable-node side reads them unrotated.
-struct QcDev {
-    int mb, nb, Z, nblk;
-    const int* row_ptr;            // [mb+1] first block of row i
-    const int* blk_col;            // [nblk]
-    const int* blk_shift;          // [nblk]
-    const int* col_ptr;            // [nb+1] into col_blk
-    const int* col_blk;            // [nblk] block ids of column j, ascending row
-    const int* blk_row;            // [nblk] base row of block b
-};
-
-// General code: check-major CSR plus a variable-major list of edge ids.
-struct CsrDev {
-    int m, n;
-    const int* row_ptr;            // [m+1]
-    const int* col_idx;            // [E]
-    const int* var_ptr;            // [n+1]
-    const int* var_edge;           // [E] edge ids of variable v, ascending
-};
 
 constexpr int kMaxCodes = 4;              // codes one decode call may mix
 
@@ -188,10 +157,6 @@ __device__ __forceinline__ unsigned long long global_ns() {
 __device__ __forceinline__ int ld_volatile(const int* p) { return *(const volatile int*)p; }
 __device__ __forceinline__ double ld_volatile(const double* p) { return *(const volatile double*)p; }
 
-__device__ __forceinline__ float clampm(float x, float l) { return fminf(fmaxf(x, -l), l); }
-__device__ __forceinline__ double clampm(double x, double l) { return fmin(fmax(x, -l), l); }
-__device__ __forceinline__ float absm(float x) { return fabsf(x); }
-__device__ __forceinline__ double absm(double x) { return fabs(x); }
 
 // Barrier over the nblocks CTAs of one group (a cooperative launch keeps them
 // all resident).  The group's arrival counter only grows: thread 0 of each
@@ -227,109 +192,6 @@ __device__ __forceinline__ bool grid_sync(Ctrl* bar, int* err, unsigned nblocks,
     }
     __syncthreads();
     return ld_volatile(err) == kErrNone;
-}
-
-// ---------------------------------------------------------------------------
-// Check-node cores.  In: clamped v2c messages v[0..D).  Out: c2v messages
-// c2v_k = (1 - 2 s) * prod_{j != k} sgn(v_j) * |v_0 [+] ... (skip k) ... [+] v_{D-1}|
-// where [+] is the boxplus, 2 atanh(tanh(a/2) tanh(b/2)).
-//
-// FP32: signs and magnitudes are kept apart, so the rule is exactly odd in
-// every input.  A magnitude x maps to r = exp(-x); boxplus of magnitudes is
-// then r_a (+) r_b = (r_a + r_b) / (1 + r_a r_b) -- the tanh-product identity
-// rewritten for 1 - tanh, which neither saturates nor cancels in FP32 -- and
-// the result is -ln r.  Exclusive combinations come from prefix and suffix
-// products (forward-backward); a degree-2 check copies the other message.
-// FP64 (debug): the tanh/atanh rule literally, products by explicit loop.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ float rcomb(float a, float b) {
-    return __fdividef(a + b, fmaf(a, b, 1.0f));
-}
-
-template <int D>
-__device__ __forceinline__ void cn_core(const float (&v)[D], unsigned sbit, float lmax,
-                                        float (&out)[D]) {
-    if constexpr (D == 1) {
-        out[0] = sbit ? -lmax : lmax;
-    } else {
-        unsigned par = sbit;
-        bool ng[D];
-#pragma unroll
-        for (int k = 0; k < D; ++k) {
-            ng[k] = v[k] < 0.0f;
-            par ^= (unsigned)ng[k];
-        }
-        float mag[D];
-        if constexpr (D == 2) {
-            mag[0] = fabsf(v[1]);
-            mag[1] = fabsf(v[0]);
-        } else {
-            float r[D], pre[D], suf[D];
-#pragma unroll
-            for (int k = 0; k < D; ++k) r[k] = __expf(-fabsf(v[k]));
-            pre[0] = r[0];
-#pragma unroll
-            for (int k = 1; k < D - 1; ++k) pre[k] = rcomb(pre[k - 1], r[k]);
-            suf[D - 1] = r[D - 1];
-#pragma unroll
-            for (int k = D - 2; k >= 1; --k) suf[k] = rcomb(r[k], suf[k + 1]);
-#pragma unroll
-            for (int k = 0; k < D; ++k) {
-                float ex = (k == 0) ? suf[1] : (k == D - 1) ? pre[D - 2] : rcomb(pre[k - 1], suf[k + 1]);
-                mag[k] = fminf(fmaxf(-__logf(ex), 0.0f), lmax);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < D; ++k) out[k] = (par ^ (unsigned)ng[k]) ? -mag[k] : mag[k];
-    }
-}
-
-template <int D>
-__device__ __forceinline__ void cn_core(const double (&v)[D], unsigned sbit, double lmax,
-                                        double (&out)[D]) {
-    double th[D];
-#pragma unroll
-    for (int k = 0; k < D; ++k) th[k] = tanh(0.5 * v[k]);
-    const double sg = sbit ? -1.0 : 1.0;
-#pragma unroll
-    for (int k = 0; k < D; ++k) {
-        double prod = 1.0;
-#pragma unroll
-        for (int j = 0; j < D; ++j)
-            if (j != k) prod *= th[j];
-        out[k] = clampm(sg * 2.0 * atanh(prod), lmax);
-    }
-}
-
-// Degree > 8: the same rules with loops over local arrays.
-__device__ __noinline__ void cn_core_n(const float* v, int d, unsigned sbit, float lmax, float* out) {
-    float r[kMaxDeg], suf[kMaxDeg];
-    unsigned par = sbit;
-    for (int k = 0; k < d; ++k) {
-        par ^= (unsigned)(v[k] < 0.0f);
-        r[k] = __expf(-fabsf(v[k]));
-    }
-    suf[d - 1] = r[d - 1];
-    for (int k = d - 2; k >= 1; --k) suf[k] = rcomb(r[k], suf[k + 1]);
-    float pre = 0.0f;
-    for (int k = 0; k < d; ++k) {
-        float ex = (k == 0) ? suf[1] : (k == d - 1) ? pre : rcomb(pre, suf[k + 1]);
-        float mag = fminf(fmaxf(-__logf(ex), 0.0f), lmax);
-        out[k] = (par ^ (unsigned)(v[k] < 0.0f)) ? -mag : mag;
-        pre = (k == 0) ? r[0] : rcomb(pre, r[k]);
-    }
-}
-
-__device__ __noinline__ void cn_core_n(const double* v, int d, unsigned sbit, double lmax, double* out) {
-    double th[kMaxDeg];
-    for (int k = 0; k < d; ++k) th[k] = tanh(0.5 * v[k]);
-    const double sg = sbit ? -1.0 : 1.0;
-    for (int k = 0; k < d; ++k) {
-        double prod = 1.0;
-        for (int j = 0; j < d; ++j)
-            if (j != k) prod *= th[j];
-        out[k] = clampm(sg * 2.0 * atanh(prod), lmax);
-    }
 }
 
 __device__ __forceinline__ unsigned syndrome_bit(const unsigned* sb, int row) {
@@ -1029,19 +891,20 @@ struct PackInfo {
     const long long* sb_off;       // [frames] word offset, NULL = f * swords
 };
 
-// Pack the syndrome bytes into bits, 32 checks per word, one frame per CTA
-// (grid-stride over frames, one warp per word); any byte other than 0/1
-// raises kErrSyndrome (the decode kernel then returns at once).
+// Pack the syndrome bytes into bits, 32 checks per word, one warp per word:
+// blockIdx.y walks the frames, blockIdx.x the frame's words; any byte other
+// than 0/1 raises kErrSyndrome (the decode kernel then returns at once).
 __global__ void pack_syndrome_kernel(const unsigned char* __restrict__ syn, int frames, PackInfo pi,
                                      unsigned* __restrict__ out, Ctrl* ctrl) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int f = blockIdx.x; f < frames; f += gridDim.x) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int warp = (int)blockIdx.x * nw + (threadIdx.x >> 5), wstride = (int)gridDim.x * nw;
+    for (int f = blockIdx.y; f < frames; f += gridDim.y) {
         const int c = pi.frame_code ? pi.frame_code[f] : 0;
         const int m = pi.m[c], swords = pi.swords[c];
         const unsigned char* s = syn + (pi.syn_off ? pi.syn_off[f] : (long long)f * m);
         unsigned* o = out + (pi.sb_off ? pi.sb_off[f] : (long long)f * swords);
         bool bad = false;
-        for (int w = warp; w < swords; w += nw) {
+        for (int w = warp; w < swords; w += wstride) {
             const int i = w * 32 + lane;
             const unsigned char b = i < m ? s[i] : (unsigned char)0;
             const unsigned bits = __ballot_sync(0xffffffffu, (b & 1u) != 0u);

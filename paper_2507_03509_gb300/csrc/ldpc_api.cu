@@ -16,56 +16,13 @@
 
 #include "../../include/ldpc.h"
 #include "bp_kernels.cuh"
+#include "host_common.h"
 
 using namespace ldpcgb;
 
 namespace {
 
 constexpr unsigned long long kBarrierTimeoutNs = 10ull * 1000ull * 1000ull * 1000ull;  // 10 s
-
-struct Workspace {
-    void* buf = nullptr;
-    size_t cap = 0;
-    Ctrl* ctrl = nullptr;      // separate small allocation
-    int* host_err = nullptr;   // pinned
-    unsigned long long* host_iters = nullptr;  // pinned
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    // staging for ldpc_decode_host
-    void* stage = nullptr;
-    size_t stage_cap = 0;
-};
-
-}  // namespace
-
-struct ldpc_graph {
-    int kind = 0;  // 0 = CSR, 1 = QC
-    int device = 0;
-    int32_t m = 0, n = 0;
-    int64_t E = 0;
-    // QC description
-    int mb = 0, nb = 0, Z = 0, nblk = 0;
-    // device arrays (one allocation)
-    void* dmem = nullptr;
-    QcDev qc{};
-    CsrDev csr{};
-    int vn_tiles = 0, cn_tiles = 0;
-    std::vector<int> row_deg, col_deg;  // QC base-matrix row and column weights
-    Workspace ws;
-};
-
-namespace {
-
-ldpc_status cuda_status(cudaError_t e) {
-    if (e == cudaSuccess) return LDPC_OK;
-    if (e == cudaErrorMemoryAllocation) return LDPC_ERR_OOM;
-    return LDPC_ERR_CUDA;
-}
-
-#define LDPC_TRY(expr)                                   \
-    do {                                                 \
-        ldpc_status st_ = cuda_status(expr);             \
-        if (st_ != LDPC_OK) return st_;                  \
-    } while (0)
 
 // Upload a set of host int arrays into one device allocation.
 ldpc_status upload_arrays(const std::vector<std::vector<int>>& arrays, void** dmem,
@@ -104,8 +61,6 @@ void free_workspace(Workspace& ws) {
         if (e) cudaEventDestroy(e);
     ws = Workspace{};
 }
-
-size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Device layout of one decode's state.
 struct Layout {
@@ -146,24 +101,6 @@ ldpc_status ensure_workspace(Workspace& ws, size_t bytes) {
     }
     return LDPC_OK;
 }
-
-// Restores the caller's current device on scope exit.
-struct DeviceGuard {
-    int prev = -1;
-    bool changed = false;
-    cudaError_t enter(int dev) {
-        cudaError_t e = cudaGetDevice(&prev);
-        if (e != cudaSuccess) return e;
-        if (prev != dev) {
-            e = cudaSetDevice(dev);
-            changed = e == cudaSuccess;
-        }
-        return e;
-    }
-    ~DeviceGuard() {
-        if (changed) cudaSetDevice(prev);
-    }
-};
 
 const QcDev& code_of(const ldpc_graph* g, QcDev*) { return g->qc; }
 const CsrDev& code_of(const ldpc_graph* g, CsrDev*) { return g->csr; }
@@ -351,8 +288,14 @@ ldpc_status launch_decode(Workspace& ws, const Job& job, const ldpc_decode_opts&
     // group barriers cleared; the queue of waiting frames starts after the first `slots`
     init_ctrl_kernel<<<1, 256, 0, stream>>>(ws.ctrl, groups, std::min(slots, frames), p.unsat, 2 * slots);
     LDPC_TRY(cudaGetLastError());
-    pack_syndrome_kernel<<<(unsigned)std::max(1, std::min(frames, sms * 8)), 256, 0, stream>>>(
-        job.syndrome, frames, pi, (unsigned*)(base + L.sbits), ws.ctrl);
+    {
+        // about four words per warp; frames along y (grid-stride beyond 65535)
+        int max_words = 1;
+        for (int c = 0; c < job.ngraphs; ++c) max_words = std::max(max_words, pi.swords[c]);
+        const dim3 pgrid((unsigned)std::min((max_words + 31) / 32, 4096), (unsigned)std::max(1, std::min(frames, 65535)));
+        pack_syndrome_kernel<<<pgrid, 256, 0, stream>>>(job.syndrome, frames, pi, (unsigned*)(base + L.sbits),
+                                                        ws.ctrl);
+    }
     LDPC_TRY(cudaGetLastError());
     if (timing) LDPC_TRY(cudaEventRecord(ws.ev[1], stream));
     {
@@ -1084,8 +1027,8 @@ extern "C" ldpc_status ldpc_decode_qc_noalloc(int32_t mb, int32_t nb, int32_t Z,
         PackInfo pi{};
         pi.m[0] = m;
         pi.swords[0] = swords;
-        pack_syndrome_kernel<<<(unsigned)std::max(1, std::min(frames, sms * 8)), 256, 0, stream>>>(
-            syndrome, frames, pi, (unsigned*)(base + L.sbits), ctrl);
+        const dim3 pgrid((unsigned)std::max(1, std::min((swords + 31) / 32, 4096)), (unsigned)std::max(1, std::min(frames, 65535)));
+        pack_syndrome_kernel<<<pgrid, 256, 0, stream>>>(syndrome, frames, pi, (unsigned*)(base + L.sbits), ctrl);
         LDPC_TRY(cudaGetLastError());
     }
     void* args[] = {(void*)&p, (void*)&cs};

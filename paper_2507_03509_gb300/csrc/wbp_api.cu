@@ -1,0 +1,325 @@
+// C ABI of weighted belief propagation (ldpc_wbp_* in include/ldpc.h).
+//
+// Host side: builds the per-class lists of message slots, owns the plan's
+// workspace (allocated once at creation), and issues the stream-ordered
+// kernel sequences of wbp_kernels.cuh -- forward with checkpoints, loss,
+// backward with recomputation between checkpoints, gradient step.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <new>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/ldpc.h"
+#include "host_common.h"
+#include "wbp_kernels.cuh"
+
+using namespace ldpcgb;
+
+struct ldpc_wbp {
+    const ldpc_graph* graph = nullptr;
+    int device = 0;
+    int F = 0, T = 0, C = 0, every = 1, fp64 = 0;
+    int m = 0, n = 0;
+    long long E = 0;
+    int nckpt = 0;               // checkpoints kept by the forward pass (iterations every, 2 every, ... < T)
+    int nseg = 0;                // recomputed iterations held during the backward pass (every - 1)
+    bool saved = false;          // a forward pass has stored checkpoints
+    void* tables = nullptr;      // cls | class_ptr | class_slot
+    const int* cls = nullptr;
+    const int* class_ptr = nullptr;
+    const int* class_slot = nullptr;
+    void* buf = nullptr;
+    size_t elem = 4;
+    // state, offsets into buf
+    char* c2v_work = nullptr;    // [F][E]
+    char* app_work = nullptr;    // [F][n]
+    std::vector<char*> ck_c2v, ck_app;    // [nckpt] of [F][E] / [F][n]
+    std::vector<char*> seg_c2v, seg_app;  // [nseg]
+    char* G = nullptr;           // [F][E]
+    char* pbuf = nullptr;        // [F][E]
+    double* partial = nullptr;   // loss partial sums [loss_blocks]
+    int loss_blocks = 0;
+    int grid_cn = 1, grid_vn = 1, grid_w = 1;
+};
+
+namespace {
+
+template <typename T, class Code>
+struct Runner {
+    ldpc_wbp* p;
+    Code code;
+    cudaStream_t s;
+
+    wbp::Args<T> base(const float* llr, const uint8_t* syn) const {
+        wbp::Args<T> a{};
+        a.F = p->F;
+        a.m = p->m;
+        a.n = p->n;
+        a.E = p->E;
+        a.lmax = T(25);
+        a.llr = llr;
+        a.syn = syn;
+        a.cls = p->cls;
+        return a;
+    }
+    // iteration k (1-based) forward: c2v^(k) into c2v_dst, APP^(k) into app_dst
+    ldpc_status fwd(const float* llr, const uint8_t* syn, const T* w, int k, const T* c2v_prev,
+                    const T* app_prev, T* c2v_dst, T* app_dst) const {
+        wbp::Args<T> a = base(llr, syn);
+        a.w = w + (size_t)(k - 1) * p->C;
+        a.c2v_prev = c2v_prev;
+        a.app_prev = app_prev;
+        a.c2v_out = c2v_dst;
+        a.app_out = app_dst;
+        wbp::cn_kernel<false, T, Code><<<p->grid_cn, wbp::kThreads, 0, s>>>(a, code);
+        LDPC_TRY(cudaGetLastError());
+        wbp::vn_fwd_kernel<T, Code><<<p->grid_vn, wbp::kThreads, 0, s>>>(a, code);
+        LDPC_TRY(cudaGetLastError());
+        return LDPC_OK;
+    }
+    T* ck_c2v(int i) const { return (T*)p->ck_c2v[i]; }
+    T* ck_app(int i) const { return (T*)p->ck_app[i]; }
+
+    ldpc_status forward(const float* llr, const uint8_t* syn, const T* w, T* app_out, bool save) {
+        const T* cprev = nullptr;
+        const T* aprev = nullptr;
+        for (int k = 1; k <= p->T; ++k) {
+            T* cdst = (T*)p->c2v_work;
+            T* adst = k == p->T ? app_out : (T*)p->app_work;
+            if (save && k % p->every == 0 && k < p->T) {
+                cdst = ck_c2v(k / p->every - 1);
+                adst = ck_app(k / p->every - 1);
+            }
+            ldpc_status st = fwd(llr, syn, w, k, cprev, aprev, cdst, adst);
+            if (st != LDPC_OK) return st;
+            cprev = cdst;
+            aprev = adst;
+        }
+        return LDPC_OK;
+    }
+
+    ldpc_status backward(const float* llr, const uint8_t* syn, const T* w, const T* grad_app, T* gw, T* gl) {
+        wbp::Args<T> a = base(llr, syn);
+        a.G = (T*)p->G;
+        a.pbuf = (T*)p->pbuf;
+        a.grad_llr = gl;
+        wbp::seed_kernel<T, Code><<<p->grid_vn, wbp::kThreads, 0, s>>>(a, code, grad_app);
+        LDPC_TRY(cudaGetLastError());
+        const int every = p->every;
+        const int nseg_total = (p->T + every - 1) / every;
+        for (int sg = nseg_total - 1; sg >= 0; --sg) {
+            const int k0 = sg * every, k1 = std::min((sg + 1) * every, p->T);
+            const T* c0 = k0 == 0 ? nullptr : ck_c2v(sg - 1);
+            const T* a0 = k0 == 0 ? nullptr : ck_app(sg - 1);
+            // recompute c2v^(k), APP^(k) for k0 < k < k1
+            for (int k = k0 + 1; k < k1; ++k) {
+                const T* cp = k - 1 == k0 ? c0 : (T*)p->seg_c2v[k - 1 - k0 - 1];
+                const T* ap = k - 1 == k0 ? a0 : (T*)p->seg_app[k - 1 - k0 - 1];
+                ldpc_status st = fwd(llr, syn, w, k, cp, ap, (T*)p->seg_c2v[k - k0 - 1], (T*)p->seg_app[k - k0 - 1]);
+                if (st != LDPC_OK) return st;
+            }
+            for (int k = k1; k > k0; --k) {
+                a.w = w + (size_t)(k - 1) * p->C;
+                a.c2v_prev = k - 1 == k0 ? c0 : (T*)p->seg_c2v[k - 1 - k0 - 1];
+                a.app_prev = k - 1 == k0 ? a0 : (T*)p->seg_app[k - 1 - k0 - 1];
+                wbp::cn_kernel<true, T, Code><<<p->grid_cn, wbp::kThreads, 0, s>>>(a, code);
+                LDPC_TRY(cudaGetLastError());
+                wbp::wgrad_kernel<T><<<p->grid_w, wbp::kThreads, 0, s>>>(
+                    (const T*)p->pbuf, p->F, p->E, p->class_ptr, p->class_slot, p->C, gw + (size_t)(k - 1) * p->C);
+                LDPC_TRY(cudaGetLastError());
+                wbp::vn_bwd_kernel<T, Code><<<p->grid_vn, wbp::kThreads, 0, s>>>(a, code);
+                LDPC_TRY(cudaGetLastError());
+            }
+        }
+        return LDPC_OK;
+    }
+};
+
+template <class Fn>
+ldpc_status dispatch(ldpc_wbp* p, cudaStream_t s, Fn&& fn) {
+    if (p->graph->kind == 1) {
+        if (p->fp64) return fn(Runner<double, QcDev>{p, p->graph->qc, s});
+        return fn(Runner<float, QcDev>{p, p->graph->qc, s});
+    }
+    if (p->fp64) return fn(Runner<double, CsrDev>{p, p->graph->csr, s});
+    return fn(Runner<float, CsrDev>{p, p->graph->csr, s});
+}
+
+void release(ldpc_wbp* p) {
+    if (p->tables) cudaFree(p->tables);
+    if (p->buf) cudaFree(p->buf);
+    p->tables = nullptr;
+    p->buf = nullptr;
+}
+
+int grid_for(long long items, int sms) {
+    const long long blocks = (items + wbp::kThreads - 1) / wbp::kThreads;
+    return (int)std::max(1LL, std::min(blocks, (long long)sms * 16));
+}
+
+}  // namespace
+
+extern "C" {
+
+ldpc_status ldpc_wbp_create(const ldpc_graph* graph, int32_t frames, int32_t iters, int32_t n_classes,
+                            const int32_t* edge_class, int32_t checkpoint_every, int32_t fp64, ldpc_wbp** out) {
+    if (!out) return LDPC_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!graph || frames < 1 || iters < 1 || n_classes < 1 || !edge_class || checkpoint_every < 1 ||
+        (fp64 != 0 && fp64 != 1))
+        return LDPC_ERR_INVALID_ARG;
+    if ((long long)frames * graph->E > (1LL << 36) || (long long)frames * graph->m > (1LL << 40))
+        return LDPC_ERR_INVALID_ARG;
+    const int Z = graph->Z;
+    const long long nkeys = graph->kind == 1 ? graph->nblk : graph->E;
+    for (long long i = 0; i < nkeys; ++i)
+        if (edge_class[i] < 0 || edge_class[i] >= n_classes) return LDPC_ERR_INVALID_ARG;
+    // per-class message slots (class order, then ascending slot)
+    std::vector<int> cnt((size_t)n_classes + 1, 0);
+    for (long long i = 0; i < nkeys; ++i) cnt[edge_class[i] + 1] += graph->kind == 1 ? Z : 1;
+    for (int c = 0; c < n_classes; ++c) cnt[c + 1] += cnt[c];
+    std::vector<int> slots((size_t)std::max<long long>(graph->E, 1));
+    std::vector<int> fill(cnt.begin(), cnt.end() - 1);
+    for (long long i = 0; i < nkeys; ++i) {
+        const int c = edge_class[i];
+        if (graph->kind == 1) {
+            for (int p = 0; p < Z; ++p) slots[fill[c]++] = (int)(i * Z + p);
+        } else {
+            slots[fill[c]++] = (int)i;
+        }
+    }
+    ldpc_wbp* p = new (std::nothrow) ldpc_wbp();
+    if (!p) return LDPC_ERR_OOM;
+    p->graph = graph;
+    p->device = graph->device;
+    p->F = frames;
+    p->T = iters;
+    p->C = n_classes;
+    p->every = std::min(checkpoint_every, iters);
+    p->fp64 = fp64;
+    p->m = graph->m;
+    p->n = graph->n;
+    p->E = graph->E;
+    p->elem = fp64 ? sizeof(double) : sizeof(float);
+    p->nckpt = (iters - 1) / p->every;
+    p->nseg = p->every - 1;
+    DeviceGuard guard;
+    cudaError_t ce = guard.enter(p->device);
+    int sms = 0;
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    const size_t tb_cls = align_up((size_t)nkeys * 4, 256), tb_ptr = align_up(((size_t)n_classes + 1) * 4, 256);
+    const size_t tb_slot = align_up(slots.size() * 4, 256);
+    if (ce == cudaSuccess) ce = cudaMalloc(&p->tables, tb_cls + tb_ptr + tb_slot);
+    if (ce == cudaSuccess) {
+        char* t = (char*)p->tables;
+        ce = cudaMemcpy(t, edge_class, (size_t)nkeys * 4, cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess) ce = cudaMemcpy(t + tb_cls, cnt.data(), cnt.size() * 4, cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpy(t + tb_cls + tb_ptr, slots.data(), slots.size() * 4, cudaMemcpyHostToDevice);
+        p->cls = (const int*)t;
+        p->class_ptr = (const int*)(t + tb_cls);
+        p->class_slot = (const int*)(t + tb_cls + tb_ptr);
+    }
+    // workspace: work c2v/APP, checkpoints, recompute segment, adjoint state, loss partials
+    const size_t sE = align_up((size_t)frames * (size_t)graph->E * p->elem, 256);
+    const size_t sN = align_up((size_t)frames * (size_t)graph->n * p->elem, 256);
+    p->loss_blocks = grid_for((long long)frames * graph->n, std::max(sms, 1));
+    const size_t total = sE + sN + (size_t)p->nckpt * (sE + sN) + (size_t)p->nseg * (sE + sN) + 2 * sE +
+                         align_up((size_t)p->loss_blocks * sizeof(double), 256);
+    if (ce == cudaSuccess) ce = cudaMalloc(&p->buf, total);
+    if (ce != cudaSuccess) {
+        release(p);
+        delete p;
+        return cuda_status(ce);
+    }
+    char* b = (char*)p->buf;
+    p->c2v_work = b; b += sE;
+    p->app_work = b; b += sN;
+    for (int i = 0; i < p->nckpt; ++i) { p->ck_c2v.push_back(b); b += sE; p->ck_app.push_back(b); b += sN; }
+    for (int i = 0; i < p->nseg; ++i) { p->seg_c2v.push_back(b); b += sE; p->seg_app.push_back(b); b += sN; }
+    p->G = b; b += sE;
+    p->pbuf = b; b += sE;
+    p->partial = (double*)b;
+    p->grid_cn = grid_for((long long)frames * graph->m, sms);
+    p->grid_vn = grid_for((long long)frames * graph->n, sms);
+    p->grid_w = std::min(n_classes, sms * 16);
+    *out = p;
+    return LDPC_OK;
+}
+
+void ldpc_wbp_destroy(ldpc_wbp* p) {
+    if (!p) return;
+    DeviceGuard guard;
+    guard.enter(p->device);
+    release(p);
+    delete p;
+}
+
+ldpc_status ldpc_wbp_forward(ldpc_wbp* p, const float* llr, const uint8_t* syndrome, const void* weights,
+                             void* app_out, int32_t save_for_backward, void* cuda_stream) {
+    if (!p || !llr || !syndrome || !weights || !app_out) return LDPC_ERR_INVALID_ARG;
+    DeviceGuard guard;
+    LDPC_TRY(guard.enter(p->device));
+    const bool save = save_for_backward != 0;
+    ldpc_status st = dispatch(p, (cudaStream_t)cuda_stream, [&](auto r) {
+        using T = std::remove_pointer_t<decltype(r.ck_c2v(0))>;
+        return r.forward(llr, syndrome, (const T*)weights, (T*)app_out, save);
+    });
+    if (st == LDPC_OK && save) p->saved = true;
+    return st;
+}
+
+ldpc_status ldpc_wbp_loss(ldpc_wbp* p, const void* app, const uint8_t* x, void* loss_out, void* grad_app,
+                          void* cuda_stream) {
+    if (!p || !app || !x || !loss_out) return LDPC_ERR_INVALID_ARG;
+    DeviceGuard guard;
+    LDPC_TRY(guard.enter(p->device));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const long long total = (long long)p->F * p->n;
+    const double scale = 1.0 / (double)total;
+    if (p->fp64) {
+        wbp::loss_kernel<double><<<p->loss_blocks, wbp::kThreads, 0, s>>>((const double*)app, x, total, scale,
+                                                                          (double*)grad_app, p->partial);
+        LDPC_TRY(cudaGetLastError());
+        wbp::loss_final_kernel<double><<<1, 32, 0, s>>>(p->partial, p->loss_blocks, scale, (double*)loss_out);
+    } else {
+        wbp::loss_kernel<float><<<p->loss_blocks, wbp::kThreads, 0, s>>>((const float*)app, x, total, scale,
+                                                                        (float*)grad_app, p->partial);
+        LDPC_TRY(cudaGetLastError());
+        wbp::loss_final_kernel<float><<<1, 32, 0, s>>>(p->partial, p->loss_blocks, scale, (float*)loss_out);
+    }
+    LDPC_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
+ldpc_status ldpc_wbp_backward(ldpc_wbp* p, const float* llr, const uint8_t* syndrome, const void* weights,
+                              const void* grad_app, void* grad_weights, void* grad_llr, void* cuda_stream) {
+    if (!p || !llr || !syndrome || !weights || !grad_app || !grad_weights) return LDPC_ERR_INVALID_ARG;
+    if (p->nckpt > 0 && !p->saved) return LDPC_ERR_INVALID_ARG;
+    DeviceGuard guard;
+    LDPC_TRY(guard.enter(p->device));
+    return dispatch(p, (cudaStream_t)cuda_stream, [&](auto r) {
+        using T = std::remove_pointer_t<decltype(r.ck_c2v(0))>;
+        return r.backward(llr, syndrome, (const T*)weights, (const T*)grad_app, (T*)grad_weights, (T*)grad_llr);
+    });
+}
+
+ldpc_status ldpc_wbp_sgd_step(ldpc_wbp* p, void* weights, const void* grad, double lr, void* cuda_stream) {
+    if (!p || !weights || !grad) return LDPC_ERR_INVALID_ARG;
+    DeviceGuard guard;
+    LDPC_TRY(guard.enter(p->device));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    const int count = p->T * p->C;
+    const int grid = std::max(1, std::min((count + 255) / 256, 1024));
+    if (p->fp64)
+        wbp::sgd_kernel<double><<<grid, 256, 0, s>>>((double*)weights, (const double*)grad, count, lr);
+    else
+        wbp::sgd_kernel<float><<<grid, 256, 0, s>>>((float*)weights, (const float*)grad, count, (float)lr);
+    LDPC_TRY(cudaGetLastError());
+    return LDPC_OK;
+}
+
+}  // extern "C"

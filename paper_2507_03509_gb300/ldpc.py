@@ -39,7 +39,9 @@ RULES = {"none": LDPC_TERM_NONE, "pce": LDPC_TERM_PCE, "pce_vnr": LDPC_TERM_PCE_
 EXPORTED = ("ldpc_decode_opts_init", "ldpc_graph_create_csr", "ldpc_graph_create_qc",
             "ldpc_graph_destroy", "ldpc_graph_info", "ldpc_decode", "ldpc_decode_host",
             "ldpc_status_str", "ldpc_decode_qc_noalloc", "ldpc_batch_create", "ldpc_batch_destroy",
-            "ldpc_batch_info", "ldpc_batch_decode", "ldpc_batch_decode_async", "ldpc_batch_autotune")
+            "ldpc_batch_info", "ldpc_batch_decode", "ldpc_batch_decode_async", "ldpc_batch_autotune",
+            "ldpc_wbp_create", "ldpc_wbp_destroy", "ldpc_wbp_forward", "ldpc_wbp_loss", "ldpc_wbp_backward",
+            "ldpc_wbp_sgd_step")
 
 NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 
@@ -101,6 +103,18 @@ def _load():
     lib.ldpc_batch_autotune.argtypes = [P, P, P, i32, ctypes.c_int, P, P, P, P, ctypes.POINTER(i32),
                                         ctypes.POINTER(i32)]
     lib.ldpc_batch_autotune.restype = ctypes.c_int
+    lib.ldpc_wbp_create.argtypes = [P, i32, i32, i32, P, i32, i32, pg]
+    lib.ldpc_wbp_create.restype = ctypes.c_int
+    lib.ldpc_wbp_destroy.argtypes = [P]
+    lib.ldpc_wbp_destroy.restype = None
+    lib.ldpc_wbp_forward.argtypes = [P, P, P, P, P, i32, P]
+    lib.ldpc_wbp_forward.restype = ctypes.c_int
+    lib.ldpc_wbp_loss.argtypes = [P, P, P, P, P, P]
+    lib.ldpc_wbp_loss.restype = ctypes.c_int
+    lib.ldpc_wbp_backward.argtypes = [P, P, P, P, P, P, P, P]
+    lib.ldpc_wbp_backward.restype = ctypes.c_int
+    lib.ldpc_wbp_sgd_step.argtypes = [P, P, P, ctypes.c_double, P]
+    lib.ldpc_wbp_sgd_step.restype = ctypes.c_int
     return lib
 
 
@@ -209,7 +223,16 @@ class Graph:
     @classmethod
     def from_qc(cls, shifts, Z):
         shifts = np.asarray(shifts)
-        return cls(ldpc_graph_create_qc(shifts.shape[0], shifts.shape[1], Z, shifts))
+        g = cls(ldpc_graph_create_qc(shifts.shape[0], shifts.shape[1], Z, shifts))
+        g.qc_blocks = int((shifts >= 0).sum())
+        return g
+
+    qc_blocks = None  # nonzero base blocks of a QC graph (None for CSR graphs)
+
+    @property
+    def class_keys(self) -> int:
+        """Entries an edge-class map of this graph has (QC: base blocks, CSR: edges)."""
+        return self.qc_blocks if self.qc_blocks is not None else self.edges
 
     @classmethod
     def from_code(cls, code):
@@ -347,7 +370,8 @@ class Batch:
         self.handle = ldpc_batch_create([g.handle for g in self.graphs], frame_graph)
         self.frames, self.llr_len, self.syndrome_len = ldpc_batch_info(self.handle)
 
-    def _out(self, device):
+    def outputs(self, device):
+        """Fresh (bits, flags, iters) device tensors for this batch."""
         import torch
         return (torch.empty(self.llr_len, dtype=torch.uint8, device=device),
                 torch.empty(self.frames, dtype=torch.uint8, device=device),
@@ -356,7 +380,7 @@ class Batch:
     def decode(self, llr, syndrome, max_iter, rule="pce_vnr", out=None, stream=None, **opt):
         import torch
         rule = RULES[rule] if isinstance(rule, str) else int(rule)
-        out = out or self._out(llr.device)
+        out = out or self.outputs(llr.device)
         s = stream if stream is not None else torch.cuda.current_stream(llr.device)
         _check(ldpc_batch_decode(self.handle, llr.data_ptr(), syndrome.data_ptr(), max_iter, rule,
                                  out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr(), make_opts(**opt),
@@ -375,7 +399,7 @@ class Batch:
     def autotune(self, llr, syndrome, max_iter, rule="pce_vnr", out=None, stream=None):
         import torch
         rule = RULES[rule] if isinstance(rule, str) else int(rule)
-        out = out or self._out(llr.device)
+        out = out or self.outputs(llr.device)
         s = stream if stream is not None else torch.cuda.current_stream(llr.device)
         return ldpc_batch_autotune(self.handle, llr.data_ptr(), syndrome.data_ptr(), max_iter, rule,
                                    out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr(), s.cuda_stream)
@@ -390,3 +414,136 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+# --------------------------------------------------------------------------
+# Weighted belief propagation (trainable decoder)
+# --------------------------------------------------------------------------
+def ldpc_wbp_create(graph_handle: int, frames: int, iters: int, n_classes: int, edge_class,
+                    checkpoint_every: int, fp64: int) -> int:
+    cls = np.ascontiguousarray(edge_class, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(_lib.ldpc_wbp_create(graph_handle, int(frames), int(iters), int(n_classes), cls.ctypes.data,
+                                int(checkpoint_every), int(fp64), ctypes.byref(h)), "ldpc_wbp_create")
+    return h.value
+
+
+def ldpc_wbp_destroy(handle: int) -> None:
+    _lib.ldpc_wbp_destroy(handle)
+
+
+def ldpc_wbp_forward(handle, llr_ptr, syndrome_ptr, weights_ptr, app_ptr, save_for_backward, stream) -> int:
+    return _lib.ldpc_wbp_forward(handle, llr_ptr, syndrome_ptr, weights_ptr, app_ptr, int(save_for_backward),
+                                 stream)
+
+
+def ldpc_wbp_loss(handle, app_ptr, x_ptr, loss_ptr, grad_app_ptr, stream) -> int:
+    return _lib.ldpc_wbp_loss(handle, app_ptr, x_ptr, loss_ptr, grad_app_ptr, stream)
+
+
+def ldpc_wbp_backward(handle, llr_ptr, syndrome_ptr, weights_ptr, grad_app_ptr, grad_w_ptr, grad_llr_ptr,
+                      stream) -> int:
+    return _lib.ldpc_wbp_backward(handle, llr_ptr, syndrome_ptr, weights_ptr, grad_app_ptr, grad_w_ptr,
+                                  grad_llr_ptr, stream)
+
+
+def ldpc_wbp_sgd_step(handle, weights_ptr, grad_ptr, lr, stream) -> int:
+    return _lib.ldpc_wbp_sgd_step(handle, weights_ptr, grad_ptr, float(lr), stream)
+
+
+class WeightedBP:
+    """A weighted-BP plan (ldpc_wbp): `frames` frames of `graph`, `iters`
+    unrolled iterations, weights [iters, n_classes] of the plan's dtype
+    (float32, or float64 with fp64=True).  edge_class: QC graphs one class per
+    nonzero base block (row-major), CSR graphs one per edge (CSR order)."""
+
+    def __init__(self, graph: Graph, frames: int, iters: int, edge_class, n_classes: int,
+                 checkpoint_every: int = 5, fp64: bool = False):
+        self.graph = graph
+        self.frames, self.iters, self.n_classes = int(frames), int(iters), int(n_classes)
+        self.fp64 = bool(fp64)
+        edge_class = np.ascontiguousarray(edge_class, dtype=np.int32)
+        if edge_class.shape != (graph.class_keys,):
+            raise ValueError(f"edge_class needs {graph.class_keys} entries, got {edge_class.shape}")
+        self.handle = None
+        self.handle = ldpc_wbp_create(graph.handle, frames, iters, n_classes, edge_class, checkpoint_every,
+                                      int(self.fp64))
+        self.generation = 0  # forward passes with save_for_backward so far
+
+    @property
+    def dtype(self):
+        import torch
+        return torch.float64 if self.fp64 else torch.float32
+
+    def _stream(self, t, stream):
+        import torch
+        return (stream if stream is not None else torch.cuda.current_stream(t.device)).cuda_stream
+
+    def forward(self, llr, syndrome, weights, app=None, save=True, stream=None):
+        import torch
+        app = app if app is not None else torch.empty((self.frames, self.graph.n), dtype=self.dtype,
+                                                      device=llr.device)
+        _check(ldpc_wbp_forward(self.handle, llr.data_ptr(), syndrome.data_ptr(), weights.data_ptr(),
+                                app.data_ptr(), save, self._stream(llr, stream)), "ldpc_wbp_forward")
+        if save:
+            self.generation += 1
+        return app
+
+    def loss(self, app, x, want_grad=True, stream=None):
+        """Mean binary cross-entropy of the soft output against x; returns
+        (loss [1] tensor, dloss/dAPP or None)."""
+        import torch
+        loss = torch.empty(1, dtype=self.dtype, device=app.device)
+        g = torch.empty_like(app) if want_grad else None
+        _check(ldpc_wbp_loss(self.handle, app.data_ptr(), x.data_ptr(), loss.data_ptr(),
+                             g.data_ptr() if g is not None else None, self._stream(app, stream)), "ldpc_wbp_loss")
+        return loss, g
+
+    def backward(self, llr, syndrome, weights, grad_app, want_llr=False, grad_w=None, stream=None):
+        import torch
+        gw = grad_w if grad_w is not None else torch.empty_like(weights)
+        gl = torch.empty((self.frames, self.graph.n), dtype=self.dtype, device=llr.device) if want_llr else None
+        _check(ldpc_wbp_backward(self.handle, llr.data_ptr(), syndrome.data_ptr(), weights.data_ptr(),
+                                 grad_app.data_ptr(), gw.data_ptr(), gl.data_ptr() if gl is not None else None,
+                                 self._stream(llr, stream)), "ldpc_wbp_backward")
+        return gw, gl
+
+    def sgd_step(self, weights, grad, lr, stream=None):
+        _check(ldpc_wbp_sgd_step(self.handle, weights.data_ptr(), grad.data_ptr(), lr,
+                                 self._stream(weights, stream)), "ldpc_wbp_sgd_step")
+
+    def close(self):
+        if self.handle:
+            ldpc_wbp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def weighted_bp(plan: WeightedBP, weights, llr, syndrome):
+    """APP after the plan's iterations as a differentiable function of the
+    weights (and of the channel LLRs), for torch.autograd."""
+    import torch
+
+    class _WBP(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, w, l):
+            app = plan.forward(l, syndrome, w.contiguous(), save=True)
+            ctx.save_for_backward(w, l)
+            ctx.generation = plan.generation
+            return app
+
+        @staticmethod
+        def backward(ctx, grad_app):
+            w, l = ctx.saved_tensors
+            if plan.generation != ctx.generation:  # another forward replaced the checkpoints
+                plan.forward(l, syndrome, w.contiguous(), save=True)
+            gw, gl = plan.backward(l, syndrome, w.contiguous(), grad_app.contiguous().to(plan.dtype),
+                                   want_llr=ctx.needs_input_grad[1])
+            return gw, (gl.to(l.dtype) if gl is not None else None)
+
+    return _WBP.apply(weights, llr)

@@ -75,7 +75,7 @@ def test_batch_async_replays_in_a_cuda_graph():
     dev = torch.device("cuda:0")
     s_llr = torch.from_numpy(llr1).to(dev)
     s_syn = torch.from_numpy(syn1).to(dev)
-    out = batch._out(dev)
+    out = batch.outputs(dev)
     status = torch.full((1,), -1, dtype=torch.int32, device=dev)
     ref1 = [t.clone() for t in batch.decode(s_llr, s_syn, 80, "pce_vnr")]        # sizes the workspace
     ref2 = [t.clone() for t in batch.decode(torch.from_numpy(llr2).to(dev), s_syn, 80, "pce_vnr")]
