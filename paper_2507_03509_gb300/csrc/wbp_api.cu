@@ -43,6 +43,14 @@ struct ldpc_wbp {
     double* partial = nullptr;   // loss partial sums [loss_blocks]
     int loss_blocks = 0;
     int grid_cn = 1, grid_vn = 1, grid_w = 1;
+    // QC plans: tiled kernels, per-tile sums of G * t, classes as lists of blocks
+    int tiles_cn = 1;            // check tiles per base row
+    int fpc_cn = 1, fpc_vn = 1;  // frames per CTA group, check / variable side
+    int groups_cn = 1;
+    long long grid_qcn = 1, grid_qvn = 1;
+    double* wpart = nullptr;     // [groups_cn][nblk][tiles_cn]
+    const int* cblk_ptr = nullptr;
+    const int* cblk = nullptr;
 };
 
 namespace {
@@ -65,6 +73,9 @@ struct Runner {
         a.cls = p->cls;
         return a;
     }
+    static constexpr bool kQc = std::is_same_v<Code, QcDev>;
+    static bool aligned(const void* ptr) { return ptr == nullptr || ((uintptr_t)ptr % 16) == 0; }
+
     // iteration k (1-based) forward: c2v^(k) into c2v_dst, APP^(k) into app_dst
     ldpc_status fwd(const float* llr, const uint8_t* syn, const T* w, int k, const T* c2v_prev,
                     const T* app_prev, T* c2v_dst, T* app_dst) const {
@@ -74,9 +85,18 @@ struct Runner {
         a.app_prev = app_prev;
         a.c2v_out = c2v_dst;
         a.app_out = app_dst;
-        wbp::cn_kernel<false, T, Code><<<p->grid_cn, wbp::kThreads, 0, s>>>(a, code);
-        LDPC_TRY(cudaGetLastError());
-        wbp::vn_fwd_kernel<T, Code><<<p->grid_vn, wbp::kThreads, 0, s>>>(a, code);
+        if constexpr (kQc) {
+            a.vec = p->graph->Z % 4 == 0 && aligned(llr) && aligned(app_dst);
+            wbp::qc_cn_kernel<false, T><<<(unsigned)p->grid_qcn, wbp::kThreads, 0, s>>>(a, code, p->tiles_cn,
+                                                                                          p->fpc_cn, nullptr);
+            LDPC_TRY(cudaGetLastError());
+            wbp::qc_vn_kernel<wbp::kVnFwd, T><<<(unsigned)p->grid_qvn, wbp::kThreads, 0, s>>>(a, code, p->fpc_vn,
+                                                                                              nullptr);
+        } else {
+            wbp::cn_kernel<false, T, Code><<<p->grid_cn, wbp::kThreads, 0, s>>>(a, code);
+            LDPC_TRY(cudaGetLastError());
+            wbp::vn_fwd_kernel<T, Code><<<p->grid_vn, wbp::kThreads, 0, s>>>(a, code);
+        }
         LDPC_TRY(cudaGetLastError());
         return LDPC_OK;
     }
@@ -106,7 +126,13 @@ struct Runner {
         a.G = (T*)p->G;
         a.pbuf = (T*)p->pbuf;
         a.grad_llr = gl;
-        wbp::seed_kernel<T, Code><<<p->grid_vn, wbp::kThreads, 0, s>>>(a, code, grad_app);
+        if constexpr (kQc) {
+            a.vec = p->graph->Z % 4 == 0 && aligned(llr) && aligned(grad_app) && aligned(gl);
+            wbp::qc_vn_kernel<wbp::kVnSeed, T><<<(unsigned)p->grid_qvn, wbp::kThreads, 0, s>>>(a, code, p->fpc_vn,
+                                                                                               grad_app);
+        } else {
+            wbp::seed_kernel<T, Code><<<p->grid_vn, wbp::kThreads, 0, s>>>(a, code, grad_app);
+        }
         LDPC_TRY(cudaGetLastError());
         const int every = p->every;
         const int nseg_total = (p->T + every - 1) / every;
@@ -125,12 +151,25 @@ struct Runner {
                 a.w = w + (size_t)(k - 1) * p->C;
                 a.c2v_prev = k - 1 == k0 ? c0 : (T*)p->seg_c2v[k - 1 - k0 - 1];
                 a.app_prev = k - 1 == k0 ? a0 : (T*)p->seg_app[k - 1 - k0 - 1];
-                wbp::cn_kernel<true, T, Code><<<p->grid_cn, wbp::kThreads, 0, s>>>(a, code);
-                LDPC_TRY(cudaGetLastError());
-                wbp::wgrad_kernel<T><<<p->grid_w, wbp::kThreads, 0, s>>>(
-                    (const T*)p->pbuf, p->F, p->E, p->class_ptr, p->class_slot, p->C, gw + (size_t)(k - 1) * p->C);
-                LDPC_TRY(cudaGetLastError());
-                wbp::vn_bwd_kernel<T, Code><<<p->grid_vn, wbp::kThreads, 0, s>>>(a, code);
+                if constexpr (kQc) {
+                    wbp::qc_cn_kernel<true, T><<<(unsigned)p->grid_qcn, wbp::kThreads, 0, s>>>(
+                        a, code, p->tiles_cn, p->fpc_cn, p->wpart);
+                    LDPC_TRY(cudaGetLastError());
+                    wbp::class_reduce_kernel<T><<<p->grid_w, wbp::kThreads, 0, s>>>(
+                        p->wpart, p->groups_cn, p->graph->nblk, p->tiles_cn, p->cblk_ptr, p->cblk, p->C,
+                        gw + (size_t)(k - 1) * p->C);
+                    LDPC_TRY(cudaGetLastError());
+                    wbp::qc_vn_kernel<wbp::kVnBwd, T><<<(unsigned)p->grid_qvn, wbp::kThreads, 0, s>>>(
+                        a, code, p->fpc_vn, nullptr);
+                } else {
+                    wbp::cn_kernel<true, T, Code><<<p->grid_cn, wbp::kThreads, 0, s>>>(a, code);
+                    LDPC_TRY(cudaGetLastError());
+                    wbp::wgrad_kernel<T><<<p->grid_w, wbp::kThreads, 0, s>>>(
+                        (const T*)p->pbuf, p->F, p->E, p->class_ptr, p->class_slot, p->C,
+                        gw + (size_t)(k - 1) * p->C);
+                    LDPC_TRY(cudaGetLastError());
+                    wbp::vn_bwd_kernel<T, Code><<<p->grid_vn, wbp::kThreads, 0, s>>>(a, code);
+                }
                 LDPC_TRY(cudaGetLastError());
             }
         }
@@ -210,24 +249,54 @@ ldpc_status ldpc_wbp_create(const ldpc_graph* graph, int32_t frames, int32_t ite
     cudaError_t ce = guard.enter(p->device);
     int sms = 0;
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    // QC: the blocks of each class (class order, ascending block)
+    std::vector<int> bptr((size_t)n_classes + 1, 0), blist((size_t)std::max<long long>(nkeys, 1));
+    if (graph->kind == 1) {
+        for (long long i = 0; i < nkeys; ++i) bptr[edge_class[i] + 1] += 1;
+        for (int c = 0; c < n_classes; ++c) bptr[c + 1] += bptr[c];
+        std::vector<int> bf(bptr.begin(), bptr.end() - 1);
+        for (long long i = 0; i < nkeys; ++i) blist[bf[edge_class[i]]++] = (int)i;
+    }
     const size_t tb_cls = align_up((size_t)nkeys * 4, 256), tb_ptr = align_up(((size_t)n_classes + 1) * 4, 256);
-    const size_t tb_slot = align_up(slots.size() * 4, 256);
-    if (ce == cudaSuccess) ce = cudaMalloc(&p->tables, tb_cls + tb_ptr + tb_slot);
+    const size_t tb_slot = align_up(slots.size() * 4, 256), tb_blist = align_up(blist.size() * 4, 256);
+    if (ce == cudaSuccess) ce = cudaMalloc(&p->tables, tb_cls + 2 * tb_ptr + tb_slot + tb_blist);
     if (ce == cudaSuccess) {
         char* t = (char*)p->tables;
         ce = cudaMemcpy(t, edge_class, (size_t)nkeys * 4, cudaMemcpyHostToDevice);
         if (ce == cudaSuccess) ce = cudaMemcpy(t + tb_cls, cnt.data(), cnt.size() * 4, cudaMemcpyHostToDevice);
         if (ce == cudaSuccess)
             ce = cudaMemcpy(t + tb_cls + tb_ptr, slots.data(), slots.size() * 4, cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpy(t + tb_cls + tb_ptr + tb_slot, bptr.data(), bptr.size() * 4, cudaMemcpyHostToDevice);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpy(t + tb_cls + 2 * tb_ptr + tb_slot, blist.data(), blist.size() * 4,
+                            cudaMemcpyHostToDevice);
         p->cls = (const int*)t;
         p->class_ptr = (const int*)(t + tb_cls);
         p->class_slot = (const int*)(t + tb_cls + tb_ptr);
+        p->cblk_ptr = (const int*)(t + tb_cls + tb_ptr + tb_slot);
+        p->cblk = (const int*)(t + tb_cls + 2 * tb_ptr + tb_slot);
     }
     // workspace: work c2v/APP, checkpoints, recompute segment, adjoint state, loss partials
     const size_t sE = align_up((size_t)frames * (size_t)graph->E * p->elem, 256);
     const size_t sN = align_up((size_t)frames * (size_t)graph->n * p->elem, 256);
     p->loss_blocks = grid_for((long long)frames * graph->n, std::max(sms, 1));
-    const size_t total = sE + sN + (size_t)p->nckpt * (sE + sN) + (size_t)p->nseg * (sE + sN) + 2 * sE +
+    const bool qc = graph->kind == 1;
+    if (qc) {
+        // frame groups sized for about four waves of resident CTAs (4 per SM)
+        const long long waves = 4LL * std::max(sms, 1) * 4;
+        p->tiles_cn = (Z + wbp::kQcCnTile - 1) / wbp::kQcCnTile;
+        const long long cn_items = (long long)frames * graph->mb * p->tiles_cn;
+        p->fpc_cn = (int)std::max(1LL, std::min<long long>(frames, (cn_items + waves - 1) / waves));
+        p->groups_cn = (frames + p->fpc_cn - 1) / p->fpc_cn;
+        p->grid_qcn = std::min<long long>((long long)p->groups_cn * graph->mb * p->tiles_cn, 1LL << 24);
+        // variable side: about 4096 (frame, variable) pairs per CTA
+        p->fpc_vn = std::max(1, std::min(frames, 4096 / std::max(Z, 1)));
+        p->grid_qvn = std::min<long long>((long long)((frames + p->fpc_vn - 1) / p->fpc_vn) * graph->nb, 1LL << 24);
+    }
+    const size_t sP = qc ? 0 : sE;  // per-edge G * t (CSR plans only)
+    const size_t sW = qc ? align_up((size_t)p->groups_cn * graph->nblk * p->tiles_cn * sizeof(double), 256) : 0;
+    const size_t total = sE + sN + (size_t)p->nckpt * (sE + sN) + (size_t)p->nseg * (sE + sN) + sE + sP + sW +
                          align_up((size_t)p->loss_blocks * sizeof(double), 256);
     if (ce == cudaSuccess) ce = cudaMalloc(&p->buf, total);
     if (ce != cudaSuccess) {
@@ -241,7 +310,8 @@ ldpc_status ldpc_wbp_create(const ldpc_graph* graph, int32_t frames, int32_t ite
     for (int i = 0; i < p->nckpt; ++i) { p->ck_c2v.push_back(b); b += sE; p->ck_app.push_back(b); b += sN; }
     for (int i = 0; i < p->nseg; ++i) { p->seg_c2v.push_back(b); b += sE; p->seg_app.push_back(b); b += sN; }
     p->G = b; b += sE;
-    p->pbuf = b; b += sE;
+    p->pbuf = sP ? b : nullptr; b += sP;
+    p->wpart = sW ? (double*)b : nullptr; b += sW;
     p->partial = (double*)b;
     p->grid_cn = grid_for((long long)frames * graph->m, sms);
     p->grid_vn = grid_for((long long)frames * graph->n, sms);
@@ -284,12 +354,12 @@ ldpc_status ldpc_wbp_loss(ldpc_wbp* p, const void* app, const uint8_t* x, void* 
         wbp::loss_kernel<double><<<p->loss_blocks, wbp::kThreads, 0, s>>>((const double*)app, x, total, scale,
                                                                           (double*)grad_app, p->partial);
         LDPC_TRY(cudaGetLastError());
-        wbp::loss_final_kernel<double><<<1, 32, 0, s>>>(p->partial, p->loss_blocks, scale, (double*)loss_out);
+        wbp::loss_final_kernel<double><<<1, wbp::kThreads, 0, s>>>(p->partial, p->loss_blocks, scale, (double*)loss_out);
     } else {
         wbp::loss_kernel<float><<<p->loss_blocks, wbp::kThreads, 0, s>>>((const float*)app, x, total, scale,
                                                                         (float*)grad_app, p->partial);
         LDPC_TRY(cudaGetLastError());
-        wbp::loss_final_kernel<float><<<1, 32, 0, s>>>(p->partial, p->loss_blocks, scale, (float*)loss_out);
+        wbp::loss_final_kernel<float><<<1, wbp::kThreads, 0, s>>>(p->partial, p->loss_blocks, scale, (float*)loss_out);
     }
     LDPC_TRY(cudaGetLastError());
     return LDPC_OK;

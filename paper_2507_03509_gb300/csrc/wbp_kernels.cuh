@@ -58,6 +58,7 @@ struct Args {
     T* G;                          // [F][E] adjoint state (see above)
     T* pbuf;                       // [F][E] per-edge G * t
     T* grad_llr;                   // [F][n] or NULL
+    int vec;                       // QC variable side: 16-byte loads allowed (Z % 4 == 0, aligned buffers)
 };
 
 // ---- graph walks: check c -> (message slot, variable, class key) --------
@@ -217,9 +218,11 @@ __device__ __forceinline__ void check_d(const Args<T>& a, const Code& g, const C
     }
 }
 
-// Degree > 6: the same with loops over local arrays (O(d^3) derivative).
+// Degree > 6: the same with loops over local arrays (O(d^3) derivative).  With
+// acc, the products G * t are added to acc[k] instead of being stored per edge.
 template <bool BWD, typename T, class Code, class Ck>
-__device__ __noinline__ void check_n(const Args<T>& a, const Code& g, const Ck& ck, int f, int c) {
+__device__ __noinline__ void check_n(const Args<T>& a, const Code& g, const Ck& ck, int f, int c,
+                                     double* acc = nullptr) {
     const int d = ck.d;
     long long slot[kMaxDeg];
     int key[kMaxDeg];
@@ -239,7 +242,10 @@ __device__ __noinline__ void check_n(const Args<T>& a, const Code& g, const Ck& 
         T dt[kMaxDeg];
         for (int k = 0; k < d; ++k) {
             const T Gk = a.G[fe + slot[k]];
-            a.pbuf[fe + slot[k]] = Gk * o[k];
+            if (acc)
+                acc[k] += (double)(Gk * o[k]);
+            else
+                a.pbuf[fe + slot[k]] = Gk * o[k];
             dt[k] = Gk * a.w[__ldg(a.cls + key[k])];
         }
         const T sg = sbit ? T(-1) : T(1);
@@ -419,19 +425,355 @@ __global__ void __launch_bounds__(kThreads) loss_kernel(const T* app, const unsi
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
+// One CTA of kThreads: thread t adds partials t, t + kThreads, ... in order,
+// then a fixed-order block sum.
 template <typename T>
-__global__ void loss_final_kernel(const double* partial, int count, double scale, T* loss_out) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double s = 0.0;
-        for (int i = 0; i < count; ++i) s += partial[i];
-        *loss_out = (T)(s * scale);
-    }
+__global__ void __launch_bounds__(kThreads) loss_final_kernel(const double* partial, int count, double scale,
+                                                              T* loss_out) {
+    __shared__ double sm[kThreads / 32];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < count; i += kThreads) s += partial[i];
+    s = block_sum(s, sm);
+    if (threadIdx.x == 0) *loss_out = (T)(s * scale);
 }
 
 // Plain gradient step on the weights: w -= lr * g.
 template <typename T>
 __global__ void sgd_kernel(T* w, const T* g, int count, T lr) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) w[i] -= lr * g[i];
+}
+
+// ---------------------------------------------------------------------------
+// Quasi-cyclic kernels.  Work is split by base row (check side) or base
+// column (variable side) and by groups of `fpc` consecutive frames: a CTA
+// reads its row's or column's block table once and then streams through the
+// group's frames, so the dependent table loads are paid once per fpc frames
+// and every thread keeps a steady stream of independent loads in flight.
+//
+// Check side: a CTA covers kQcCnTile consecutive checks t of base row i (tile)
+// for each frame of its group, each thread kQcCPT checks per frame with all
+// their loads issued before any arithmetic.  In the adjoint it also sums
+// G * t per block over its checks and frames (per thread in the plan's type,
+// then a fixed-order FP64 block reduction) into wpart[(g * nblk + b) * tiles + tile],
+// g the frame group; class_reduce_kernel adds those up per class.
+//
+// Variable side: the group's (frame, variable) pairs of base column j are
+// walked four at a time per thread, as 16-byte vectors when a.vec is set
+// (message blocks are stored unrotated, so a column's messages are
+// contiguous; Z % 4 == 0 keeps four consecutive variables in one frame).
+// ---------------------------------------------------------------------------
+constexpr int kQcCPT = 2;
+constexpr int kQcCnTile = kThreads * kQcCPT;
+
+template <int D, bool BWD, typename T>
+__device__ __forceinline__ void qc_cn_rows(const Args<T>& a, const QcDev& q, int g, int fpc, int i, int tile, int b0,
+                                           double* wpart, int tiles, double* sm) {
+    const int Z = q.Z;
+    int sh[D], vo[D], mo[D];
+    T wk[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        sh[k] = __ldg(q.blk_shift + b0 + k);
+        vo[k] = __ldg(q.blk_col + b0 + k) * Z;
+        mo[k] = (b0 + k) * Z;
+        wk[k] = a.w[__ldg(a.cls + b0 + k)];
+    }
+    T acc[D];  // per-thread sums of G * t in the plan's type
+#pragma unroll
+    for (int k = 0; k < D; ++k) acc[k] = T(0);
+    const int f_end = min(a.F, (g + 1) * fpc);
+    for (int f = g * fpc; f < f_end; ++f) {
+        const size_t fe = (size_t)f * (size_t)a.E, fn = (size_t)f * (size_t)a.n;
+        const unsigned char* syn = a.syn + (size_t)f * a.m + (size_t)i * Z;
+        T u[kQcCPT][D], Gv[kQcCPT][D];
+        unsigned sb[kQcCPT];
+#pragma unroll
+        for (int r = 0; r < kQcCPT; ++r) {
+            const int t = tile * kQcCnTile + r * kThreads + (int)threadIdx.x;
+            if (t >= Z) continue;
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                int p = t + sh[k];
+                if (p >= Z) p -= Z;
+                u[r][k] = a.app_prev ? a.app_prev[fn + vo[k] + p] - a.c2v_prev[fe + mo[k] + p]
+                                     : (T)__ldg(a.llr + fn + vo[k] + p);
+                if constexpr (BWD) Gv[r][k] = a.G[fe + mo[k] + p];
+            }
+            sb[r] = __ldg(syn + t) != 0 ? 1u : 0u;
+        }
+#pragma unroll
+        for (int r = 0; r < kQcCPT; ++r) {
+            const int t = tile * kQcCnTile + r * kThreads + (int)threadIdx.x;
+            if (t >= Z) continue;
+            T av[D], o[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) av[k] = clampm(u[r][k], a.lmax);
+            cn_core<D>(av, sb[r], a.lmax, o);
+            if constexpr (!BWD) {
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    int p = t + sh[k];
+                    if (p >= Z) p -= Z;
+                    a.c2v_out[fe + mo[k] + p] = wk[k] * o[k];
+                }
+            } else {
+                T dt[D], da[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    acc[k] += Gv[r][k] * o[k];
+                    dt[k] = D == 1 ? T(0) : Gv[r][k] * wk[k];
+                }
+                const T sg = sb[r] ? T(-1) : T(1);
+                if constexpr (D == 1) {
+                    da[0] = T(0);
+                } else if constexpr (sizeof(T) == 4) {
+                    float rr[D];
+                    bool ng[D];
+#pragma unroll
+                    for (int k = 0; k < D; ++k) {
+                        rr[k] = __expf(-fabsf(av[k]));
+                        ng[k] = av[k] < 0.0f;
+                    }
+#pragma unroll
+                    for (int j = 0; j < D; ++j) {
+                        float s = 0.0f;
+#pragma unroll
+                        for (int e = 0; e < D; ++e)
+                            if (e != j) s = fmaf(dt[e], dbox<D>(rr, ng, e, j), s);
+                        da[j] = sg * s;
+                    }
+                } else {
+                    double th[D];
+#pragma unroll
+                    for (int k = 0; k < D; ++k) th[k] = tanh(0.5 * av[k]);
+#pragma unroll
+                    for (int j = 0; j < D; ++j) {
+                        double s = 0.0;
+#pragma unroll
+                        for (int e = 0; e < D; ++e)
+                            if (e != j) s += dt[e] * sg * dbox<D>(th, e, j);
+                        da[j] = s;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    int p = t + sh[j];
+                    if (p >= Z) p -= Z;
+                    a.G[fe + mo[j] + p] = absm(u[r][j]) <= a.lmax ? da[j] : T(0);
+                }
+            }
+        }
+    }
+    if constexpr (BWD) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const double s = block_sum((double)acc[k], sm);
+            if (threadIdx.x == 0) wpart[((size_t)g * q.nblk + b0 + k) * tiles + tile] = s;
+        }
+    }
+}
+
+// Rows of weight > 4: each thread runs the generic check for its checks (a
+// local copy of the arguments keeps the hot paths free of it).
+template <bool BWD, typename T>
+__device__ __noinline__ void qc_cn_rows_n(const Args<T> a, const QcDev q, int g, int fpc, int i, int tile, int b0,
+                                          int d, double* wpart, int tiles, double* sm) {
+    double acc[kMaxDeg];
+    for (int k = 0; k < d; ++k) acc[k] = 0.0;
+    const int f_end = min(a.F, (g + 1) * fpc);
+    for (int f = g * fpc; f < f_end; ++f) {
+        for (int r = 0; r < kQcCPT; ++r) {
+            const int t = tile * kQcCnTile + r * kThreads + (int)threadIdx.x;
+            if (t >= q.Z) continue;
+            QcCheck ck;
+            ck.b0 = b0;
+            ck.d = d;
+            ck.t = t;
+            check_n<BWD>(a, q, ck, f, i * q.Z + t, BWD ? acc : nullptr);
+        }
+    }
+    if constexpr (BWD) {
+        for (int k = 0; k < d; ++k) {
+            const double s = block_sum(acc[k], sm);
+            if (threadIdx.x == 0) wpart[((size_t)g * q.nblk + b0 + k) * tiles + tile] = s;
+        }
+    }
+}
+
+template <bool BWD, typename T>
+__global__ void __launch_bounds__(kThreads, 4) qc_cn_kernel(Args<T> a, QcDev q, int tiles, int fpc, double* wpart) {
+    __shared__ double sm[kThreads / 32];
+    const int groups = (a.F + fpc - 1) / fpc;
+    const long long total = (long long)groups * q.mb * tiles;
+    for (long long blk = blockIdx.x; blk < total; blk += gridDim.x) {
+        // row-major over (row, tile), frame groups innermost: CTAs that run
+        // together share the row's table and read neighbouring frames
+        const int g = (int)(blk % groups);
+        const long long rt = blk / groups;
+        const int i = (int)(rt / tiles), tile = (int)(rt - (long long)i * tiles);
+        const int b0 = __ldg(q.row_ptr + i), d = __ldg(q.row_ptr + i + 1) - b0;
+        switch (d) {
+            case 0: break;
+            case 1: qc_cn_rows<1, BWD>(a, q, g, fpc, i, tile, b0, wpart, tiles, sm); break;
+            case 2: qc_cn_rows<2, BWD>(a, q, g, fpc, i, tile, b0, wpart, tiles, sm); break;
+            case 3: qc_cn_rows<3, BWD>(a, q, g, fpc, i, tile, b0, wpart, tiles, sm); break;
+            case 4: qc_cn_rows<4, BWD>(a, q, g, fpc, i, tile, b0, wpart, tiles, sm); break;
+            default: qc_cn_rows_n<BWD>(a, q, g, fpc, i, tile, b0, d, wpart, tiles, sm); break;
+        }
+    }
+}
+
+// Variable side.  MODE kVnFwd: APP = Lch + sum of c2v (ascending row order);
+// kVnBwd: S = sum du, dloss/dLch += S, G = S - du; kVnSeed: G = dloss/dAPP on
+// every edge, dloss/dLch = dloss/dAPP.
+enum : int { kVnFwd = 0, kVnBwd = 1, kVnSeed = 2 };
+
+template <int MODE, int DV, typename T>
+__device__ __forceinline__ void qc_vn_one(const Args<T>& a, const QcDev& q, size_t fe, size_t vi, int p,
+                                          const int (&blk)[DV > 0 ? DV : 1], int cb0, int dv, const T* grad_app) {
+    constexpr bool kFixed = DV > 0;
+    const int nd = kFixed ? DV : dv;
+    auto slot = [&](int b) -> size_t {
+        if constexpr (kFixed) return fe + (size_t)blk[b] * q.Z + p;
+        else return fe + (size_t)__ldg(q.col_blk + cb0 + b) * q.Z + p;
+    };
+    if constexpr (MODE == kVnFwd) {
+        T s = (T)__ldg(a.llr + vi);
+        for (int b = 0; b < nd; ++b) s += a.c2v_out[slot(b)];
+        a.app_out[vi] = s;
+    } else if constexpr (MODE == kVnBwd) {
+        T s = T(0);
+        for (int b = 0; b < nd; ++b) s += a.G[slot(b)];
+        if (a.grad_llr) a.grad_llr[vi] += s;
+        for (int b = 0; b < nd; ++b) {
+            T* gp = a.G + slot(b);
+            *gp = s - *gp;
+        }
+    } else {
+        const T gv = grad_app[vi];
+        if (a.grad_llr) a.grad_llr[vi] = gv;
+        for (int b = 0; b < nd; ++b) a.G[slot(b)] = gv;
+    }
+}
+
+template <int MODE, int DV>
+__device__ __forceinline__ void qc_vn_vec(const Args<float>& a, const QcDev& q, size_t fe, size_t vi, int p,
+                                          const int (&blk)[DV], const float* grad_app) {
+    size_t mb[DV];
+#pragma unroll
+    for (int b = 0; b < DV; ++b) mb[b] = fe + (size_t)blk[b] * q.Z + p;
+    if constexpr (MODE == kVnFwd) {
+        float4 s = __ldg(reinterpret_cast<const float4*>(a.llr + vi));
+        float4 m[DV];
+#pragma unroll
+        for (int b = 0; b < DV; ++b) m[b] = *reinterpret_cast<const float4*>(a.c2v_out + mb[b]);
+#pragma unroll
+        for (int b = 0; b < DV; ++b) {
+            s.x += m[b].x;
+            s.y += m[b].y;
+            s.z += m[b].z;
+            s.w += m[b].w;
+        }
+        *reinterpret_cast<float4*>(a.app_out + vi) = s;
+    } else if constexpr (MODE == kVnBwd) {
+        float4 m[DV];
+#pragma unroll
+        for (int b = 0; b < DV; ++b) m[b] = *reinterpret_cast<const float4*>(a.G + mb[b]);
+        float4 s = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+        for (int b = 0; b < DV; ++b) {
+            s.x += m[b].x;
+            s.y += m[b].y;
+            s.z += m[b].z;
+            s.w += m[b].w;
+        }
+        if (a.grad_llr) {
+            float4* gl = reinterpret_cast<float4*>(a.grad_llr + vi);
+            float4 v = *gl;
+            v.x += s.x;
+            v.y += s.y;
+            v.z += s.z;
+            v.w += s.w;
+            *gl = v;
+        }
+#pragma unroll
+        for (int b = 0; b < DV; ++b)
+            *reinterpret_cast<float4*>(a.G + mb[b]) =
+                make_float4(s.x - m[b].x, s.y - m[b].y, s.z - m[b].z, s.w - m[b].w);
+    } else {
+        const float4 gv = *reinterpret_cast<const float4*>(grad_app + vi);
+        if (a.grad_llr) *reinterpret_cast<float4*>(a.grad_llr + vi) = gv;
+#pragma unroll
+        for (int b = 0; b < DV; ++b) *reinterpret_cast<float4*>(a.G + mb[b]) = gv;
+    }
+}
+
+template <int MODE, int DV, typename T>
+__device__ __forceinline__ void qc_vn_cols(const Args<T>& a, const QcDev& q, int g, int fpc, int j, int cb0, int dv,
+                                           const T* grad_app) {
+    const int Z = q.Z;
+    int blk[DV > 0 ? DV : 1];
+    if constexpr (DV > 0) {
+#pragma unroll
+        for (int b = 0; b < DV; ++b) blk[b] = __ldg(q.col_blk + cb0 + b);
+    }
+    const int f0 = g * fpc, nf = min(a.F, f0 + fpc) - f0;
+    const int count = nf * Z;  // (frame, variable) pairs of the group in column j
+    for (int idx = 4 * (int)threadIdx.x; idx < count; idx += 4 * kThreads) {
+        const int fl = idx / Z, p = idx - fl * Z;
+        const size_t fe = (size_t)(f0 + fl) * (size_t)a.E, fn = (size_t)(f0 + fl) * (size_t)a.n;
+        const size_t vi = fn + (size_t)j * Z + p;
+        if constexpr (sizeof(T) == 4 && DV > 0) {
+            if (a.vec) {  // Z % 4 == 0: the four variables are p .. p + 3 of one frame
+                qc_vn_vec<MODE, DV>(a, q, fe, vi, p, blk, grad_app);
+                continue;
+            }
+        }
+        for (int e = 0; e < 4 && idx + e < count; ++e) {
+            const int fe2 = (idx + e) / Z, pe = (idx + e) - fe2 * Z;
+            qc_vn_one<MODE, DV, T>(a, q, (size_t)(f0 + fe2) * (size_t)a.E,
+                                   (size_t)(f0 + fe2) * (size_t)a.n + (size_t)j * Z + pe, pe, blk, cb0, dv, grad_app);
+        }
+    }
+}
+
+template <int MODE, typename T>
+__global__ void __launch_bounds__(kThreads) qc_vn_kernel(Args<T> a, QcDev q, int fpc, const T* grad_app) {
+    const int groups = (a.F + fpc - 1) / fpc;
+    const long long total = (long long)groups * q.nb;
+    for (long long blk = blockIdx.x; blk < total; blk += gridDim.x) {
+        const int g = (int)(blk % groups), j = (int)(blk / groups);
+        const int cb0 = __ldg(q.col_ptr + j), dv = __ldg(q.col_ptr + j + 1) - cb0;
+        switch (dv) {
+            case 1: qc_vn_cols<MODE, 1, T>(a, q, g, fpc, j, cb0, 1, grad_app); break;
+            case 2: qc_vn_cols<MODE, 2, T>(a, q, g, fpc, j, cb0, 2, grad_app); break;
+            case 3: qc_vn_cols<MODE, 3, T>(a, q, g, fpc, j, cb0, 3, grad_app); break;
+            case 4: qc_vn_cols<MODE, 4, T>(a, q, g, fpc, j, cb0, 4, grad_app); break;
+            default: qc_vn_cols<MODE, 0, T>(a, q, g, fpc, j, cb0, dv, grad_app); break;
+        }
+    }
+}
+
+// dloss/dw_k[cl] = sum over the class's blocks b, the frame groups g and the
+// tiles of wpart (one CTA per class, grid-stride over classes, fixed order).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) class_reduce_kernel(const double* wpart, int groups, int nblk, int tiles,
+                                                                const int* cblk_ptr, const int* cblk, int C, T* gw) {
+    __shared__ double sm[kThreads / 32];
+    for (int c = blockIdx.x; c < C; c += gridDim.x) {
+        const int lo = __ldg(cblk_ptr + c), nbk = __ldg(cblk_ptr + c + 1) - lo;
+        const long long per_g = (long long)nbk * tiles;
+        const long long total = (long long)groups * per_g;
+        double acc = 0.0;
+        for (long long i = threadIdx.x; i < total; i += kThreads) {
+            const int g = (int)(i / per_g);
+            const int r = (int)(i - (long long)g * per_g);
+            const int bi = r / tiles, tile = r - bi * tiles;
+            acc += wpart[((size_t)g * nblk + __ldg(cblk + lo + bi)) * tiles + tile];
+        }
+        const double s = block_sum(acc, sm);
+        if (threadIdx.x == 0) gw[c] = (T)s;
+    }
 }
 
 }  // namespace wbp
