@@ -84,10 +84,14 @@ def algorithmic_bytes_per_frame_iter(code) -> int:
     return 8 * int(code.edges) + 12 * int(code.n)
 
 
+DECODER_SOURCES = ("bp_kernels.cuh", "cn_math.cuh", "device_types.h", "host_common.h", "ldpc_api.cu")
+
+
 def kernel_source_hash() -> str:
+    """Hash of the sources the persistent decoder kernel is built from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2507_03509_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in DECODER_SOURCES:
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

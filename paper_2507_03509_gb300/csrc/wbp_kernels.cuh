@@ -128,13 +128,20 @@ __device__ __forceinline__ long long var_slot(const CsrDev& g, const VarWalk& vw
 // d(a_j [+] B)/da_j for B = boxplus of inputs i not in {e, j}; FP32 r-domain.
 template <int D>
 __device__ __forceinline__ float dbox(const float (&r)[D], const bool (&ng)[D], int e, int j) {
+    if constexpr (D == 2) return 1.0f;  // B is empty: a degree-2 check copies its other input
     float rb = 0.0f;
     bool neg = false;
+    if constexpr (D == 3) {  // B is the one remaining input
+        const int i = 3 - e - j;
+        rb = r[i];
+        neg = ng[i];
+    } else {
 #pragma unroll
-    for (int i = 0; i < D; ++i) {
-        if (i == e || i == j) continue;
-        rb = rcomb(rb, r[i]);
-        neg ^= ng[i];
+        for (int i = 0; i < D; ++i) {
+            if (i == e || i == j) continue;
+            rb = rcomb(rb, r[i]);
+            neg ^= ng[i];
+        }
     }
     const float rj = r[j];
     const float val = __fdividef(rj * fmaf(-rb, rb, 1.0f), (rj + rb) * fmaf(rj, rb, 1.0f));
