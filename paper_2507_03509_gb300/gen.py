@@ -301,6 +301,11 @@ WORKLOADS = {
     4: dict(name="wbp_qc_n65536_r0.1_T20", kind="wbp", mb=115, nb=128, Z=512, n_w2=64, frames=128, beta=0.9,
             rate=0.1, iters=20, checkpoint=5,
             fd=dict(n=256, m=230, var_degree=3, check_degrees={3: 152, 4: 78}, seed=1404)),
+    # a type-based-protograph-like multi-edge-type code at the paper's rate and
+    # length (R = 1/50, n = 10^6): 8 core columns (core column 0 punctured),
+    # 192 degree-1 columns; used for the VNR-ET beta sweep on degree-1 variables
+    7: dict(name="qc_tbp_like_n1e6_r0.02", kind="tbp", Z=5000, frames=32, beta=0.9, rate=0.02, max_iter=500,
+            punctured_cols=(0,)),
     # a (3,6)-regular QC code of the same length class whose BP waterfall lies at
     # beta ~ 0.86-0.89, where early termination changes FER and mean iterations
     # (the regime of the paper's Figs. 1-2); used for the beta sweep
@@ -318,6 +323,8 @@ def workload_code(number: int, Z: int | None = None):
         return random_csr_code(w["n"], w["m"], w["var_degree"], w["check_degrees"], seed)
     if w["kind"] == "batch":
         raise ValueError("a batch workload has several codes: use batch_codes()")
+    if w["kind"] == "tbp":
+        return tbp_like_qc_code(Z or w["Z"], seed=seed)
     if "col_weight" in w:
         weights = np.full(w["nb"], w["col_weight"], dtype=np.int64)
     else:
@@ -355,6 +362,59 @@ def wbp_fd_code(number: int = 4) -> CSRCode:
     """The small random code of a weighted-BP workload's finite-difference check."""
     d = WORKLOADS[number]["fd"]
     return random_csr_code(d["n"], d["m"], d["var_degree"], d["check_degrees"], d["seed"])
+
+
+def tbp_like_base(k_core: int, core_rows: int, lower_rows: int, core_deg: int, lower_core_deg: int,
+                  seed: int) -> np.ndarray:
+    """Base matrix of a multi-edge-type protograph in the style of the paper's
+    type-based protograph (TBP) codes for low rates (section "Simulations",
+    R = 1/50): k_core core columns and lower_rows degree-1 columns.
+
+    Rows 0 .. core_rows-1 tie the core columns together (each core column
+    meets core_deg of them).  Row core_rows + r holds degree-1 column
+    k_core + r and lower_core_deg core columns.  Core columns are spread over
+    the lower rows as evenly as the totals allow (seeded).  Rate
+    1 - (core_rows + lower_rows) / (k_core + lower_rows)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    mb, nb = core_rows + lower_rows, k_core + lower_rows
+    B = np.zeros((mb, nb), dtype=np.int8)
+    core = qc_base_matrix(core_rows, k_core, np.full(k_core, core_deg), seed + 1)
+    B[:core_rows, :k_core] = core
+    use = np.zeros(k_core, dtype=np.int64)  # lower-row connections per core column so far
+    for r in range(lower_rows):
+        tie = rng.random(k_core)
+        cols = np.lexsort((tie, use))[:lower_core_deg]  # least used first, ties at random
+        B[core_rows + r, cols] = 1
+        use[cols] += 1
+        B[core_rows + r, k_core + r] = 1
+    return B
+
+
+def tbp_like_qc_code(Z: int, k_core: int = 8, core_rows: int = 4, lower_rows: int = 192, core_deg: int = 3,
+                     lower_core_deg: int = 2, seed: int = 1007) -> QCCode:
+    """QC lift of tbp_like_base with circulant shifts uniform in [0, Z).  The
+    defaults give R = 4/200 = 1/50 (n = 200 Z): core columns of degree 3 + 48,
+    core rows of degree 6, lower rows of degree 3 (two core bits and one
+    degree-1 bit), the shape of published low-rate multi-edge-type codes."""
+    B = tbp_like_base(k_core, core_rows, lower_rows, core_deg, lower_core_deg, seed)
+    rng = np.random.Generator(np.random.PCG64(seed + 7919))
+    shifts = np.where(B > 0, rng.integers(0, Z, size=B.shape), -1).astype(np.int32)
+    return QCCode(B.shape[0], B.shape[1], Z, shifts)
+
+
+SHORTENED_LLR = 100.0  # channel value of a shortened (known) bit: strong, finite
+
+
+def rate_adapt(frames: Frames, punctured, shortened) -> Frames:
+    """Rate adaptation of received frames.  Punctured bits were never sent:
+    Lch = 0.  Shortened bits are known to both sides: Lch = +-SHORTENED_LLR
+    with the sign of the known bit.  x and the syndrome are unchanged."""
+    llr = frames.llr.copy()
+    p = np.asarray(punctured, dtype=np.int64)
+    sh = np.asarray(shortened, dtype=np.int64)
+    llr[:, p] = 0.0
+    llr[:, sh] = (SHORTENED_LLR * (1.0 - 2.0 * frames.x[:, sh].astype(np.float64))).astype(np.float32)
+    return Frames(frames.x, llr, frames.syndrome, frames.sigma)
 
 
 def batch_codes(number: int):
@@ -417,4 +477,9 @@ def workload_frames(number: int, code, frames: int | None = None, first: int = 0
     rate = w["rate"]
     sigma = sigma_for_capacity(rate / b)
     seeds = [2000 * number + f for f in range(first, first + F)]
-    return make_frames(code, np.full(F, sigma), seeds)
+    fr = make_frames(code, np.full(F, sigma), seeds)
+    if w.get("punctured_cols"):
+        Z = code.Z
+        punct = np.concatenate([np.arange(j * Z, (j + 1) * Z) for j in w["punctured_cols"]])
+        fr = rate_adapt(fr, punct, [])
+    return fr

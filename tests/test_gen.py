@@ -112,3 +112,31 @@ def test_batch_workload_layout_and_reproducibility():
         assert (gen.syndrome(c, x) == a.syndrome[a.syn_off[f]:a.syn_off[f + 1]]).all()
         assert 0.85 <= a.beta[f] <= 0.97
         assert gen.biawgn_capacity(a.sigma[f]) == pytest.approx(c.rate / a.beta[f], rel=1e-9)
+
+
+def test_tbp_like_code_structure():
+    c = gen.tbp_like_qc_code(16)
+    B = (c.shifts >= 0).astype(int)
+    assert (c.mb, c.nb) == (196, 200) and abs(c.rate - 0.02) < 1e-12
+    cols, rows = B.sum(0), B.sum(1)
+    assert (cols[:8] == 51).all() and (cols[8:] == 1).all()          # core columns, degree-1 columns
+    assert (rows[:4] == 6).all() and (rows[4:] == 3).all()           # core rows, lower rows
+    assert (B[4:, 8:] == np.eye(192, dtype=int)).all()              # one degree-1 column per lower row
+    assert B[:4, 8:].sum() == 0
+    csr = c.to_csr()
+    deg = np.bincount(csr.colidx, minlength=c.n)
+    assert (deg[8 * 16:] == 1).all() and (deg[:8 * 16] == 51).all()
+
+
+def test_rate_adapt_puncture_and_shorten():
+    c = gen.workload_code(1)
+    fr = gen.workload_frames(1, c, frames=3)
+    p, sh = np.arange(0, 40), np.arange(100, 130)
+    ad = gen.rate_adapt(fr, p, sh)
+    assert (ad.llr[:, p] == 0).all()
+    assert (ad.llr[:, sh] == gen.SHORTENED_LLR * (1 - 2 * fr.x[:, sh].astype(np.float32))).all()
+    rest = np.setdiff1d(np.arange(c.n), np.concatenate([p, sh]))
+    assert (ad.llr[:, rest] == fr.llr[:, rest]).all()
+    assert ad.syndrome is fr.syndrome and ad.x is fr.x
+    w = gen.workload_frames(7, gen.workload_code(7, Z=16), frames=2)
+    assert (w.llr[:, :16] == 0).all() and (w.llr[:, 16:] != 0).all()   # core column 0 punctured

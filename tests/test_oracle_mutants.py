@@ -47,6 +47,7 @@ MUTANTS = {
 
 PINS = [
     lambda o: [pins.test_trees_match_bruteforce_map(o, seed) for seed in range(3)],
+    lambda o: [pins.test_trees_with_punctured_and_shortened_bits_match_bruteforce_map(o, seed) for seed in range(2)],
     pins.test_degree2_check_closed_form,
     pins.test_degree1_check_and_isolated_variable,
     pins.test_three_cycle_unsatisfiable_syndrome,

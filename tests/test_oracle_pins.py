@@ -81,6 +81,34 @@ def test_trees_match_bruteforce_map(oracle_mod, seed):
     assert out["iters"][0] == iters
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_trees_with_punctured_and_shortened_bits_match_bruteforce_map(oracle_mod, seed):
+    """Rate adaptation on trees: punctured bits (Lch = 0) and shortened bits
+    (Lch = +-100, known) leave BP exact; only the clamp of a shortened bit's
+    own outgoing messages at 25 departs from MAP, by ~e^-25.  Trees where a
+    free bit's MAP value reaches 15 (a shortened bit copied through a
+    degree-2 check, where the clamp itself binds) are redrawn."""
+    rng = np.random.default_rng(300 + seed)
+    for _ in range(100):
+        code = random_tree(rng, int(rng.integers(7, 13)))
+        llr = (rng.standard_normal(code.n) * 0.9).astype(np.float32)
+        perm = rng.permutation(code.n)
+        punct, short = perm[: max(1, code.n // 4)], perm[code.n // 4: code.n // 4 + max(1, code.n // 6)]
+        llr[punct] = 0.0
+        llr[short] = (100.0 * rng.choice([-1.0, 1.0], size=short.size)).astype(np.float32)
+        s = rng.integers(0, 2, code.m).astype(np.uint8)
+        exact = brute_force_app(code, llr, s)
+        free = np.setdiff1d(np.arange(code.n), short)
+        if np.abs(exact[free]).max() < 15.0:
+            break
+    else:
+        pytest.fail("no tree without a binding clamp drawn")
+    iters = 2 * (code.n + code.m)
+    out = oracle_mod.decode(code, llr[None], s[None], iters, NONE, final_app=True)
+    np.testing.assert_allclose(out["app_final"][0], exact, rtol=1e-8, atol=1e-8)
+    assert (out["bits"][0][short] == (llr[short] < 0)).all()
+
+
 def test_degree2_check_closed_form(oracle_mod):
     """A degree-2 check passes the other variable's message on, sign set by
     its syndrome bit: c2v = (1 - 2 s) * v2c_other."""
