@@ -78,6 +78,9 @@ def _load():
             lib.oracle_decode.argtypes = [i64, i64, P, P, i64, P, P, i32, i32, i32, dbl,
                                           P, P, P, P, i32, P, P, P, i32]
             lib.oracle_decode.restype = ctypes.c_int
+            lib.oracle_decode_weighted.argtypes = [i64, i64, P, P, i64, P, P, i32, i32, i32, dbl,
+                                                   P, P, P, P, i32, P, P, P, i32, P, i32, i32, P]
+            lib.oracle_decode_weighted.restype = ctypes.c_int
             lib.oracle_max_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
@@ -93,11 +96,14 @@ def _ptr(a):
 
 def decode(code, llr, syndrome, max_iter: int, rule: int = RULE_PCE_VNR,
            vnr_first_iter: int = 2, lmax: float = 25.0, trace_iters: int = 0,
-           threads: int = 0, trace=("c2v", "app", "q"), final_app: bool = False):
+           threads: int = 0, trace=("c2v", "app", "q"), final_app: bool = False, weights=None,
+           edge_class=None):
     """Decode frames with the FP64 oracle.
 
     code: any object with m, n, rowptr, colidx (check-major CSR, columns sorted).
     llr: float32 [F, n]; syndrome: uint8 [F, m] (0/1).
+    weights [w_iters, C] with edge_class [E] (CSR order): learned weights on
+    the check-to-variable messages, row min(k, w_iters) in iteration k.
     Returns dict(bits uint8 [F,n], flags uint8 [F], iters int32 [F]); with
     final_app, app_final float64 [F,n] (APP of the last iteration run); and,
     if trace_iters > 0, the traces named in `trace`: c2v float64 [T,F,E] (CSR
@@ -125,10 +131,17 @@ def decode(code, llr, syndrome, max_iter: int, rule: int = RULE_PCE_VNR,
     ta = np.full((T, F, n), np.nan) if T > 0 and "app" in trace else None
     tq = np.full((T, F), np.nan) if T > 0 and "q" in trace else None
     af = np.zeros((F, n)) if final_app else None
-    rc = lib.oracle_decode(m, n, _ptr(rowptr), _ptr(colidx), F, _ptr(llr), _ptr(syndrome),
-                           int(max_iter), int(rule), int(vnr_first_iter), float(lmax),
-                           _ptr(bits), _ptr(flags), _ptr(iters), _ptr(af), T, _ptr(tc), _ptr(ta),
-                           _ptr(tq), int(threads))
+    args = (m, n, _ptr(rowptr), _ptr(colidx), F, _ptr(llr), _ptr(syndrome), int(max_iter), int(rule),
+            int(vnr_first_iter), float(lmax), _ptr(bits), _ptr(flags), _ptr(iters), _ptr(af), T, _ptr(tc),
+            _ptr(ta), _ptr(tq), int(threads))
+    if weights is None:
+        rc = lib.oracle_decode(*args)
+    else:
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        cls = np.ascontiguousarray(edge_class, dtype=np.int32)
+        if w.ndim != 2 or cls.shape != (E,):
+            raise ValueError("weights [w_iters, classes] and edge_class [E] expected")
+        rc = lib.oracle_decode_weighted(*args, _ptr(w), int(w.shape[0]), int(w.shape[1]), _ptr(cls))
     if rc != 0:
         raise RuntimeError("oracle_decode failed (bad arguments or out of memory)")
     out = dict(bits=bits, flags=flags, iters=iters)

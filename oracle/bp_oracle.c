@@ -21,6 +21,10 @@
  *   no test is made before the first iteration; v2c and c2v messages are
  *   clamped to [-lmax, lmax]; the APP value is not clamped.
  *
+ * oracle_decode_weighted adds learned weights (one per iteration and edge
+ * class) on the check-to-variable messages, the reading the weighted-BP
+ * oracle (wbp_oracle.c) also takes; the early-termination rules are unchanged.
+ *
  * Everything is plain loops in the order the algorithm states them; the
  * exclusive sums and products are taken by explicit loops, never by removing
  * one's own term from a total.
@@ -86,7 +90,8 @@ static int decode_frame(int64_t m, int64_t n, const int64_t *rowptr, const int32
                         int max_iter, int rule, int vnr_first_iter, double lmax,
                         uint8_t *bits_out, uint8_t *flag_out, int32_t *iters_out,
                         double *app_out, int trace_iters, int64_t frame, int64_t frames,
-                        double *trace_c2v, double *trace_app, double *trace_q)
+                        double *trace_c2v, double *trace_app, double *trace_q,
+                        const double *w, int w_iters, int n_classes, const int32_t *edge_class)
 {
     int64_t E = rowptr[m];
     double *c2v = (double *)calloc((size_t)(E > 0 ? E : 1), sizeof(double));
@@ -128,6 +133,8 @@ static int decode_frame(int64_t m, int64_t n, const int64_t *rowptr, const int32
                 for (int64_t f = rowptr[c]; f < rowptr[c + 1]; f++)
                     if (f != e) prod *= tanh(0.5 * v2c[f]);
                 c2v[e] = clampd(sgn * 2.0 * atanh(prod), lmax);
+                if (w) /* weighted decoding: iteration k scales by row min(k, w_iters) */
+                    c2v[e] *= w[(int64_t)((k < w_iters ? k : w_iters) - 1) * n_classes + edge_class[e]];
             }
         }
         /* 3. a-posteriori LLR and hard decision. */
@@ -175,12 +182,12 @@ static int decode_frame(int64_t m, int64_t n, const int64_t *rowptr, const int32
  * threads <= 0 uses the OpenMP default.  Returns 0, or -1 on bad input or
  * allocation failure.
  */
-int oracle_decode(int64_t m, int64_t n, const int64_t *rowptr, const int32_t *colidx,
-                  int64_t frames, const float *llr, const uint8_t *syndrome,
-                  int max_iter, int rule, int vnr_first_iter, double lmax,
-                  uint8_t *bits_out, uint8_t *flags_out, int32_t *iters_out, double *app_out,
-                  int trace_iters, double *trace_c2v, double *trace_app, double *trace_q,
-                  int threads)
+static int decode_all(int64_t m, int64_t n, const int64_t *rowptr, const int32_t *colidx,
+                      int64_t frames, const float *llr, const uint8_t *syndrome,
+                      int max_iter, int rule, int vnr_first_iter, double lmax,
+                      uint8_t *bits_out, uint8_t *flags_out, int32_t *iters_out, double *app_out,
+                      int trace_iters, double *trace_c2v, double *trace_app, double *trace_q,
+                      int threads, const double *w, int w_iters, int n_classes, const int32_t *edge_class)
 {
     if (m < 0 || n < 0 || frames < 0 || rule < 0 || rule > 2 || max_iter < 1) return -1;
     var_adj va;
@@ -195,12 +202,46 @@ int oracle_decode(int64_t m, int64_t n, const int64_t *rowptr, const int32_t *co
                          max_iter, rule, vnr_first_iter, lmax, bits_out + f * n,
                          flags_out + f, iters_out + f, app_out ? app_out + f * n : NULL,
                          trace_iters, f, frames,
-                         trace_c2v, trace_app, trace_q) != 0)
+                         trace_c2v, trace_app, trace_q, w, w_iters, n_classes, edge_class) != 0)
             err |= 1;
     }
     free(va.ptr);
     free(va.edge);
     return err ? -1 : 0;
+}
+
+int oracle_decode(int64_t m, int64_t n, const int64_t *rowptr, const int32_t *colidx,
+                  int64_t frames, const float *llr, const uint8_t *syndrome,
+                  int max_iter, int rule, int vnr_first_iter, double lmax,
+                  uint8_t *bits_out, uint8_t *flags_out, int32_t *iters_out, double *app_out,
+                  int trace_iters, double *trace_c2v, double *trace_app, double *trace_q,
+                  int threads)
+{
+    return decode_all(m, n, rowptr, colidx, frames, llr, syndrome, max_iter, rule, vnr_first_iter, lmax,
+                      bits_out, flags_out, iters_out, app_out, trace_iters, trace_c2v, trace_app, trace_q,
+                      threads, NULL, 0, 0, NULL);
+}
+
+/*
+ * The same decoder with the check-to-variable messages of iteration k scaled
+ * by w[min(k, w_iters) - 1][edge_class[e]] (learned weights; iterations past
+ * the last trained one keep its weights).  w: [w_iters][n_classes] doubles,
+ * edge_class: [E] in CSR edge order with values in [0, n_classes).
+ */
+int oracle_decode_weighted(int64_t m, int64_t n, const int64_t *rowptr, const int32_t *colidx,
+                           int64_t frames, const float *llr, const uint8_t *syndrome,
+                           int max_iter, int rule, int vnr_first_iter, double lmax,
+                           uint8_t *bits_out, uint8_t *flags_out, int32_t *iters_out, double *app_out,
+                           int trace_iters, double *trace_c2v, double *trace_app, double *trace_q,
+                           int threads, const double *w, int w_iters, int n_classes,
+                           const int32_t *edge_class)
+{
+    if (!w || w_iters < 1 || n_classes < 1 || !edge_class || m < 0) return -1;
+    for (int64_t e = 0; e < rowptr[m]; e++)
+        if (edge_class[e] < 0 || edge_class[e] >= n_classes) return -1;
+    return decode_all(m, n, rowptr, colidx, frames, llr, syndrome, max_iter, rule, vnr_first_iter, lmax,
+                      bits_out, flags_out, iters_out, app_out, trace_iters, trace_c2v, trace_app, trace_q,
+                      threads, w, w_iters, n_classes, edge_class);
 }
 
 /* Number of OpenMP threads a parallel region would use (1 without OpenMP). */

@@ -14,6 +14,7 @@ import pytest
 
 import oracle
 import test_oracle_pins as pins
+import test_weighted_decode_pins as wpins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "bp_oracle.c")
 
@@ -43,6 +44,8 @@ MUTANTS = {
     "VNR tested before PCE": [(PCE_BLOCK + VNR_BLOCK, VNR_BLOCK + PCE_BLOCK)],
     "parity check ignores the syndrome": [("int par = s[c];", "int par = 0;")],
     "q history not updated": [("        q_prev = q;\n", "")],
+    "learned weight ignores the edge class": [("* n_classes + edge_class[e]];", "* n_classes + 0];")],
+    "past the last weight row, the first row is used": [("(k < w_iters ? k : w_iters) - 1", "(k < w_iters ? k : 1) - 1")],
 }
 
 PINS = [
@@ -56,6 +59,10 @@ PINS = [
     pins.test_sign_symmetry_exact,
     pins.test_success_means_zero_syndrome,
     pins.test_noise_free_limit,
+    lambda o: [wpins.test_unit_weights_are_the_plain_decoder(o, r) for r in (0, 2)],
+    wpins.test_rule_none_equals_weighted_bp_forward,
+    lambda o: [wpins.test_rows_past_the_last_repeat_it(o, r) for r in (0, 2)],
+    wpins.test_zero_weights_closed_form,
 ]
 
 
@@ -66,6 +73,7 @@ class _MutantOracle:
         self._lib = lib
         for name in ("RULE_NONE", "RULE_PCE", "RULE_PCE_VNR", "FLAG_SUCCESS", "FLAG_ABORTED"):
             setattr(self, name, getattr(oracle, name))
+        self.wbp = oracle.wbp  # the weighted-BP oracle is a separate library, not mutated here
 
     def decode(self, *args, **kwargs):
         saved = oracle._lib
@@ -90,6 +98,9 @@ def build_mutant(tmp_path, edits):
     P, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
     lib.oracle_decode.argtypes = [i64, i64, P, P, i64, P, P, i32, i32, i32, dbl, P, P, P, P, i32, P, P, P, i32]
     lib.oracle_decode.restype = ctypes.c_int
+    lib.oracle_decode_weighted.argtypes = [i64, i64, P, P, i64, P, P, i32, i32, i32, dbl, P, P, P, P, i32, P, P, P,
+                                           i32, P, i32, i32, P]
+    lib.oracle_decode_weighted.restype = ctypes.c_int
     lib.oracle_max_threads.restype = ctypes.c_int
     return lib
 
