@@ -367,6 +367,12 @@ def run_ours(args):
            "d2h_bytes_per_step": int(F * code.n + F + 4 * F)}
 
     et_regime = None if args.lean or world > 1 else et_paper_regime(ldpc, dev)
+    learned = None
+    if wl.get("code_from") == 2 and not args.lean and world == 1:  # the streaming configuration
+        learned = {"this_workload": learned_weights_comparison(ldpc, dev, args.workload, code, frames, wl["max_iter"]),
+                   "tbp_like_beta_0.84": learned_weights_comparison(
+                       ldpc, dev, 7, gen.workload_code(7), gen.workload_frames(7, gen.workload_code(7), frames=32,
+                                                                               beta=0.84), 500)}
 
     if cpu_pending:
         d_mean_o = oracle_iters_mean(wl["name"], "pce_vnr")
@@ -394,6 +400,7 @@ def run_ours(args):
             "vs_pce": comp["pce"]["ms_per_step"] / (main["ms"] / args.steps),
             "vs_none": comp["none"]["ms_per_step"] / (main["ms"] / args.steps)},
         "et_paper_regime": et_regime,
+        "learned_weights": learned,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src,
                      "traffic": (traffic_fi * per_launch_fi) if traffic_fi else None,
@@ -408,6 +415,67 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def learned_weights_comparison(ldpc, dev, number, code, frames, max_iter, T=20, train_frames=16, steps=30):
+    """Plain flooding (D_max), PCE+VNR early termination, and early termination
+    with learned weights (one per iteration and base block, trained by the
+    weighted-BP adjoint on other frames of the same workload: T unrolled
+    iterations, BCE loss, normalised gradient steps: each moves the largest
+    weight by 0.01) on the same frames: decoded Mbit/s, mean iterations, FER."""
+    import torch
+    nblk = int((code.shifts >= 0).sum())
+    cls = np.arange(nblk, dtype=np.int32)
+    g = ldpc.Graph.from_code(code)
+    wl = gen.WORKLOADS[number]
+    beta = float(gen.biawgn_capacity(frames.sigma[0]))
+    beta = code.rate / beta
+    train = gen.workload_frames(number, code, frames=train_frames, first=100000, beta=beta)
+    plan = ldpc.WeightedBP(g, train_frames, T, cls, nblk, checkpoint_every=5)
+    tl, ts, tx = (torch.from_numpy(a).to(dev) for a in (train.llr, train.syndrome, train.x))
+    w = torch.ones((T, nblk), dtype=torch.float32, device=dev)
+    losses = []
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        app = plan.forward(tl, ts, w)
+        loss, gapp = plan.loss(app, tx)
+        gw, _ = plan.backward(tl, ts, w, gapp)
+        plan.sgd_step(w, gw, 0.01 / max(float(gw.abs().max().item()), 1e-30))
+        losses.append(float(loss.item()))
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    llr = torch.from_numpy(frames.llr).to(dev)
+    syn = torch.from_numpy(frames.syndrome).to(dev)
+    F = frames.llr.shape[0]
+    out = {"code": wl["name"], "beta": round(beta, 4), "frames": F, "max_iter": max_iter,
+           "training": {"frames": train_frames, "iters": T, "steps": steps, "loss_first": losses[0],
+                        "loss_last": losses[-1], "seconds": train_s,
+                        "weights_min": float(w.min().item()), "weights_max": float(w.max().item())}}
+
+    def stats(bits, flags, iters, ms):
+        b, fl, it = bits.cpu().numpy(), flags.cpu().numpy(), iters.cpu().numpy()
+        ok = ((fl & 1) > 0) & (b == frames.x).all(1)
+        return {"mbit_s": code.n * F / (ms * 1e-3) / 1e6, "d_mean": float(it.mean()), "fer": float(1 - ok.mean()),
+                "aborted": int(((fl & 2) > 0).sum()), "ms": ms}
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        e1.synchronize()
+        return r, e0.elapsed_time(e1)
+
+    for name, fn in (("flooding", lambda: ldpc.decode(g, llr, syn, max_iter, "none")),
+                     ("early_termination", lambda: ldpc.decode(g, llr, syn, max_iter, "pce_vnr")),
+                     ("learned_weights_et", lambda: plan.decode(llr, syn, w, max_iter, "pce_vnr"))):
+        r, ms = timed(fn)
+        out[name] = stats(*r, ms)
+    plan.close()
+    g.close()
+    return out
 
 
 def et_paper_regime(ldpc, dev, betas=(0.875, 0.8765), frames=64):

@@ -318,6 +318,18 @@ LDPC_API ldpc_status ldpc_wbp_loss(ldpc_wbp* plan, const void* app, const uint8_
 LDPC_API ldpc_status ldpc_wbp_backward(ldpc_wbp* plan, const float* llr, const uint8_t* syndrome,
                                        const void* weights, const void* grad_app, void* grad_weights,
                                        void* grad_llr, void* cuda_stream);
+/* Early-terminating decode (as ldpc_decode, same arguments and options) with
+ * the plan's learned weights: in iteration k every check-to-variable message
+ * of class cl is scaled by weights[min(k, iters) - 1][cl] (iterations past the
+ * plan's last keep its weights).  weights: device float [iters][n_classes]
+ * (float whatever the plan's type; opts->fp64 selects the decoder's
+ * arithmetic).  The plan's graph and class map are used; `frames` is
+ * independent of the plan's frame count.  Traces are available as in
+ * ldpc_decode.  Returns when the results are ready. */
+LDPC_API ldpc_status ldpc_wbp_decode(const ldpc_wbp* plan, int32_t frames, const float* llr, const uint8_t* syndrome,
+                                     const float* weights, int32_t max_iter, ldpc_term_rule rule, uint8_t* bits_out,
+                                     uint8_t* flags_out, int32_t* iters_out, const ldpc_decode_opts* opts,
+                                     void* cuda_stream);
 /* weights -= lr * grad over [iters][n_classes] (a plain gradient step). */
 LDPC_API ldpc_status ldpc_wbp_sgd_step(ldpc_wbp* plan, void* weights, const void* grad, double lr,
                                        void* cuda_stream);

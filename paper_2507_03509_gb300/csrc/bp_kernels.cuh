@@ -99,6 +99,11 @@ struct Params {
     int groups;                    // independent CTA groups, each with its own slots and barrier
     int slots_per_group;           // slots = groups * slots_per_group
     int* new_frame;                // [slots] frame taken from the queue by a slot that stopped
+    // learned weights (NULL: none): check-to-variable messages of iteration k are
+    // scaled by wts[min(k, w_iters) - 1][wcls[key]], key = base block (QC) or edge (CSR)
+    const float* wts;
+    const int* wcls;
+    int w_iters, w_classes;
 };
 
 // Where one running frame's data lives (slot s decoding frame f of code ci).
@@ -114,7 +119,14 @@ struct FrameCtx {
     int f, n;
     long long E;
     int cn_chunk, vn_chunk, nqb, vec4;
+    const float* wrow;             // weights of the iteration the check pass computes (NULL: none)
 };
+
+// Weight of the message of class key `key`: 1 without learned weights.
+template <typename T>
+__device__ __forceinline__ T msg_weight(const Params<T>& p, const FrameCtx<T>& fc, int key) {
+    return fc.wrow ? T(__ldg(fc.wrow + __ldg(p.wcls + key))) : T(1);
+}
 
 template <typename T, class Code>
 __device__ __forceinline__ FrameCtx<T> frame_ctx(const Params<T>& p, const CodeInfo<Code>& ci, int s, int f) {
@@ -135,7 +147,16 @@ __device__ __forceinline__ FrameCtx<T> frame_ctx(const Params<T>& p, const CodeI
     c.vn_chunk = ci.vn_chunk;
     c.nqb = ci.nqb;
     c.vec4 = ci.vec4;
+    c.wrow = nullptr;
     return c;
+}
+
+// The weight row of the check pass that follows k completed iterations.
+template <typename T>
+__device__ __forceinline__ const float* weight_row(const Params<T>& p, int k) {
+    if (!p.wts) return nullptr;
+    const int r = min(k + 1, p.w_iters) - 1;
+    return p.wts + (size_t)r * p.w_classes;
 }
 
 // ---------------------------------------------------------------------------
@@ -272,8 +293,13 @@ __device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, c
 #pragma unroll
                 for (int j = 0; j < D; ++j) v[j] = clampm(a[c][j] - o[c][j], p.lmax);
                 cn_core<D>(v, sbit, p.lmax, out);
+                if (fc.wrow) {
 #pragma unroll
-                for (int j = 0; j < D; ++j) c2v[mo[j] + pos[c][j]] = out[j];
+                    for (int j = 0; j < D; ++j) c2v[mo[j] + pos[c][j]] = out[j] * msg_weight(p, fc, b0 + j);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < D; ++j) c2v[mo[j] + pos[c][j]] = out[j];
+                }
             }
         }
     }
@@ -315,7 +341,7 @@ __device__ bool qc_cn_item_n(const Params<T>& p, const QcDev& q, const FrameCtx<
             for (int j = 0; j < d; ++j) {
                 int pp = t + __ldg(q.blk_shift + b0 + j);
                 pp = pp >= Z ? pp - Z : pp;
-                c2v[(b0 + j) * Z + pp] = out[j];
+                c2v[(b0 + j) * Z + pp] = out[j] * msg_weight(p, fc, b0 + j);
             }
         }
     }
@@ -395,7 +421,7 @@ __device__ __forceinline__ bool csr_cn_check(const Params<T>& p, const CsrDev& g
     for (int j = 0; j < D; ++j) v[j] = clampm(a[j] - o[j], p.lmax);
     cn_core<D>(v, sbit, p.lmax, out);
 #pragma unroll
-    for (int j = 0; j < D; ++j) c2v[e0 + j] = out[j];
+    for (int j = 0; j < D; ++j) c2v[e0 + j] = out[j] * msg_weight(p, fc, e0 + j);
     return unsat;
 }
 
@@ -424,7 +450,7 @@ __device__ bool csr_cn_check_n(const Params<T>& p, const CsrDev& g, const FrameC
     const bool unsat = want_synd && pr != 0u;
     if (mode == kModeSynd) return unsat;
     cn_core_n(v, d, sbit, p.lmax, out);
-    for (int j = 0; j < d; ++j) c2v[e0 + j] = out[j];
+    for (int j = 0; j < d; ++j) c2v[e0 + j] = out[j] * msg_weight(p, fc, e0 + j);
     return unsat;
 }
 
@@ -755,7 +781,8 @@ __global__ void __launch_bounds__(kThreads, 4) bp_decode_kernel(Params<T> p, Cod
             const int k = st_k[l];
             const int mode = k == 0 ? kModeFirst : (k >= p.max_iter ? kModeSynd : kModeFull);
             const bool want_synd = k >= 1 && (p.rule != kRuleNone || k >= p.max_iter);
-            const FrameCtx<T> fc = frame_ctx(p, ci, s, st_frame[l]);
+            FrameCtx<T> fc = frame_ctx(p, ci, s, st_frame[l]);
+            fc.wrow = weight_row(p, k);
             const bool unsat = cn_tile<T>(p, ci.code, fc, mode, want_synd, tile);
             if (want_synd && __any_sync(0xffffffffu, unsat) && lane == 0)
                 atomicOr(&p.unsat[par * p.slots + s], 1);

@@ -60,6 +60,10 @@ inline ldpc_status cuda_status(cudaError_t e) {
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Graph, device class map (validated at plan creation), iterations and
+// classes of a weighted-BP plan, for decoding with its learned weights.
+bool wbp_plan_classes(const ldpc_wbp* plan, const ldpc_graph** graph, const int** cls, int* iters, int* classes);
+
 // Restores the caller's current device on scope exit.
 struct DeviceGuard {
     int prev = -1;

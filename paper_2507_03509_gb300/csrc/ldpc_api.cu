@@ -125,6 +125,9 @@ struct Job {
     int32_t* iters_out;
     int max_iter, rule;
     bool var_unaligned[kMaxCodes];  // some frame of code c starts at an offset not a multiple of 4
+    const float* wts;            // learned weights [w_iters][w_classes] or NULL
+    const int* wcls;             // class of each base block (QC) / edge (CSR)
+    int w_iters, w_classes;
 };
 
 // QC item sizes: simulate the static assignment (item it goes to CTA it mod
@@ -282,6 +285,10 @@ ldpc_status launch_decode(Workspace& ws, const Job& job, const ldpc_decode_opts&
     p.groups = groups;
     p.slots_per_group = slots_per_group;
     p.new_frame = (int*)(base + L.new_frame);
+    p.wts = job.wts;
+    p.wcls = job.wcls;
+    p.w_iters = job.w_iters;
+    p.w_classes = job.w_classes;
 
     const bool timing = o.stats != nullptr && status_out == nullptr;
     if (timing) LDPC_TRY(cudaEventRecord(ws.ev[0], stream));
@@ -342,7 +349,8 @@ ldpc_status launch_decode(Workspace& ws, const Job& job, const ldpc_decode_opts&
 template <typename T, class Code>
 ldpc_status launch_single(ldpc_graph* g, int frames, const float* llr, const uint8_t* syndrome, int max_iter,
                           int rule, uint8_t* bits_out, uint8_t* flags_out, int32_t* iters_out,
-                          const ldpc_decode_opts& o, cudaStream_t stream) {
+                          const ldpc_decode_opts& o, cudaStream_t stream, const float* wts = nullptr,
+                          const int* wcls = nullptr, int w_iters = 0, int w_classes = 0) {
     const ldpc_graph* gs[1] = {g};
     Job job{};
     job.graphs = gs;
@@ -357,6 +365,10 @@ ldpc_status launch_single(ldpc_graph* g, int frames, const float* llr, const uin
     job.iters_out = iters_out;
     job.max_iter = max_iter;
     job.rule = rule;
+    job.wts = wts;
+    job.wcls = wcls;
+    job.w_iters = w_iters;
+    job.w_classes = w_classes;
     return launch_decode<T, Code>(g->ws, job, o, stream);
 }
 
@@ -374,6 +386,11 @@ ldpc_status check_decode_args(const ldpc_graph* graph, int32_t frames, const voi
     if ((long long)frames * graph->n > (1LL << 40)) return LDPC_ERR_INVALID_ARG;
     return LDPC_OK;
 }
+
+ldpc_status decode_weighted(const ldpc_graph* graph, int32_t frames, const float* llr, const uint8_t* syndrome,
+                            int32_t max_iter, ldpc_term_rule rule, uint8_t* bits_out, uint8_t* flags_out,
+                            int32_t* iters_out, const ldpc_decode_opts* opts, void* cuda_stream, const float* wts,
+                            const int* wcls, int w_iters, int w_classes);
 
 }  // namespace
 
@@ -529,6 +546,29 @@ ldpc_status ldpc_graph_info(const ldpc_graph* g, int32_t* m, int32_t* n, int64_t
 ldpc_status ldpc_decode(const ldpc_graph* graph, int32_t frames, const float* llr, const uint8_t* syndrome,
                         int32_t max_iter, ldpc_term_rule rule, uint8_t* bits_out, uint8_t* flags_out,
                         int32_t* iters_out, const ldpc_decode_opts* opts, void* cuda_stream) {
+    return decode_weighted(graph, frames, llr, syndrome, max_iter, rule, bits_out, flags_out, iters_out, opts,
+                           cuda_stream, nullptr, nullptr, 0, 0);
+}
+
+ldpc_status ldpc_wbp_decode(const ldpc_wbp* plan, int32_t frames, const float* llr, const uint8_t* syndrome,
+                            const float* weights, int32_t max_iter, ldpc_term_rule rule, uint8_t* bits_out,
+                            uint8_t* flags_out, int32_t* iters_out, const ldpc_decode_opts* opts, void* cuda_stream) {
+    const ldpc_graph* graph = nullptr;
+    const int* cls = nullptr;
+    int iters = 0, classes = 0;
+    if (!wbp_plan_classes(plan, &graph, &cls, &iters, &classes) || !weights) return LDPC_ERR_INVALID_ARG;
+    return decode_weighted(graph, frames, llr, syndrome, max_iter, rule, bits_out, flags_out, iters_out, opts,
+                           cuda_stream, weights, cls, iters, classes);
+}
+
+}  // extern "C"
+
+namespace {
+
+ldpc_status decode_weighted(const ldpc_graph* graph, int32_t frames, const float* llr, const uint8_t* syndrome,
+                            int32_t max_iter, ldpc_term_rule rule, uint8_t* bits_out, uint8_t* flags_out,
+                            int32_t* iters_out, const ldpc_decode_opts* opts, void* cuda_stream, const float* wts,
+                            const int* wcls, int w_iters, int w_classes) {
     ldpc_decode_opts o;
     ldpc_decode_opts_init(&o);
     if (opts) o = *opts;
@@ -547,16 +587,20 @@ ldpc_status ldpc_decode(const ldpc_graph* graph, int32_t frames, const float* ll
     if (g->kind == 1) {
         if (o.fp64)
             return launch_single<double, QcDev>(g, frames, llr, syndrome, max_iter, (int)rule, bits_out, flags_out,
-                                                iters_out, o, stream);
+                                                iters_out, o, stream, wts, wcls, w_iters, w_classes);
         return launch_single<float, QcDev>(g, frames, llr, syndrome, max_iter, (int)rule, bits_out, flags_out,
-                                           iters_out, o, stream);
+                                           iters_out, o, stream, wts, wcls, w_iters, w_classes);
     }
     if (o.fp64)
         return launch_single<double, CsrDev>(g, frames, llr, syndrome, max_iter, (int)rule, bits_out, flags_out,
-                                             iters_out, o, stream);
+                                             iters_out, o, stream, wts, wcls, w_iters, w_classes);
     return launch_single<float, CsrDev>(g, frames, llr, syndrome, max_iter, (int)rule, bits_out, flags_out,
-                                        iters_out, o, stream);
+                                        iters_out, o, stream, wts, wcls, w_iters, w_classes);
 }
+
+}  // namespace
+
+extern "C" {
 
 ldpc_status ldpc_decode_host(const ldpc_graph* graph, int32_t frames, const float* llr, const uint8_t* syndrome,
                              int32_t max_iter, ldpc_term_rule rule, uint8_t* bits_out, uint8_t* flags_out,

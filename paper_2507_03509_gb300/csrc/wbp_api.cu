@@ -201,6 +201,17 @@ int grid_for(long long items, int sms) {
 
 }  // namespace
 
+namespace ldpcgb {
+bool wbp_plan_classes(const ldpc_wbp* p, const ldpc_graph** graph, const int** cls, int* iters, int* classes) {
+    if (!p) return false;
+    *graph = p->graph;
+    *cls = p->cls;
+    *iters = p->T;
+    *classes = p->C;
+    return true;
+}
+}  // namespace ldpcgb
+
 extern "C" {
 
 ldpc_status ldpc_wbp_create(const ldpc_graph* graph, int32_t frames, int32_t iters, int32_t n_classes,

@@ -41,7 +41,7 @@ EXPORTED = ("ldpc_decode_opts_init", "ldpc_graph_create_csr", "ldpc_graph_create
             "ldpc_status_str", "ldpc_decode_qc_noalloc", "ldpc_batch_create", "ldpc_batch_destroy",
             "ldpc_batch_info", "ldpc_batch_decode", "ldpc_batch_decode_async", "ldpc_batch_autotune",
             "ldpc_wbp_create", "ldpc_wbp_destroy", "ldpc_wbp_forward", "ldpc_wbp_loss", "ldpc_wbp_backward",
-            "ldpc_wbp_sgd_step")
+            "ldpc_wbp_sgd_step", "ldpc_wbp_decode")
 
 NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 
@@ -115,6 +115,8 @@ def _load():
     lib.ldpc_wbp_backward.restype = ctypes.c_int
     lib.ldpc_wbp_sgd_step.argtypes = [P, P, P, ctypes.c_double, P]
     lib.ldpc_wbp_sgd_step.restype = ctypes.c_int
+    lib.ldpc_wbp_decode.argtypes = [P, i32, P, P, P, i32, ctypes.c_int, P, P, P, ctypes.POINTER(ldpc_decode_opts), P]
+    lib.ldpc_wbp_decode.restype = ctypes.c_int
     return lib
 
 
@@ -447,6 +449,13 @@ def ldpc_wbp_backward(handle, llr_ptr, syndrome_ptr, weights_ptr, grad_app_ptr, 
                                   grad_llr_ptr, stream)
 
 
+def ldpc_wbp_decode(handle, frames, llr_ptr, syndrome_ptr, weights_ptr, max_iter, rule, bits_ptr, flags_ptr,
+                    iters_ptr, opts, stream) -> int:
+    return _lib.ldpc_wbp_decode(handle, int(frames), llr_ptr, syndrome_ptr, weights_ptr, int(max_iter), int(rule),
+                                bits_ptr, flags_ptr, iters_ptr, ctypes.byref(opts) if opts is not None else None,
+                                stream)
+
+
 def ldpc_wbp_sgd_step(handle, weights_ptr, grad_ptr, lr, stream) -> int:
     return _lib.ldpc_wbp_sgd_step(handle, weights_ptr, grad_ptr, float(lr), stream)
 
@@ -507,6 +516,23 @@ class WeightedBP:
                                  grad_app.data_ptr(), gw.data_ptr(), gl.data_ptr() if gl is not None else None,
                                  self._stream(llr, stream)), "ldpc_wbp_backward")
         return gw, gl
+
+    def decode(self, llr, syndrome, weights, max_iter, rule="pce_vnr", out=None, stream=None, **opt):
+        """Early-terminating decode with these learned weights (float32
+        [iters, n_classes]); llr [F, n] float32, syndrome [F, m] uint8 on the
+        device; returns (bits, flags, iters) as ldpc.decode does."""
+        import torch
+        rule = RULES[rule] if isinstance(rule, str) else int(rule)
+        F = llr.shape[0]
+        if out is None:
+            out = (torch.empty((F, self.graph.n), dtype=torch.uint8, device=llr.device),
+                   torch.empty(F, dtype=torch.uint8, device=llr.device),
+                   torch.empty(F, dtype=torch.int32, device=llr.device))
+        w = weights.to(torch.float32).contiguous()
+        _check(ldpc_wbp_decode(self.handle, F, llr.data_ptr(), syndrome.data_ptr(), w.data_ptr(), max_iter, rule,
+                               out[0].data_ptr(), out[1].data_ptr(), out[2].data_ptr(), make_opts(**opt),
+                               self._stream(llr, stream)), "ldpc_wbp_decode")
+        return out
 
     def sgd_step(self, weights, grad, lr, stream=None):
         _check(ldpc_wbp_sgd_step(self.handle, weights.data_ptr(), grad.data_ptr(), lr,

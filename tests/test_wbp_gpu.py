@@ -297,3 +297,87 @@ def test_argument_errors():
     with pytest.raises(ldpc.LdpcError):                      # checkpoints never saved
         plan.backward(llr, syn, w, torch.zeros((1, code.n), device=dev))
     plan.close()
+
+
+# ---------------------------------------------------------------------------
+# Early-terminating decoding with learned weights (ldpc_wbp_decode)
+# ---------------------------------------------------------------------------
+def weighted_decode(ldpc, plan, fr, w, max_iter, rule, **opt):
+    import torch
+    dev = torch.device("cuda:0")
+    llr, syn, _ = tensors(fr, dev)
+    wt = torch.tensor(w, dtype=torch.float32, device=dev)
+    T = opt.pop("trace_iters", 0)
+    F, n = fr.llr.shape
+    tr = {}
+    if T:
+        dt = torch.float64 if opt.get("fp64") else torch.float32
+        tr = dict(trace_iters=T, trace_app=torch.full((T, F, n), float("nan"), dtype=dt, device=dev),
+                  trace_q=torch.full((T, F), float("nan"), dtype=torch.float64, device=dev))
+    bits, flags, iters = plan.decode(llr, syn, wt, max_iter, rule, **opt, **tr)
+    torch.cuda.synchronize()
+    out = dict(bits=bits.cpu().numpy(), flags=flags.cpu().numpy(), iters=iters.cpu().numpy())
+    if T:
+        out.update(app=tr["trace_app"].double().cpu().numpy(), q=tr["trace_q"].cpu().numpy())
+    return out
+
+
+def test_weighted_decode_unit_weights_is_plain_decode():
+    import torch
+    ldpc = lib()
+    code, cls_blk, _, C, fr = qc_setup(Z=128, frames=6, beta=0.9, seed=5)
+    g = ldpc.Graph.from_code(code)
+    plan = ldpc.WeightedBP(g, 1, 4, cls_blk, C)
+    from _decode_helpers import gpu_decode
+    ref = gpu_decode(ldpc, g, fr.llr, fr.syndrome, 60, "pce_vnr")
+    got = weighted_decode(ldpc, plan, fr, np.ones((4, C)), 60, "pce_vnr")
+    for k in ("bits", "flags", "iters"):
+        assert np.array_equal(got[k], ref[k]), k
+    plan.close()
+
+
+@pytest.mark.parametrize("rule", ["pce_vnr", "none"])
+def test_weighted_decode_matches_oracle(oracle_mod, rule):
+    """Weighted messages and APP over the first iterations, and the decisions:
+    a frame whose FP32 decisions differ from the oracle's is re-run in FP64,
+    which must equal them."""
+    ldpc = lib()
+    code, cls_blk, cls_csr, C, fr = qc_setup(Z=128, frames=8, beta=0.75, seed=6)
+    g = ldpc.Graph.from_code(code)
+    plan = ldpc.WeightedBP(g, 1, 3, cls_blk, C)
+    w = np.random.default_rng(7).uniform(0.7, 1.1, size=(3, C)).astype(np.float32)
+    csr = code.to_csr()
+    T = 6
+    got = weighted_decode(ldpc, plan, fr, w, T, "none", trace_iters=T)
+    orc = oracle_mod.decode(csr, fr.llr, fr.syndrome, T, 0, trace_iters=T, trace=("app", "q"), weights=w,
+                            edge_class=cls_csr)
+    np.testing.assert_allclose(got["app"], orc["app"], rtol=1e-4, atol=1e-4)
+    np.testing.assert_allclose(got["q"], orc["q"], rtol=1e-5)
+    rid = {"none": 0, "pce_vnr": 2}[rule]
+    got = weighted_decode(ldpc, plan, fr, w, 80, rule)
+    orc = oracle_mod.decode(csr, fr.llr, fr.syndrome, 80, rid, weights=w, edge_class=cls_csr)
+    bad = np.nonzero((got["iters"] != orc["iters"]) | (got["flags"] != orc["flags"])
+                     | (got["bits"] != orc["bits"]).any(1))[0]
+    if bad.size:
+        sub = gen.Frames(fr.x[bad], fr.llr[bad], fr.syndrome[bad], fr.sigma[bad])
+        g64 = weighted_decode(ldpc, plan, sub, w, 80, rule, fp64=True)
+        for i, f in enumerate(bad):
+            assert (g64["iters"][i], g64["flags"][i]) == (orc["iters"][f], orc["flags"][f]), f
+            assert np.array_equal(g64["bits"][i], orc["bits"][f]), f
+    assert bad.size <= 2
+    plan.close()
+
+
+def test_weighted_decode_reuses_the_last_row():
+    ldpc = lib()
+    code, cls_blk, _, C, fr = qc_setup(Z=128, frames=4, beta=0.75, seed=7)
+    g = ldpc.Graph.from_code(code)
+    short = ldpc.WeightedBP(g, 1, 2, cls_blk, C)
+    long = ldpc.WeightedBP(g, 1, 9, cls_blk, C)
+    w = np.random.default_rng(8).uniform(0.7, 1.1, size=(2, C)).astype(np.float32)
+    a = weighted_decode(ldpc, short, fr, w, 40, "pce_vnr")
+    b = weighted_decode(ldpc, long, fr, np.concatenate([w, np.repeat(w[-1:], 7, axis=0)]), 40, "pce_vnr")
+    for k in ("bits", "flags", "iters"):
+        assert np.array_equal(a[k], b[k]), k
+    short.close()
+    long.close()
