@@ -122,10 +122,12 @@ struct FrameCtx {
     const float* wrow;             // weights of the iteration the check pass computes (NULL: none)
 };
 
-// Weight of the message of class key `key`: 1 without learned weights.
-template <typename T>
-__device__ __forceinline__ T msg_weight(const Params<T>& p, const FrameCtx<T>& fc, int key) {
-    return fc.wrow ? T(__ldg(fc.wrow + __ldg(p.wcls + key))) : T(1);
+// A check message scaled by its learned weight (W: the weighted kernel); the
+// unweighted kernel stores the message as computed.
+template <bool W, typename T>
+__device__ __forceinline__ T weighted(const Params<T>& p, const FrameCtx<T>& fc, T msg, int key) {
+    if constexpr (W) return msg * T(__ldg(fc.wrow + __ldg(p.wcls + key)));
+    else return msg;
 }
 
 template <typename T, class Code>
@@ -232,7 +234,7 @@ constexpr int kQcVnChunk = 4096;         // default variables of one base column
 constexpr int kQBlock = 4 * kThreads;    // variables per q partial sum (per warp: 128)
 constexpr int kQParts = 8;               // a frame's q is reduced in this many fixed ranges, by different CTAs
 
-template <int D, int MODE, bool SYND, typename T>
+template <int D, int MODE, bool SYND, bool W, typename T>
 __device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, const FrameCtx<T>& fc, int i, int t0,
                                            int b0) {
     const int Z = q.Z;
@@ -293,13 +295,8 @@ __device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, c
 #pragma unroll
                 for (int j = 0; j < D; ++j) v[j] = clampm(a[c][j] - o[c][j], p.lmax);
                 cn_core<D>(v, sbit, p.lmax, out);
-                if (fc.wrow) {
 #pragma unroll
-                    for (int j = 0; j < D; ++j) c2v[mo[j] + pos[c][j]] = out[j] * msg_weight(p, fc, b0 + j);
-                } else {
-#pragma unroll
-                    for (int j = 0; j < D; ++j) c2v[mo[j] + pos[c][j]] = out[j];
-                }
+                for (int j = 0; j < D; ++j) c2v[mo[j] + pos[c][j]] = weighted<W>(p, fc, out[j], b0 + j);
             }
         }
     }
@@ -307,7 +304,7 @@ __device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, c
 }
 
 // Rows of weight > 6: runtime degree, local arrays.
-template <int MODE, bool SYND, typename T>
+template <int MODE, bool SYND, bool W, typename T>
 __device__ bool qc_cn_item_n(const Params<T>& p, const QcDev& q, const FrameCtx<T>& fc, int i, int t0, int b0,
                              int d) {
     const int Z = q.Z;
@@ -341,14 +338,14 @@ __device__ bool qc_cn_item_n(const Params<T>& p, const QcDev& q, const FrameCtx<
             for (int j = 0; j < d; ++j) {
                 int pp = t + __ldg(q.blk_shift + b0 + j);
                 pp = pp >= Z ? pp - Z : pp;
-                c2v[(b0 + j) * Z + pp] = out[j] * msg_weight(p, fc, b0 + j);
+                c2v[(b0 + j) * Z + pp] = weighted<W>(p, fc, out[j], b0 + j);
             }
         }
     }
     return unsat;
 }
 
-template <int MODE, bool SYND, typename T>
+template <int MODE, bool SYND, bool W, typename T>
 __device__ __forceinline__ bool qc_cn_dispatch(const Params<T>& p, const QcDev& q, const FrameCtx<T>& fc, int i,
                                                int t0, int b0, int d) {
     switch (d) {
@@ -362,17 +359,17 @@ __device__ __forceinline__ bool qc_cn_dispatch(const Params<T>& p, const QcDev& 
             }
             return unsat;
         }
-        case 1: return qc_cn_item<1, MODE, SYND, T>(p, q, fc, i, t0, b0);
-        case 2: return qc_cn_item<2, MODE, SYND, T>(p, q, fc, i, t0, b0);
-        case 3: return qc_cn_item<3, MODE, SYND, T>(p, q, fc, i, t0, b0);
-        case 4: return qc_cn_item<4, MODE, SYND, T>(p, q, fc, i, t0, b0);
-        case 5: return qc_cn_item<5, MODE, SYND, T>(p, q, fc, i, t0, b0);
-        case 6: return qc_cn_item<6, MODE, SYND, T>(p, q, fc, i, t0, b0);
-        default: return qc_cn_item_n<MODE, SYND, T>(p, q, fc, i, t0, b0, d);
+        case 1: return qc_cn_item<1, MODE, SYND, W, T>(p, q, fc, i, t0, b0);
+        case 2: return qc_cn_item<2, MODE, SYND, W, T>(p, q, fc, i, t0, b0);
+        case 3: return qc_cn_item<3, MODE, SYND, W, T>(p, q, fc, i, t0, b0);
+        case 4: return qc_cn_item<4, MODE, SYND, W, T>(p, q, fc, i, t0, b0);
+        case 5: return qc_cn_item<5, MODE, SYND, W, T>(p, q, fc, i, t0, b0);
+        case 6: return qc_cn_item<6, MODE, SYND, W, T>(p, q, fc, i, t0, b0);
+        default: return qc_cn_item_n<MODE, SYND, W, T>(p, q, fc, i, t0, b0, d);
     }
 }
 
-template <typename T>
+template <bool W, typename T>
 __device__ __forceinline__ bool cn_tile(const Params<T>& p, const QcDev& q, const FrameCtx<T>& fc, int mode,
                                         bool want_synd, int tile) {
     const int per_row = (q.Z + fc.cn_chunk - 1) / fc.cn_chunk;
@@ -380,16 +377,16 @@ __device__ __forceinline__ bool cn_tile(const Params<T>& p, const QcDev& q, cons
     const int t0 = (tile - i * per_row) * fc.cn_chunk;
     const int b0 = __ldg(q.row_ptr + i);
     const int d = __ldg(q.row_ptr + i + 1) - b0;
-    if (mode == kModeFirst) return qc_cn_dispatch<kModeFirst, false, T>(p, q, fc, i, t0, b0, d);
-    if (mode == kModeSynd) return qc_cn_dispatch<kModeSynd, true, T>(p, q, fc, i, t0, b0, d);
-    if (want_synd) return qc_cn_dispatch<kModeFull, true, T>(p, q, fc, i, t0, b0, d);
-    return qc_cn_dispatch<kModeFull, false, T>(p, q, fc, i, t0, b0, d);
+    if (mode == kModeFirst) return qc_cn_dispatch<kModeFirst, false, W, T>(p, q, fc, i, t0, b0, d);
+    if (mode == kModeSynd) return qc_cn_dispatch<kModeSynd, true, false, T>(p, q, fc, i, t0, b0, d);
+    if (want_synd) return qc_cn_dispatch<kModeFull, true, W, T>(p, q, fc, i, t0, b0, d);
+    return qc_cn_dispatch<kModeFull, false, W, T>(p, q, fc, i, t0, b0, d);
 }
 
 // ---------------------------------------------------------------------------
 // CSR check-node tile: checks tile*kCnTile ...; one check per thread-slot.
 // ---------------------------------------------------------------------------
-template <int D, typename T>
+template <int D, bool W, typename T>
 __device__ __forceinline__ bool csr_cn_check(const Params<T>& p, const CsrDev& g, const FrameCtx<T>& fc, int mode,
                                              bool want_synd, int row, int e0) {
     T* c2v = fc.c2v;
@@ -421,11 +418,11 @@ __device__ __forceinline__ bool csr_cn_check(const Params<T>& p, const CsrDev& g
     for (int j = 0; j < D; ++j) v[j] = clampm(a[j] - o[j], p.lmax);
     cn_core<D>(v, sbit, p.lmax, out);
 #pragma unroll
-    for (int j = 0; j < D; ++j) c2v[e0 + j] = out[j] * msg_weight(p, fc, e0 + j);
+    for (int j = 0; j < D; ++j) c2v[e0 + j] = weighted<W>(p, fc, out[j], e0 + j);
     return unsat;
 }
 
-template <typename T>
+template <bool W, typename T>
 __device__ bool csr_cn_check_n(const Params<T>& p, const CsrDev& g, const FrameCtx<T>& fc, int mode, bool want_synd,
                                int row, int e0, int d) {
     T* c2v = fc.c2v;
@@ -450,11 +447,11 @@ __device__ bool csr_cn_check_n(const Params<T>& p, const CsrDev& g, const FrameC
     const bool unsat = want_synd && pr != 0u;
     if (mode == kModeSynd) return unsat;
     cn_core_n(v, d, sbit, p.lmax, out);
-    for (int j = 0; j < d; ++j) c2v[e0 + j] = out[j] * msg_weight(p, fc, e0 + j);
+    for (int j = 0; j < d; ++j) c2v[e0 + j] = weighted<W>(p, fc, out[j], e0 + j);
     return unsat;
 }
 
-template <typename T>
+template <bool W, typename T>
 __device__ __forceinline__ bool cn_tile(const Params<T>& p, const CsrDev& g, const FrameCtx<T>& fc, int mode,
                                         bool want_synd, int tile) {
     bool unsat = false;
@@ -464,13 +461,13 @@ __device__ __forceinline__ bool cn_tile(const Params<T>& p, const CsrDev& g, con
         const int e0 = __ldg(g.row_ptr + row);
         const int d = __ldg(g.row_ptr + row + 1) - e0;
         switch (d) {
-            case 1: unsat |= csr_cn_check<1, T>(p, g, fc, mode, want_synd, row, e0); break;
-            case 2: unsat |= csr_cn_check<2, T>(p, g, fc, mode, want_synd, row, e0); break;
-            case 3: unsat |= csr_cn_check<3, T>(p, g, fc, mode, want_synd, row, e0); break;
-            case 4: unsat |= csr_cn_check<4, T>(p, g, fc, mode, want_synd, row, e0); break;
-            case 5: unsat |= csr_cn_check<5, T>(p, g, fc, mode, want_synd, row, e0); break;
-            case 6: unsat |= csr_cn_check<6, T>(p, g, fc, mode, want_synd, row, e0); break;
-            default: unsat |= csr_cn_check_n<T>(p, g, fc, mode, want_synd, row, e0, d); break;
+            case 1: unsat |= csr_cn_check<1, W, T>(p, g, fc, mode, want_synd, row, e0); break;
+            case 2: unsat |= csr_cn_check<2, W, T>(p, g, fc, mode, want_synd, row, e0); break;
+            case 3: unsat |= csr_cn_check<3, W, T>(p, g, fc, mode, want_synd, row, e0); break;
+            case 4: unsat |= csr_cn_check<4, W, T>(p, g, fc, mode, want_synd, row, e0); break;
+            case 5: unsat |= csr_cn_check<5, W, T>(p, g, fc, mode, want_synd, row, e0); break;
+            case 6: unsat |= csr_cn_check<6, W, T>(p, g, fc, mode, want_synd, row, e0); break;
+            default: unsat |= csr_cn_check_n<W, T>(p, g, fc, mode, want_synd, row, e0, d); break;
         }
     }
     return unsat;
@@ -716,7 +713,7 @@ __device__ __forceinline__ double block_sum_fixed(const double* part, int count,
 // the other groups' CTAs on the same SMs keep computing, and only the few
 // frames in flight have to stay in L2.
 // ---------------------------------------------------------------------------
-template <typename T, class Code>
+template <typename T, class Code, bool W>
 __global__ void __launch_bounds__(kThreads, 4) bp_decode_kernel(Params<T> p, CodeSet<Code> cs) {
     const int SG = p.slots_per_group;
     extern __shared__ double smem_dyn[];
@@ -782,8 +779,8 @@ __global__ void __launch_bounds__(kThreads, 4) bp_decode_kernel(Params<T> p, Cod
             const int mode = k == 0 ? kModeFirst : (k >= p.max_iter ? kModeSynd : kModeFull);
             const bool want_synd = k >= 1 && (p.rule != kRuleNone || k >= p.max_iter);
             FrameCtx<T> fc = frame_ctx(p, ci, s, st_frame[l]);
-            fc.wrow = weight_row(p, k);
-            const bool unsat = cn_tile<T>(p, ci.code, fc, mode, want_synd, tile);
+            if constexpr (W) fc.wrow = weight_row(p, k);
+            const bool unsat = cn_tile<W, T>(p, ci.code, fc, mode, want_synd, tile);
             if (want_synd && __any_sync(0xffffffffu, unsat) && lane == 0)
                 atomicOr(&p.unsat[par * p.slots + s], 1);
         }

@@ -171,7 +171,8 @@ template <typename T, class Code>
 ldpc_status launch_decode(Workspace& ws, const Job& job, const ldpc_decode_opts& o, cudaStream_t stream,
                           int32_t* status_out = nullptr) {
     const int frames = job.frames;
-    auto kernel = bp_decode_kernel<T, Code>;
+    // the weighted kernel is a separate instantiation: the unweighted one carries no weight code
+    auto kernel = job.wts ? bp_decode_kernel<T, Code, true> : bp_decode_kernel<T, Code, false>;
     int dev = 0, sms = 0, per_sm = 0, coop = 0;
     LDPC_TRY(cudaGetDevice(&dev));
     LDPC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
@@ -1005,7 +1006,7 @@ extern "C" ldpc_status ldpc_decode_qc_noalloc(int32_t mb, int32_t nb, int32_t Z,
     LDPC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     LDPC_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     if (!coop) return LDPC_ERR_CUDA;
-    auto kernel = bp_decode_kernel<float, QcDev>;
+    auto kernel = bp_decode_kernel<float, QcDev, false>;
     const size_t smem = (size_t)slots * (sizeof(double) + 4 * sizeof(int));
     LDPC_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSlots * 24));
     LDPC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, kMaxSlots * 24));
