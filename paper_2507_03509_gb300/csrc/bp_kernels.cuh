@@ -217,6 +217,10 @@ __device__ __forceinline__ bool grid_sync(Ctrl* bar, int* err, unsigned nblocks,
     return ld_volatile(err) == kErrNone;
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* ptr) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
+}
+
 __device__ __forceinline__ unsigned syndrome_bit(const unsigned* sb, int row) {
     return (__ldg(sb + (row >> 5)) >> (row & 31)) & 1u;
 }
@@ -252,7 +256,26 @@ __device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, c
         vo[j] = __ldg(q.blk_col + b0 + j) * Z;
         mo[j] = (b0 + j) * Z;
     }
-    // checks in flight per thread: more for light rows (memory-level parallelism)
+    // L2 prefetch of the item's windows (one 128-byte line per 32 positions):
+    // fire-and-forget requests that hold no registers, so many more lines are
+    // in flight than the loads below could keep
+    if constexpr (MODE != kModeSynd) {
+        const int len = t_end - t0;
+        for (int off = 32 * (int)threadIdx.x; off < len; off += 32 * kThreads) {
+#pragma unroll
+            for (int j = 0; j < D; ++j) {
+                int pp = t0 + off + sh[j];
+                pp = pp >= Z ? pp - Z : pp;
+                if constexpr (MODE == kModeFirst) {
+                    prefetch_l2(llr + vo[j] + pp);
+                } else {
+                    prefetch_l2(app + vo[j] + pp);
+                    prefetch_l2(c2v + mo[j] + pp);
+                }
+            }
+        }
+    }
+    // checks in flight per thread
     constexpr int NC = 2;
     bool unsat = false;
     for (int tb = t0 + (int)threadIdx.x; tb < t_end; tb += NC * kThreads) {
@@ -534,6 +557,11 @@ __device__ __forceinline__ void qc_vn_cols(const Params<T>& p, const QcDev& q, c
     bool vec = false;
     if constexpr (sizeof(T) == 4) vec = fc.vec4 != 0;
     const int qb_per_col = (Z + kQBlock - 1) / kQBlock;
+    // L2 prefetch of the item's message blocks and channel values (contiguous)
+    for (int off = u0 + 32 * (int)threadIdx.x; off < u_end; off += 32 * kThreads) {
+        prefetch_l2(llr + off);
+        for (int b = 0; b < nd; ++b) prefetch_l2(c2v + __ldg(q.col_blk + cb0 + b) * Z + off);
+    }
     for (int ub = u0; ub < u_end; ub += kQBlock) {
         const int u = ub + 4 * (int)threadIdx.x;
         T acc = T(0), acc0 = T(0);
