@@ -256,9 +256,10 @@ __device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, c
         vo[j] = __ldg(q.blk_col + b0 + j) * Z;
         mo[j] = (b0 + j) * Z;
     }
-    // L2 prefetch of the item's windows (one 128-byte line per 32 positions):
-    // fire-and-forget requests that hold no registers, so many more lines are
-    // in flight than the loads below could keep
+    // L2 prefetch of the item's message windows (one 128-byte line per 32
+    // positions): fire-and-forget requests that hold no registers, so many more
+    // lines are in flight than the loads below could keep.  APP needs none: each
+    // APP value is read by every block of its column and mostly hits in L2.
     if constexpr (MODE != kModeSynd) {
         const int len = t_end - t0;
         for (int off = 32 * (int)threadIdx.x; off < len; off += 32 * kThreads) {
@@ -269,7 +270,6 @@ __device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, c
                 if constexpr (MODE == kModeFirst) {
                     prefetch_l2(llr + vo[j] + pp);
                 } else {
-                    prefetch_l2(app + vo[j] + pp);
                     prefetch_l2(c2v + mo[j] + pp);
                 }
             }
