@@ -469,7 +469,7 @@ __global__ void sgd_kernel(T* w, const T* g, int count, T lr) {
 // (message blocks are stored unrotated, so a column's messages are
 // contiguous; Z % 4 == 0 keeps four consecutive variables in one frame).
 // ---------------------------------------------------------------------------
-constexpr int kQcCPT = 2;
+constexpr int kQcCPT = 1;
 constexpr int kQcCnTile = kThreads * kQcCPT;
 
 template <int D, bool BWD, typename T>
