@@ -217,11 +217,15 @@ LDPC_API ldpc_status ldpc_batch_decode_async(ldpc_batch* batch, const float* llr
                                              int32_t max_iter, ldpc_term_rule rule, uint8_t* bits_out,
                                              uint8_t* flags_out, int32_t* iters_out, int32_t* status_out,
                                              const ldpc_decode_opts* opts, void* cuda_stream);
-/* Autotuner: decodes the given inputs once per candidate schedule (CTA groups
- * 1, 2, 4, 8 x frames in flight: all, 8 per group, 2 per group), keeps the
- * fastest by kernel time, and uses it for this plan's later decodes whose
- * opts leave groups / max_active_frames at 0.  The outputs hold the last
- * candidate's (identical) results.  best_groups / best_slots may be NULL. */
+/* Autotuner: decodes the given inputs once per candidate block schedule (CTA
+ * groups 1, 2, 4, 8 x frames in flight: all, 8 per group, 2 per group) and
+ * keeps the fastest by kernel time; then, for QC codes, it tunes each code's
+ * item sizes (checks of a base row per item: 512-4096; variables of a base
+ * column: 1024-8192) one code and side at a time from the built-in model's
+ * pick.  The plan uses the result for its later decodes whose opts leave
+ * groups / max_active_frames at 0.  Results do not depend on any of these
+ * choices; the outputs hold the last candidate's results.  best_groups /
+ * best_slots may be NULL. */
 LDPC_API ldpc_status ldpc_batch_autotune(ldpc_batch* batch, const float* llr, const uint8_t* syndrome,
                                          int32_t max_iter, ldpc_term_rule rule, uint8_t* bits_out,
                                          uint8_t* flags_out, int32_t* iters_out, void* cuda_stream,

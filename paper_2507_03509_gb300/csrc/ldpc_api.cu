@@ -128,6 +128,8 @@ struct Job {
     const float* wts;            // learned weights [w_iters][w_classes] or NULL
     const int* wcls;             // class of each base block (QC) / edge (CSR)
     int w_iters, w_classes;
+    int cn_chunk[kMaxCodes];     // QC item sizes chosen by a caller (0: the model's pick)
+    int vn_chunk[kMaxCodes];
 };
 
 // QC item sizes: simulate the static assignment (item it goes to CTA it mod
@@ -219,6 +221,14 @@ ldpc_status launch_decode(Workspace& ws, const Job& job, const ldpc_decode_opts&
         ci.vec4 = 0;
         if (g->kind == 1) {
             pick_chunks(g, grid / groups, slots_per_group, &ci.cn_chunk, &ci.cn_tiles, &ci.vn_chunk, &ci.vn_tiles);
+            if (job.cn_chunk[c] > 0) {  // measured by the batch autotuner
+                ci.cn_chunk = job.cn_chunk[c];
+                ci.cn_tiles = g->mb * ((g->Z + ci.cn_chunk - 1) / ci.cn_chunk);
+            }
+            if (job.vn_chunk[c] > 0) {
+                ci.vn_chunk = job.vn_chunk[c];
+                ci.vn_tiles = g->nb * ((g->Z + ci.vn_chunk - 1) / ci.vn_chunk);
+            }
             ci.nqb = g->nb * ((g->Z + kQBlock - 1) / kQBlock);
             // 16-byte variable-side loads: Z % 4 == 0 and every frame's Lch and
             // decisions 16-byte aligned (the buffer aligned, every frame of the
@@ -662,6 +672,7 @@ struct ldpc_batch {
     long long llr_len = 0, syn_len = 0, sb_words = 0;
     bool var_unaligned[kMaxCodes] = {};     // a frame of code c starts at an offset not a multiple of 4
     int tuned_groups = 0, tuned_slots = 0;  // from ldpc_batch_autotune (0 = none)
+    int tuned_cn[kMaxCodes] = {}, tuned_vn[kMaxCodes] = {};  // QC item sizes per code (0 = model's pick)
     Workspace ws;
 };
 
@@ -696,7 +707,11 @@ ldpc_status batch_launch(ldpc_batch* b, const float* llr, const uint8_t* syndrom
     job.iters_out = iters_out;
     job.max_iter = max_iter;
     job.rule = (int)rule;
-    for (int c = 0; c < kMaxCodes; ++c) job.var_unaligned[c] = b->var_unaligned[c];
+    for (int c = 0; c < kMaxCodes; ++c) {
+        job.var_unaligned[c] = b->var_unaligned[c];
+        job.cn_chunk[c] = b->tuned_cn[c];
+        job.vn_chunk[c] = b->tuned_vn[c];
+    }
     if (b->kind == 1) {
         if (o.fp64) return launch_decode<double, QcDev>(b->ws, job, o, stream, status_out);
         return launch_decode<float, QcDev>(b->ws, job, o, stream, status_out);
@@ -841,6 +856,7 @@ ldpc_status ldpc_batch_autotune(ldpc_batch* b, const float* llr, const uint8_t* 
     const int F = std::min(b->frames, kMaxSlots);
     float best_ms = -1.0f;
     int bg = 0, bs = 0;
+    for (int c = 0; c < kMaxCodes; ++c) b->tuned_cn[c] = b->tuned_vn[c] = 0;  // start from the model
     // one untimed decode at the largest slot count first: sizes the workspace
     // and warms caches and clocks, so the first candidate is not timed cold
     o.groups = 1;
@@ -870,6 +886,34 @@ ldpc_status ldpc_batch_autotune(ldpc_batch* b, const float* llr, const uint8_t* 
     }
     b->tuned_groups = bg;
     b->tuned_slots = bs;
+    // then, per QC code, its item sizes (check side, then variable side) by
+    // coordinate descent from the model's pick, with the block schedule fixed
+    if (b->kind == 1) {
+        static const int cn_cand[] = {512, 1024, 2048, 4096};
+        static const int vn_cand[] = {1024, 2048, 4096, 8192};
+        o.groups = bg;
+        o.max_active_frames = bs;
+        for (int c = 0; c < (int)b->graphs.size(); ++c) {
+            for (int side = 0; side < 2; ++side) {
+                int* slot = side == 0 ? &b->tuned_cn[c] : &b->tuned_vn[c];
+                const int* cand = side == 0 ? cn_cand : vn_cand;
+                int keep = 0;  // 0: the model's pick, timed first
+                for (int ci = -1; ci < 4; ++ci) {
+                    *slot = ci < 0 ? 0 : cand[ci];
+                    ldpc_decode_stats stats{};
+                    o.stats = &stats;
+                    st = batch_launch(b, llr, syndrome, max_iter, rule, bits_out, flags_out, iters_out, o,
+                                      (cudaStream_t)cuda_stream, nullptr);
+                    if (st != LDPC_OK) return st;
+                    if (stats.kernel_ms < best_ms) {
+                        best_ms = stats.kernel_ms;
+                        keep = *slot;
+                    }
+                }
+                *slot = keep;
+            }
+        }
+    }
     if (best_groups) *best_groups = bg;
     if (best_slots) *best_slots = bs;
     return LDPC_OK;
