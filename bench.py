@@ -366,7 +366,10 @@ def run_ours(args):
            "h2d_bytes_per_step": int(frames.llr.nbytes + frames.syndrome.nbytes),
            "d2h_bytes_per_step": int(F * code.n + F + 4 * F)}
 
-    et_regime = None if args.lean or world > 1 else et_paper_regime(ldpc, dev)
+    et_regime = None
+    if not args.lean and world == 1:
+        et_regime = {"regular_3_6": et_paper_regime(ldpc, dev),
+                     "tbp_like_r0.02": et_paper_regime(ldpc, dev, betas=(0.86, 0.88), frames=32, number=7)}
     learned = None
     if wl.get("code_from") == 2 and not args.lean and world == 1:  # the streaming configuration
         learned = {"this_workload": learned_weights_comparison(ldpc, dev, args.workload, code, frames, wl["max_iter"]),
@@ -478,11 +481,12 @@ def learned_weights_comparison(ldpc, dev, number, code, frames, max_iter, T=20, 
     return out
 
 
-def et_paper_regime(ldpc, dev, betas=(0.875, 0.8765), frames=64):
-    """Early termination where the paper measures it: the (3,6)-regular QC code
-    inside its waterfall; K ratios of PCE+VNR against the D_max baselines."""
+def et_paper_regime(ldpc, dev, betas=(0.875, 0.8765), frames=64, number=6):
+    """Early termination where the paper measures it: a code inside its BP
+    waterfall (default the (3,6)-regular QC code); FER, mean iterations, time
+    and K of PCE+VNR against the D_max baselines on the same frames, and the
+    decoding-time ratio wherever the FER of PCE+VNR equals that of D_max 500."""
     import torch
-    number = 6
     code = gen.workload_code(number)
     graph = ldpc.Graph.from_code(code)
     out = {"workload": gen.WORKLOADS[number]["name"], "frames": frames, "points": []}
@@ -502,6 +506,8 @@ def et_paper_regime(ldpc, dev, betas=(0.875, 0.8765), frames=64):
         kv = pt["pce_vnr_500"]["K"]
         pt["K_vnr_over_pce500"] = kv / pt["pce_500"]["K"] if pt["pce_500"]["K"] > 0 else None
         pt["K_vnr_over_pce250"] = kv / pt["pce_250"]["K"] if pt["pce_250"]["K"] > 0 else None
+        if pt["pce_vnr_500"]["fer"] == pt["pce_500"]["fer"]:
+            pt["speedup_at_equal_fer_vs_pce500"] = pt["pce_500"]["ms"] / pt["pce_vnr_500"]["ms"]
         out["points"].append(pt)
     graph.close()
     return out

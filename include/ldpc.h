@@ -284,8 +284,9 @@ LDPC_API ldpc_status ldpc_decode_qc_noalloc(int32_t mb, int32_t nb, int32_t Z, c
  * is created with fp64 = 1.  Every buffer typed `void*` below holds that type.
  * All buffers are device buffers owned by the caller; the plan owns its
  * workspace (allocated at creation).  No call allocates or waits for the GPU:
- * each is stream-ordered and can be captured in a CUDA graph.  Syndrome and
- * bit bytes count as 1 when nonzero.
+ * each is stream-ordered and can be captured in a CUDA graph.  Calls on one
+ * plan share its workspace, so their GPU work must not overlap (order them on
+ * one stream).  Syndrome and bit bytes count as 1 when nonzero.
  * ------------------------------------------------------------------------- */
 typedef struct ldpc_wbp ldpc_wbp;
 
