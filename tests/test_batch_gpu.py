@@ -129,3 +129,32 @@ def test_batch_argument_errors():
         ldpc.Batch([g, q], [0, 1])          # CSR and QC mixed
     with pytest.raises(ldpc.LdpcError):
         ldpc.Batch([g], [0, 1])             # frame_graph out of range
+
+
+def test_csr_batch_matches_per_code_decodes():
+    """A batch of two general (CSR) codes: the n = 4096 code and the n = 256
+    code, frames interleaved; every frame as decoded by its own code alone."""
+    import torch
+    ldpc = lib()
+    codes = [gen.workload_code(1), gen.wbp_fd_code()]
+    graphs = [ldpc.Graph.from_code(c) for c in codes]
+    which = np.array([0, 1, 1, 0, 1, 0, 0, 1, 1, 1], dtype=np.int32)
+    per = []
+    for f, c in enumerate(which):
+        code = codes[c]
+        per.append(gen.make_frames(code, [gen.sigma_for_capacity(code.rate / 0.88)], [6100 + f]))
+    llr = np.concatenate([fr.llr[0] for fr in per])
+    syn = np.concatenate([fr.syndrome[0] for fr in per])
+    batch = ldpc.Batch(graphs, which)
+    dev = torch.device("cuda:0")
+    bits, flags, iters = (t.cpu().numpy() for t in batch.decode(torch.from_numpy(llr).to(dev),
+                                                                 torch.from_numpy(syn).to(dev), 100, "pce_vnr"))
+    off = np.concatenate([[0], np.cumsum([codes[c].n for c in which])])
+    for c, g in enumerate(graphs):
+        idx = np.nonzero(which == c)[0]
+        ref = gpu_decode(ldpc, g, np.stack([per[f].llr[0] for f in idx]), np.stack([per[f].syndrome[0] for f in idx]),
+                         100, "pce_vnr")
+        for i, f in enumerate(idx):
+            assert (bits[off[f]:off[f + 1]] == ref["bits"][i]).all(), f
+            assert flags[f] == ref["flags"][i] and iters[f] == ref["iters"][i], f
+    batch.close()

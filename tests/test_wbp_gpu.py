@@ -381,3 +381,25 @@ def test_weighted_decode_reuses_the_last_row():
         assert np.array_equal(a[k], b[k]), k
     short.close()
     long.close()
+
+
+def test_weighted_decode_csr_matches_oracle(oracle_mod):
+    """Learned-weight decoding of a general (CSR) code, one class per check
+    degree: decisions equal the oracle's (FP64 re-run where FP32 differs)."""
+    ldpc = lib()
+    code, cls, C, fr = fd_setup(frames=8, beta=0.8, seed=9)
+    g = ldpc.Graph.from_code(code)
+    plan = ldpc.WeightedBP(g, 1, 4, cls, C)
+    w = np.random.default_rng(10).uniform(0.7, 1.1, size=(4, C)).astype(np.float32)
+    got = weighted_decode(ldpc, plan, fr, w, 60, "pce_vnr")
+    orc = oracle_mod.decode(code, fr.llr, fr.syndrome, 60, 2, weights=w, edge_class=cls)
+    bad = np.nonzero((got["iters"] != orc["iters"]) | (got["flags"] != orc["flags"])
+                     | (got["bits"] != orc["bits"]).any(1))[0]
+    if bad.size:
+        sub = gen.Frames(fr.x[bad], fr.llr[bad], fr.syndrome[bad], fr.sigma[bad])
+        g64 = weighted_decode(ldpc, plan, sub, w, 60, "pce_vnr", fp64=True)
+        for i, f in enumerate(bad):
+            assert (g64["iters"][i], g64["flags"][i]) == (orc["iters"][f], orc["flags"][f]), f
+            assert np.array_equal(g64["bits"][i], orc["bits"][f]), f
+    assert bad.size <= 2
+    plan.close()
