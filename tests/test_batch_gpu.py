@@ -158,3 +158,32 @@ def test_csr_batch_matches_per_code_decodes():
             assert (bits[off[f]:off[f + 1]] == ref["bits"][i]).all(), f
             assert flags[f] == ref["flags"][i] and iters[f] == ref["iters"][i], f
     batch.close()
+
+
+def test_batch_async_timeout_comes_back_in_the_status_word():
+    """Failure detection on the stream-ordered path: with the test hook that
+    makes the first barrier wait for one CTA more than exist, every wait ends
+    at its 200 ms limit, the device status word reads LDPC_ERR_TIMEOUT (5),
+    and the next decode on the same plan and context is correct."""
+    import torch
+    ldpc = lib()
+    codes = three_codes()
+    graphs = [ldpc.Graph.from_code(c) for c in codes]
+    which, llr, syn, _, _ = make_batch(codes, 6, seed=11)
+    batch = ldpc.Batch(graphs, which)
+    dev = torch.device("cuda:0")
+    t_llr, t_syn = torch.from_numpy(llr).to(dev), torch.from_numpy(syn).to(dev)
+    ref = [t.clone() for t in batch.decode(t_llr, t_syn, 40, "pce_vnr")]
+    out = batch.outputs(dev)
+    status = torch.full((1,), -1, dtype=torch.int32, device=dev)
+    batch.decode_async(t_llr, t_syn, 40, "pce_vnr", out, status, test_unreachable_barrier=True,
+                       barrier_timeout_ms=200)
+    torch.cuda.synchronize()
+    assert status.item() == ldpc.LDPC_ERR_TIMEOUT
+    status.fill_(-1)
+    batch.decode_async(t_llr, t_syn, 40, "pce_vnr", out, status)
+    torch.cuda.synchronize()
+    assert status.item() == 0
+    for a, b in zip(out, ref):
+        assert torch.equal(a, b)
+    batch.close()
