@@ -486,20 +486,31 @@ struct CnIn {
 
 template <int D, bool BWD, typename T>
 __device__ __forceinline__ void qc_cn_load(const Args<T>& a, int f, const int (&ia)[D], const int (&im)[D],
-                                           size_t srow, CnIn<D, T>& in) {
+                                           const unsigned char* syn_t, CnIn<D, T>& in) {
+    // frame base pointers, then 32-bit offsets within the frame
     const size_t fe = (size_t)f * (size_t)a.E, fn = (size_t)f * (size_t)a.n;
+    if (a.app_prev) {
+        const T* xf = a.app_prev + fn;
+        const T* cf = a.c2v_prev + fe;
 #pragma unroll
-    for (int k = 0; k < D; ++k) {
-        if (a.app_prev) {
-            in.x[k] = a.app_prev[fn + ia[k]];
-            in.c[k] = a.c2v_prev[fe + im[k]];
-        } else {
-            in.x[k] = (T)__ldg(a.llr + fn + ia[k]);
+        for (int k = 0; k < D; ++k) {
+            in.x[k] = xf[ia[k]];
+            in.c[k] = cf[im[k]];
+        }
+    } else {
+        const float* lf = a.llr + fn;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            in.x[k] = (T)__ldg(lf + ia[k]);
             in.c[k] = T(0);
         }
-        if constexpr (BWD) in.G[k] = a.G[fe + im[k]];
     }
-    in.sb = __ldg(a.syn + (size_t)f * a.m + srow) != 0 ? 1u : 0u;
+    if constexpr (BWD) {
+        const T* gf = a.G + fe;
+#pragma unroll
+        for (int k = 0; k < D; ++k) in.G[k] = gf[im[k]];
+    }
+    in.sb = __ldg(syn_t + (size_t)f * (size_t)a.m) != 0 ? 1u : 0u;
 }
 
 template <int D, bool BWD, typename T>
@@ -514,8 +525,9 @@ __device__ __forceinline__ void qc_cn_frame(const Args<T>& a, int f, const int (
     }
     cn_core<D>(av, in.sb, a.lmax, o);
     if constexpr (!BWD) {
+        T* of = a.c2v_out + fe;
 #pragma unroll
-        for (int k = 0; k < D; ++k) a.c2v_out[fe + im[k]] = wk[k] * o[k];
+        for (int k = 0; k < D; ++k) of[im[k]] = wk[k] * o[k];
     } else {
         T dt[D], da[D];
 #pragma unroll
@@ -523,7 +535,7 @@ __device__ __forceinline__ void qc_cn_frame(const Args<T>& a, int f, const int (
             acc[k] += in.G[k] * o[k];
             dt[k] = D == 1 ? T(0) : in.G[k] * wk[k];
         }
-        const T sg = in.sb ? T(-1) : T(1);
+    const T sg = in.sb ? T(-1) : T(1);
         if constexpr (D == 1) {
             da[0] = T(0);
         } else if constexpr (sizeof(T) == 4) {
@@ -555,8 +567,9 @@ __device__ __forceinline__ void qc_cn_frame(const Args<T>& a, int f, const int (
                 da[j] = s;
             }
         }
+        T* gf = a.G + fe;
 #pragma unroll
-        for (int j = 0; j < D; ++j) a.G[fe + im[j]] = absm(u[j]) <= a.lmax ? da[j] : T(0);
+        for (int j = 0; j < D; ++j) gf[im[j]] = absm(u[j]) <= a.lmax ? da[j] : T(0);
     }
 }
 
@@ -576,7 +589,7 @@ __device__ __forceinline__ void qc_cn_rows(const Args<T>& a, const QcDev& q, int
         wk[k] = a.w[__ldg(a.cls + b0 + k)];
         acc[k] = T(0);
     }
-    const size_t srow = (size_t)i * Z + t;
+    const unsigned char* syn_t = a.syn + ((size_t)i * Z + t);  // frame 0's byte of check (i, t)
     const int f0 = g * fpc, f_end = min(a.F, f0 + fpc);
     if (t < Z && f0 < f_end) {
         // FP32 adjoint: one frame ahead (measured: training step 6.14 -> 5.93 ms
@@ -585,16 +598,16 @@ __device__ __forceinline__ void qc_cn_rows(const Args<T>& a, const QcDev& q, int
         // FP64 (the parity mode)
         constexpr bool kAhead = BWD && sizeof(T) == 4;
         CnIn<D, T> cur;
-        qc_cn_load<D, BWD>(a, f0, ia, im, srow, cur);
+        qc_cn_load<D, BWD>(a, f0, ia, im, syn_t, cur);
         for (int f = f0; f < f_end; ++f) {
             if constexpr (kAhead) {
                 CnIn<D, T> nxt;
                 const bool more = f + 1 < f_end;
-                if (more) qc_cn_load<D, BWD>(a, f + 1, ia, im, srow, nxt);
+                if (more) qc_cn_load<D, BWD>(a, f + 1, ia, im, syn_t, nxt);
                 qc_cn_frame<D, BWD>(a, f, im, wk, cur, acc);
                 if (more) cur = nxt;
             } else {
-                if (f > f0) qc_cn_load<D, BWD>(a, f, ia, im, srow, cur);
+                if (f > f0) qc_cn_load<D, BWD>(a, f, ia, im, syn_t, cur);
                 qc_cn_frame<D, BWD>(a, f, im, wk, cur, acc);
             }
         }
@@ -641,9 +654,19 @@ __global__ void __launch_bounds__(kThreads, 4) qc_cn_kernel(Args<T> a, QcDev q, 
     for (long long blk = blockIdx.x; blk < total; blk += gridDim.x) {
         // row-major over (row, tile), frame groups innermost: CTAs that run
         // together share the row's table and read neighbouring frames
-        const int g = (int)(blk % groups);
-        const long long rt = blk / groups;
-        const int i = (int)(rt / tiles), tile = (int)(rt - (long long)i * tiles);
+        // (32-bit division where the index fits: the 64-bit one is a long routine)
+        int g, i, tile;
+        if (total <= 0x7fffffffLL) {
+            const int b = (int)blk, rt = b / groups;
+            g = b - rt * groups;
+            i = rt / tiles;
+            tile = rt - i * tiles;
+        } else {
+            const long long rt = blk / groups;
+            g = (int)(blk - rt * groups);
+            i = (int)(rt / tiles);
+            tile = (int)(rt - (long long)i * tiles);
+        }
         const int b0 = __ldg(q.row_ptr + i), d = __ldg(q.row_ptr + i + 1) - b0;
         switch (d) {
             case 0: break;
