@@ -646,8 +646,14 @@ __device__ __noinline__ void qc_cn_rows_n(const Args<T> a, const QcDev q, int g,
     }
 }
 
+// Occupancy over registers: these passes are bound by the latency of their
+// gathers, so more resident warps pay more than spill-free code.  Measured on
+// the n = 65536, 128-frame training step: 4 CTAs per SM for both passes (64
+// registers, no spills in the forward) 5.80 ms; forward 8 CTAs per SM (32
+// registers) with the adjoint at 6 (40 registers) 5.33 ms; forward 6, adjoint
+// 5: 5.37 ms.  FP64 plans (the parity mode) keep 4 CTAs per SM.
 template <bool BWD, typename T>
-__global__ void __launch_bounds__(kThreads, 4) qc_cn_kernel(Args<T> a, QcDev q, int tiles, int fpc, double* wpart) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (BWD ? 6 : 8) : 4) qc_cn_kernel(Args<T> a, QcDev q, int tiles, int fpc, double* wpart) {
     __shared__ double sm[kThreads / 32];
     const int groups = (a.F + fpc - 1) / fpc;
     const long long total = (long long)groups * q.mb * tiles;
@@ -793,8 +799,10 @@ __device__ __forceinline__ void qc_vn_cols(const Args<T>& a, const QcDev& q, int
     }
 }
 
+// 6 CTAs per SM (40 registers) for FP32: 5.29 -> 5.15 ms per training step at
+// n = 65536 x 128 frames (8 per SM: 5.23 ms).
 template <int MODE, typename T>
-__global__ void __launch_bounds__(kThreads) qc_vn_kernel(Args<T> a, QcDev q, int fpc, const T* grad_app) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 1) qc_vn_kernel(Args<T> a, QcDev q, int fpc, const T* grad_app) {
     const int groups = (a.F + fpc - 1) / fpc;
     const long long total = (long long)groups * q.nb;
     for (long long blk = blockIdx.x; blk < total; blk += gridDim.x) {
