@@ -458,11 +458,8 @@ __global__ void sgd_kernel(T* w, const T* g, int count, T lr) {
 // and every thread keeps a steady stream of independent loads in flight.
 //
 // Check side: a CTA covers kQcCnTile consecutive checks t of base row i (tile)
-// for each frame of its group, one check per thread per frame.  In the FP32
-// adjoint the loads of frame f + 1 are issued before the arithmetic of frame f
-// (software pipelining), so every thread keeps one frame's loads in flight
-// while it computes; the arithmetic and its order are those of one frame at a
-// time.
+// for each frame of its group, one check per thread per frame; the latency of
+// the gathers is hidden by many resident warps (see the launch bounds).
 // In the adjoint it also sums G * t per block over its checks and frames (per
 // thread in the plan's type, frames in ascending order, then a fixed-order
 // FP64 block reduction) into wpart[(g * nblk + b) * tiles + tile], g the frame
@@ -592,24 +589,13 @@ __device__ __forceinline__ void qc_cn_rows(const Args<T>& a, const QcDev& q, int
     const unsigned char* syn_t = a.syn + ((size_t)i * Z + t);  // frame 0's byte of check (i, t)
     const int f0 = g * fpc, f_end = min(a.F, f0 + fpc);
     if (t < Z && f0 < f_end) {
-        // FP32 adjoint: one frame ahead (measured: training step 6.14 -> 5.93 ms
-        // at n = 65536 x 128 frames); the forward pass, whose checks carry fewer
-        // loads, was 2 % slower that way and keeps one frame at a time, as does
-        // FP64 (the parity mode)
-        constexpr bool kAhead = BWD && sizeof(T) == 4;
-        CnIn<D, T> cur;
-        qc_cn_load<D, BWD>(a, f0, ia, im, syn_t, cur);
+        // one frame at a time: with 5-8 resident CTAs per SM, loading frame
+        // f + 1 ahead of frame f's arithmetic (more registers, more spills) was
+        // slower; it paid only at 4 CTAs per SM
+        CnIn<D, T> in;
         for (int f = f0; f < f_end; ++f) {
-            if constexpr (kAhead) {
-                CnIn<D, T> nxt;
-                const bool more = f + 1 < f_end;
-                if (more) qc_cn_load<D, BWD>(a, f + 1, ia, im, syn_t, nxt);
-                qc_cn_frame<D, BWD>(a, f, im, wk, cur, acc);
-                if (more) cur = nxt;
-            } else {
-                if (f > f0) qc_cn_load<D, BWD>(a, f, ia, im, syn_t, cur);
-                qc_cn_frame<D, BWD>(a, f, im, wk, cur, acc);
-            }
+            qc_cn_load<D, BWD>(a, f, ia, im, syn_t, in);
+            qc_cn_frame<D, BWD>(a, f, im, wk, in, acc);
         }
     }
     if constexpr (BWD) {
@@ -647,13 +633,16 @@ __device__ __noinline__ void qc_cn_rows_n(const Args<T> a, const QcDev q, int g,
 }
 
 // Occupancy over registers: these passes are bound by the latency of their
-// gathers, so more resident warps pay more than spill-free code.  Measured on
-// the n = 65536, 128-frame training step: 4 CTAs per SM for both passes (64
-// registers, no spills in the forward) 5.80 ms; forward 8 CTAs per SM (32
-// registers) with the adjoint at 6 (40 registers) 5.33 ms; forward 6, adjoint
-// 5: 5.37 ms.  FP64 plans (the parity mode) keep 4 CTAs per SM.
+// gathers, so more resident warps pay more than spill-free code, up to the
+// point where spill traffic (local loads wait like gathers) eats the gain.
+// Measured on the n = 65536, 128-frame training step: 4 CTAs per SM for both
+// passes (64 registers, adjoint loading one frame ahead) 5.80 ms; forward at
+// 8 CTAs per SM (32 registers) with the adjoint at 6 (40 registers) 5.33 ms;
+// adjoint one frame at a time at 5 (48 registers, 68 bytes of spills)
+// 4.73 ms, at 6 (40 registers, 128 bytes) 5.21 ms, at 8 5.50 ms.  FP64 plans
+// (the parity mode) keep 4 CTAs per SM.
 template <bool BWD, typename T>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (BWD ? 6 : 8) : 4) qc_cn_kernel(Args<T> a, QcDev q, int tiles, int fpc, double* wpart) {
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? (BWD ? 5 : 8) : 4) qc_cn_kernel(Args<T> a, QcDev q, int tiles, int fpc, double* wpart) {
     __shared__ double sm[kThreads / 32];
     const int groups = (a.F + fpc - 1) / fpc;
     const long long total = (long long)groups * q.mb * tiles;
