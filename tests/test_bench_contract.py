@@ -38,6 +38,8 @@ def test_reference_arm_headline_workload(oracle_mod):
     d = reference_line()
     check_contract(d)
     assert d["config"]["workload"] == "qc_n1e6_r0.02" and d["unit"] == "Mbit/s"
+    # the per-core figure beside the all-core rate
+    assert d["cpu_baseline"]["single_thread_s_per_frame_iter"] > 0 and d["cpu_baseline"]["single_thread_sample"]
 
 
 @pytest.mark.parametrize("extra", [("--workload", "3", "--frames", "6"), ("--workload", "4")])
