@@ -15,6 +15,8 @@ not decode and leaves it alone where they do, and so raises K = N R (1 - FER)/D
 (3,6)-regular QC code (the base matrix of the n = 960,000 sweep code, lifted by
 Z = 64) across its waterfall.  CPU only.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -81,3 +83,34 @@ def test_paper_regime_on_the_waterfall(runs):
     r = runs[0.95]
     assert fer(r["pce"]) == 1.0 and fer(r["vnr"]) == 1.0
     assert r["vnr"]["iters"].mean() < 0.3 * D_MAX
+
+
+def _stored(name):
+    """Stored oracle decisions: {frame: (iters, flags, bits sha256)}."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    rows = {}
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            f, it, fl, _, h = line.split()
+            rows[int(f)] = (int(it), int(fl), h)
+    return rows
+
+
+@pytest.mark.parametrize("workload,rules,d_max", [
+    ("csr_n4096_r0.1", ("none", "pce", "pce_vnr"), 200),
+    ("qc_n1e6_r0.02", ("pce", "pce_vnr"), 500),
+])
+def test_stored_full_size_decisions_keep_the_order_of_the_rules(workload, rules, d_max):
+    # the decisions the GPU parity tests compare with obey the same per-frame order
+    runs = {r: _stored(f"oracle_{workload}_{r}.txt") for r in rules}
+    frames = runs["pce"].keys()
+    assert all(runs[r].keys() == frames for r in rules)
+    for f in frames:
+        pce, vnr = runs["pce"][f], runs["pce_vnr"][f]
+        if "none" in runs:
+            assert runs["none"][f][0] == d_max
+        assert vnr[0] <= pce[0] <= d_max
+        if not vnr[1] & ABORTED:
+            assert vnr == pce
+        else:
+            assert not vnr[1] & SUCCESS and (pce[0] > vnr[0] or not pce[1] & SUCCESS)
