@@ -121,8 +121,10 @@ typedef struct ldpc_decode_opts {
  * concurrency and grid, no trace, no stats).  NULL is ignored. */
 LDPC_API void ldpc_decode_opts_init(ldpc_decode_opts* opts);
 
-/* Build a decoder graph from a binary H in check-major CSR form (paper:
- * "a bipartite graph, which is defined by the parity check matrix H").
+/* Build a decoder graph from a binary H in check-major CSR form: the Tanner
+ * graph on which the paper's decoder passes messages (section "Early
+ * Termination") has one check node per row of H and one variable node per
+ * column, joined wherever H holds a 1.
  *   m, n     : checks, variables (m >= 1, n >= 1)
  *   row_ptr  : host int32 [m+1], row_ptr[0] = 0, non-decreasing
  *   col_idx  : host int32 [row_ptr[m]], each row strictly increasing, in [0, n)
@@ -249,6 +251,9 @@ LDPC_API ldpc_status ldpc_batch_autotune(ldpc_batch* batch, const float* llr, co
  * vnr_first_iter 2, clamp 25).  The graph tables and all decoder state live in
  * one file-scope device array of LDPC_NOALLOC_SCRATCH_BYTES; as many frames as
  * fit are decoded at once and the rest wait in the queue.
+ * Schedule: one CTA group over the whole grid and the default item sizes
+ * (2048 checks, 4096 variables), whatever ldpc_decode would pick; results are
+ * bit-identical to ldpc_decode's, only the speed differs.
  *
  * Limits: the packed syndrome of all frames plus the state of one frame
  * (about 14 bytes per edge plus 8 bytes per variable) must fit the scratch,

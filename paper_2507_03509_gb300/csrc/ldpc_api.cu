@@ -180,11 +180,11 @@ ldpc_status launch_decode(Workspace& ws, const Job& job, const ldpc_decode_opts&
     LDPC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     LDPC_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     if (!coop) return LDPC_ERR_CUDA;
-    // occupancy with the largest slot table we may use (28 bytes of shared memory per slot)
-    const auto smem_for = [](int sg) { return (size_t)((sg * 28 + 127) / 128) * 128; };
-    LDPC_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_for(kMaxSlots)));
+    // occupancy with the largest slot table we may use
+    LDPC_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)decode_smem_bytes(kMaxSlots)));
     LDPC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads,
-                                                           smem_for(std::min(frames, kMaxSlots))));
+                                                           decode_smem_bytes(std::min(frames, kMaxSlots))));
     if (per_sm < 1) return LDPC_ERR_CUDA;
     int grid = std::min(per_sm * sms, kMaxGrid);
     if (o.grid_ctas > 0) grid = std::min(grid, o.grid_ctas);
@@ -197,7 +197,7 @@ ldpc_status launch_decode(Workspace& ws, const Job& job, const ldpc_decode_opts&
     const int slots_per_group = (want_slots + groups - 1) / groups;
     const int slots = groups * slots_per_group;
     grid = (grid / groups) * groups;
-    const size_t smem = smem_for(slots_per_group);
+    const size_t smem = decode_smem_bytes(slots_per_group);
 
     // per-code sizes; slots are sized for the largest code
     CodeSet<Code> cs{};
@@ -1051,9 +1051,11 @@ extern "C" ldpc_status ldpc_decode_qc_noalloc(int32_t mb, int32_t nb, int32_t Z,
     LDPC_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
     if (!coop) return LDPC_ERR_CUDA;
     auto kernel = bp_decode_kernel<float, QcDev, false>;
-    const size_t smem = (size_t)slots * (sizeof(double) + 4 * sizeof(int));
-    LDPC_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSlots * 24));
-    LDPC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, kMaxSlots * 24));
+    // one group holds every slot: the same per-slot table as ldpc_decode's launches
+    const size_t smem = decode_smem_bytes(slots);
+    LDPC_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)decode_smem_bytes(kMaxSlots)));
+    LDPC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem));
     if (per_sm < 1) return LDPC_ERR_CUDA;
     const int grid = std::min(per_sm * sms, kMaxGrid);
 

@@ -38,7 +38,12 @@ def _noalloc(ldpc, code, llr, syn, max_iter, rule):
     return dict(bits=bits.cpu().numpy(), flags=flags.cpu().numpy(), iters=iters.cpu().numpy())
 
 
-@pytest.mark.parametrize("Z,frames,max_iter", [(2600, (6, 9), 60), (20000, (8, 5), 12)])
+# (lifting size, frames of the two calls, D_max).  The small liftings put one
+# frame in each of hundreds of slots, so the per-slot tables in shared memory
+# are at their largest; the Z = 20000 case (n = 10^6) does not fit every frame
+# at once and refills slots from the queue.
+@pytest.mark.parametrize("Z,frames,max_iter", [(2600, (6, 9), 60), (20000, (8, 5), 12), (64, (256, 200), 60),
+                                               (512, (96, 128), 40)])
 def test_noalloc_matches_ldpc_decode_on_consecutive_calls(Z, frames, max_iter):
     ldpc = lib()
     code = gen.workload_code(2, Z=Z)
