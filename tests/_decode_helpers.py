@@ -5,10 +5,47 @@ Tolerances: per-edge messages and APP values agree to 1e-4 relative plus
 1e-5 absolute over the first 10 iterations; decisions (bits, flags,
 iterations) agree on every frame, and a frame whose FP32 decisions differ is
 re-run in the decoder's FP64 mode, which must agree with the oracle exactly.
+
+How many frames may take either way out is capped per call (FP32_ESCAPE_FRAC,
+FP64_TIE_FRAC), and every call's counts are kept in PARITY_LOG, which the
+test session prints at its end.
 """
+import os
+
 import numpy as np
 
 RTOL, ATOL = 1e-4, 1e-5
+
+# At most this fraction of a call's frames (at least one frame) may differ in
+# FP32 and be accepted through the FP64 re-run and the trajectory check ...
+FP32_ESCAPE_FRAC = 0.10
+# ... and at most this fraction (at least one frame) may still differ in the
+# FP64 re-run and be accepted as an FP64-level near-tie of the trajectory.
+# Such frames reached a fixed point that is not a codeword: q then rises by
+# geometrically shrinking steps, and the VNR test stops the frame once a step
+# falls below FP64 rounding noise, at an iteration that the summation order
+# decides.  The most seen is 2 of the 64 frames of the n = 4096 workload.
+FP64_TIE_FRAC = 0.05
+
+# One entry per decision comparison of the session: test, rule, frames, the
+# frames that differed in FP32 and those accepted as FP64 near-ties.
+PARITY_LOG = []
+
+
+# Largest relative difference |q_gpu - q_oracle| / q_oracle seen per traced
+# comparison (test_q_trace_within_tie_band), printed at the session's end.
+Q_LOG = []
+
+
+def escape_caps(frames, fp32_escape_frac=FP32_ESCAPE_FRAC):
+    """(FP32 escapes, FP64 near-ties) allowed for a comparison of `frames` frames."""
+    return max(1, int(fp32_escape_frac * frames)), max(1, int(FP64_TIE_FRAC * frames))
+
+
+def log_parity(rule, frames, fp32_mismatch, fp64_ties):
+    test = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
+    PARITY_LOG.append(dict(test=test, rule=rule, frames=int(frames), fp32_mismatch=[int(f) for f in fp32_mismatch],
+                           fp64_ties=[int(f) for f in fp64_ties]))
 
 
 def lib():
@@ -147,7 +184,7 @@ def validate_trajectory(oracle, code, llr_f, syn_f, res, orc, max_iter, rule, pr
 
 
 def check_decisions(ldpc, graph, code_csr, oracle, llr, syn, max_iter, rule, report=None,
-                    max_mismatch_frac=1.0, **opts):
+                    fp32_escape_frac=FP32_ESCAPE_FRAC, **opts):
     """FP32 GPU decisions vs the oracle on every frame.
 
     Frames that differ are re-run in the decoder's FP64 mode, which must agree
@@ -155,17 +192,18 @@ def check_decisions(ldpc, graph, code_csr, oracle, llr, syn, max_iter, rule, rep
     near-tie at FP64 rounding level, pass validate_trajectory at FP64
     tolerance.  The FP32 result of every differing frame must pass
     validate_trajectory at FP32 tolerance (so no difference is accepted unless
-    the oracle's own trajectory shows a near-tie there), and at most
-    max_mismatch_frac of the frames may differ.  FP32 differences are mostly VNR
+    the oracle's own trajectory shows a near-tie there).  escape_caps() bounds
+    how many frames may take each way out.  FP32 differences are mostly VNR
     aborts on frames that reached a fixed point: there the FP64 q stays flat (a
-    tie, decoding goes on) while the FP32 q moves by an ulp and may fall.
+    tie, decoding goes on) while the FP32 q moves by rounding and may fall.
     Returns (differing frames, gpu result, oracle result)."""
     kw = dict(vnr_first_iter=opts.get("vnr_first_iter", 2), clamp=opts.get("clamp", 25.0))
     orc = oracle.decode(code_csr, llr, syn, max_iter, RULE_IDS[rule], vnr_first_iter=kw["vnr_first_iter"],
                         lmax=kw["clamp"])
     got = gpu_decode(ldpc, graph, llr, syn, max_iter, rule, **opts)
     bad = mismatched_frames(got, orc)
-    assert bad.size <= max(1, int(max_mismatch_frac * llr.shape[0])), \
+    cap32, cap64 = escape_caps(llr.shape[0], fp32_escape_frac)
+    assert bad.size <= cap32, \
         (f"FP32 decisions differ on {bad.size} of {llr.shape[0]} frames: "
          + "; ".join(f"f{f}: gpu D={got['iters'][f]} fl={got['flags'][f]} / oracle D={orc['iters'][f]} "
                      f"fl={orc['flags'][f]}, {(got['bits'][f] != orc['bits'][f]).sum()} bits" for f in bad))
@@ -182,6 +220,8 @@ def check_decisions(ldpc, graph, code_csr, oracle, llr, syn, max_iter, rule, rep
                 p64 = validate_trajectory(oracle, code_csr, llr[f], syn[f], r64, o, max_iter, rule, "fp64", **kw)
                 assert not p64, f"frame {f} (FP64 re-run): {p64}"
                 fp64_ties.append(int(f))
+    log_parity(rule, llr.shape[0], bad, fp64_ties)
+    assert len(fp64_ties) <= cap64, f"{len(fp64_ties)} frames hang on FP64 near-ties: {fp64_ties}"
     if report is not None:
         report.append(dict(rule=rule, frames=int(llr.shape[0]), fp32_mismatch=bad.tolist(), fp64_ties=fp64_ties))
     return bad.tolist(), got, orc

@@ -17,7 +17,7 @@ import numpy as np
 import pytest
 
 from paper_2507_03509_gb300 import gen
-from _decode_helpers import assert_close_messages, gpu_decode, lib, validate_trajectory
+from _decode_helpers import assert_close_messages, escape_caps, gpu_decode, lib, log_parity, validate_trajectory
 
 pytestmark = pytest.mark.gpu
 
@@ -59,6 +59,8 @@ def test_fullsize_decisions_match_stored_oracle(ldpc, full, rule):
     got = gpu_decode(ldpc, graph, fr.llr, fr.syndrome, w["max_iter"], rule)
     bad = [f for f in range(fr.llr.shape[0])
            if (got["iters"][f], got["flags"][f], digest(got["bits"][f])) != (gold[f][0], gold[f][1], gold[f][3])]
+    log_parity(rule, fr.llr.shape[0], bad, [])
+    assert len(bad) <= escape_caps(fr.llr.shape[0])[0], f"FP32 decisions differ on frames {bad}"
     if bad:
         idx = np.asarray(bad)
         g64 = gpu_decode(ldpc, graph, fr.llr[idx], fr.syndrome[idx], w["max_iter"], rule, fp64=True)
@@ -147,6 +149,8 @@ def test_batch_fullsize_decisions_match_stored_oracle(ldpc, oracle_mod):
     bits, flags, iters = (t.cpu().numpy() for t in out)
     got = {f: (int(iters[f]), int(flags[f]), digest(bits[bf.var_off[f]:bf.var_off[f + 1]])) for f in range(F)}
     bad = [f for f in range(F) if got[f] != (gold[f][0], gold[f][1], gold[f][3])]
+    cap32, cap64 = escape_caps(F)
+    assert len(bad) <= cap32, f"FP32 decisions differ on {len(bad)} of {F} frames: {bad}"
     fp64_ties = []
     for c, (code, g) in enumerate(zip(codes, graphs)):
         idx = [f for f in bad if bf.frame_code[f] == c]
@@ -167,5 +171,7 @@ def test_batch_fullsize_decisions_match_stored_oracle(ldpc, oracle_mod):
         if f not in bad:
             x = bf.x[bf.var_off[f]:bf.var_off[f + 1]]
             assert int((bits[bf.var_off[f]:bf.var_off[f + 1]] != x).sum()) == gold[f][2]
+    log_parity("pce_vnr", F, bad, fp64_ties)
+    assert len(fp64_ties) <= cap64, f"{len(fp64_ties)} frames hang on FP64 near-ties: {fp64_ties}"
     print(f"batch parity: {len(bad)} of {F} frames re-run in FP64, {len(fp64_ties)} FP64 near-ties {fp64_ties}")
     batch.close()

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from paper_2507_03509_gb300 import gen
-from _decode_helpers import (assert_close_messages, check_decisions, gpu_decode, lib,
+from _decode_helpers import (Q_LOG, TOL, assert_close_messages, check_decisions, gpu_decode, lib,
                              mismatched_frames, RULE_IDS)
 
 pytestmark = pytest.mark.gpu
@@ -58,6 +58,40 @@ def test_trace_messages_qc(ldpc, oracle, qc_small):
     assert_close_messages(got["c2v"], orc["c2v"], "c2v")
     assert_close_messages(got["app"], orc["app"], "app")
     np.testing.assert_allclose(got["q"], orc["q"], rtol=1e-5)
+
+
+@pytest.mark.parametrize("case", ["csr_n4096", "qc_z2600", "reg36_z64"])
+def test_q_trace_within_tie_band(ldpc, oracle, csr1, qc_small, case):
+    """q^(k) of the FP32 decoder (FP64 sums of FP32 APP values) against the
+    oracle's FP64 q, rule NONE.  A VNR decision can only differ from the
+    oracle's where the oracle's own step q^(k) - q^(k-1) is within the two
+    iterations' q differences, so the near-tie band rtol_q of the decision
+    checks must be at least twice the largest relative difference; the test
+    holds the difference to half the band over the first 20 iterations and
+    records it over 60 (unconverged frames drift apart later, A25)."""
+    import torch
+    if case == "csr_n4096":
+        code, fr = csr1, gen.workload_frames(1, csr1, frames=16)
+    elif case == "qc_z2600":
+        code, fr = qc_small, gen.workload_frames(2, qc_small, frames=4)
+    else:
+        code = gen.workload_code(6, Z=64)
+        fr = gen.workload_frames(6, code, frames=16, beta=0.8)
+    K = 60
+    csr = code.to_csr() if hasattr(code, "to_csr") else code
+    orc = oracle.decode(csr, fr.llr, fr.syndrome, K, 0, trace_iters=K, trace=("q",))
+    g = ldpc.Graph.from_code(code)
+    dev = torch.device("cuda:0")
+    tq = torch.full((K, fr.llr.shape[0]), float("nan"), dtype=torch.float64, device=dev)
+    ldpc.decode(g, torch.from_numpy(fr.llr).to(dev), torch.from_numpy(fr.syndrome).to(dev), K, "none",
+                trace_iters=K, trace_q=tq)
+    torch.cuda.synchronize()
+    q = tq.cpu().numpy()
+    rel = np.abs(q - orc["q"]) / np.abs(orc["q"])
+    Q_LOG.append(dict(case=case, max_rel=float(rel[:20].max()), iters=20, rtol_q=TOL["fp32"]["rtol_q"]))
+    Q_LOG.append(dict(case=case, max_rel=float(rel.max()), iters=K, rtol_q=TOL["fp32"]["rtol_q"]))
+    assert rel[:20].max() <= 0.5 * TOL["fp32"]["rtol_q"], f"max relative q difference {rel[:20].max():.3g}"
+    g.close()
 
 
 @pytest.mark.parametrize("rule", ["pce_vnr", "pce", "none"])
@@ -198,8 +232,12 @@ def test_degenerate_qc_shapes(ldpc, oracle):
     got = gpu_decode(ldpc, g, llr, s, 10, "none", trace_iters=10)
     assert_close_messages(got["c2v"], orc["c2v"], "c2v")
     assert_close_messages(got["app"], orc["app"], "app")
+    # Nearly a forest: every frame reaches an exact fixed point within three
+    # iterations, after which q is flat in exact arithmetic, so each VNR test is
+    # a tie (A5) that FP32 rounding may break either way.  Every such frame
+    # still has to pass the trajectory check and agree exactly in FP64.
     for rule in ("pce_vnr", "pce"):
-        check_decisions(ldpc, g, code.to_csr(), oracle, llr, s, 12, rule)
+        check_decisions(ldpc, g, code.to_csr(), oracle, llr, s, 12, rule, fp32_escape_frac=1.0)
 
 
 @pytest.mark.parametrize("opts", [dict(vnr_first_iter=1), dict(clamp=8.0), dict(vnr_first_iter=4)])

@@ -6,9 +6,9 @@ products) with other summation orders, so APP, loss and gradients agree to
 up to ~1e10 at saturated inputs), hence 1e-9 here.  FP32 plans run the
 decoder's r-domain check rule with fast exp/log (a few ulp per operation);
 APP values agree with the oracle like the decoder's messages do (1e-4 relative
-plus 1e-4 absolute after 10-20 iterations), and the gradients, sums of
-products of such values over every iteration, to 2e-3 of the largest
-component.
+plus 1e-4 absolute after 10-20 iterations), and every gradient element, a sum
+of products of such values over every iteration, to 2e-3 of its own value
+plus 1e-4 of the largest element of its row.
 """
 import numpy as np
 import pytest
@@ -98,10 +98,25 @@ def check(got, ref, fp64):
     else:
         np.testing.assert_allclose(got["app"], ref["app"], rtol=1e-4, atol=1e-4)
         assert got["loss"] == pytest.approx(ref["loss"], rel=1e-5)
-        sc = np.abs(ref["grad_w"]).max()
-        assert np.abs(got["grad_w"] - ref["grad_w"]).max() <= 2e-3 * sc
-        scl = np.abs(ref["grad_llr"]).max()
-        assert np.abs(got["grad_llr"] - ref["grad_llr"]).max() <= 2e-3 * scl
+        # every element to FP32_GRAD_RTOL of its own FP64 value, with an absolute
+        # floor of FP32_GRAD_FLOOR times the largest value of its row (one
+        # iteration's weights, one frame's channel values), so a small class
+        # gradient is held to its own size, not to the largest one's
+        per_element_close(got["grad_w"], ref["grad_w"], "grad_w")
+        per_element_close(got["grad_llr"], ref["grad_llr"], "grad_llr")
+
+
+FP32_GRAD_RTOL, FP32_GRAD_FLOOR = 2e-3, 1e-4
+
+
+def per_element_close(got, want, what):
+    floor = FP32_GRAD_FLOOR * np.abs(want).max(axis=-1, keepdims=True)
+    err = np.abs(got - want)
+    tol = FP32_GRAD_RTOL * np.abs(want) + floor
+    worst = np.unravel_index(np.argmax(err / np.maximum(tol, 1e-300)), err.shape)
+    assert (err <= tol).all(), (f"{what}: {(err > tol).sum()} of {err.size} elements out of tolerance; worst at "
+                                f"{worst}: got {got[worst]:.6g}, want {want[worst]:.6g}, ratio "
+                                f"{err[worst] / tol[worst]:.3g}")
 
 
 def test_fp64_gradient_matches_finite_differences():
@@ -219,8 +234,7 @@ def test_fullsize_training_step_and_sampled_parity(oracle_mod):
     ref = oracle_mod.wbp(code.to_csr(), fr.llr[:2], fr.syndrome[:2], fr.x[:2], T, cls_csr, wv, grad=True)
     np.testing.assert_allclose(app_s.double().cpu().numpy(), ref["app"], rtol=1e-4, atol=1e-4)
     assert float(loss_s.item()) == pytest.approx(ref["loss"], rel=1e-5)
-    sc = np.abs(ref["grad_w"]).max()
-    assert np.abs(gw_s.double().cpu().numpy() - ref["grad_w"]).max() <= 2e-3 * sc
+    per_element_close(gw_s.double().cpu().numpy(), ref["grad_w"], "grad_w")
     # SGD lowers the loss
     losses = []
     for _ in range(4):
