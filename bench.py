@@ -53,8 +53,10 @@ def parse():
                     help="only the timed decodes: no fixed-iteration runs, no host-buffer runs, no CPU baseline")
     ap.add_argument("--sweep", action="store_true",
                     help="beta sweep (paper Figs. 1-2): FER, mean iterations and throughput K for PCE-ET with "
-                         "D_max in {100, 250, 500} against PCE+VNR-ET; prints one JSON line per beta")
+                         "D_max in {100, 250, 500, 1000} against PCE+VNR-ET; prints one JSON line per beta")
     ap.add_argument("--betas", default="0.84,0.85,0.86,0.87,0.88,0.89,0.90,0.92")
+    ap.add_argument("--et-frames", type=int, default=512,
+                    help="frames per beta of the equal-FER early-termination comparison")
     return ap.parse_args()
 
 
@@ -80,8 +82,11 @@ def job_value_mbit_s(n: int, frames_per_rank: int, steps: int, world: int, job_m
 
 
 def algorithmic_bytes_per_frame_iter(code) -> int:
-    """8E (c2v read + write) + 12n (Lch read, APP write, APP read once)."""
-    return 8 * int(code.edges) + 12 * int(code.n)
+    """8E (c2v read + write) + 12n (Lch read, APP write, APP read once), plus
+    for a CSR code its index reads: col_idx on the check side (4E) and the
+    variable-major edge list on the variable side (4E).  A QC code needs no
+    index bytes (positions come from the shift table)."""
+    return 8 * int(code.edges) + 12 * int(code.n) + csr_index_bytes_per_frame_iter(code)
 
 
 DECODER_SOURCES = ("bp_kernels.cuh", "cn_math.cuh", "device_types.h", "host_common.h", "ldpc_api.cu")
@@ -265,19 +270,8 @@ def run_reference(args):
 # ---------------------------------------------------------------------------
 def run_ours(args):
     import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-
-    from paper_2507_03509_gb300 import build
-    build.build()
-    from paper_2507_03509_gb300 import ldpc
+    ctx = gpu_context()
+    ldpc, dev, dist, world, rank, local = ctx
 
     wl = dict(gen.WORKLOADS[args.workload])
     if args.max_iter:
@@ -388,8 +382,11 @@ def run_ours(args):
 
     et_regime = None
     if not args.lean and world == 1:
-        et_regime = {"regular_3_6": et_paper_regime(ldpc, dev),
-                     "tbp_like_r0.02": et_paper_regime(ldpc, dev, betas=(0.86, 0.88), frames=32, number=7)}
+        et_regime = {"tbp_like_r0.02": et_equal_fer(ldpc, dev, 7, (0.83, 0.84), frames=args.et_frames),
+                     "regular_3_6": et_equal_fer(ldpc, dev, 6, (0.8735, 0.875), frames=args.et_frames)}
+    others = None
+    if not args.lean and world == 1 and args.workload == 2:
+        others = other_configurations(args, ctx)
     learned = None
     if wl.get("code_from") == 2 and not args.lean and world == 1:  # the streaming configuration
         learned = {"this_workload": learned_weights_comparison(ldpc, dev, args.workload, code, frames, wl["max_iter"]),
@@ -425,8 +422,9 @@ def run_ours(args):
         "et_speedup": None if not comp else {
             "vs_pce": comp["pce"]["ms_per_step"] / (main["ms"] / args.steps),
             "vs_none": comp["none"]["ms_per_step"] / (main["ms"] / args.steps)},
-        "et_paper_regime": et_regime,
+        "et_equal_fer": et_regime,
         "learned_weights": learned,
+        "other_configurations": others,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src,
                      "traffic": (traffic_fi * per_launch_fi) if traffic_fi else None,
@@ -443,7 +441,8 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def learned_weights_comparison(ldpc, dev, number, code, frames, max_iter, T=20, train_frames=16, steps=30):
+def learned_weights_comparison(ldpc, dev, number, code, frames, max_iter, T=20, train_frames=16, steps=30,
+                               warm=True):
     """Plain flooding (D_max), PCE+VNR early termination, and early termination
     with learned weights (one per iteration and base block, trained by the
     weighted-BP adjoint on other frames of the same workload: T unrolled
@@ -485,7 +484,8 @@ def learned_weights_comparison(ldpc, dev, number, code, frames, max_iter, T=20, 
                 "aborted": int(((fl & 2) > 0).sum()), "ms": ms}
 
     def timed(fn):
-        fn()
+        if warm:
+            fn()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
@@ -504,34 +504,241 @@ def learned_weights_comparison(ldpc, dev, number, code, frames, max_iter, T=20, 
     return out
 
 
-def et_paper_regime(ldpc, dev, betas=(0.875, 0.8765), frames=64, number=6):
-    """Early termination where the paper measures it: a code inside its BP
-    waterfall (default the (3,6)-regular QC code); FER, mean iterations, time
-    and K of PCE+VNR against the D_max baselines on the same frames, and the
-    decoding-time ratio wherever the FER of PCE+VNR equals that of D_max 500."""
+def csr_index_bytes_per_frame_iter(code) -> int:
+    """A CSR code's index traffic per frame-iteration: the check side reads
+    col_idx (4E) and the variable side the variable-major edge list (4E)."""
+    return 0 if hasattr(code, "shifts") else 8 * int(code.edges)
+
+
+def l2_copy_gbs(dev, mbytes=32, reps=200):
+    """Measured on-chip (L2-resident) copy bandwidth: a mbytes buffer copied
+    into another (both fit the 129 MB L2) reps times; read + write bytes over
+    CUDA-event time, best of 5."""
+    import torch
+    a = torch.ones(mbytes * 2**20 // 4, dtype=torch.float32, device=dev)
+    b = torch.empty_like(a)
+    for _ in range(10):
+        b.copy_(a)
+    best = 0.0
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            b.copy_(a)
+        e1.record()
+        e1.synchronize()
+        best = max(best, 2 * a.numel() * 4 * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9)
+    return best
+
+
+def l2_resident(ldpc, dev, steps=10):
+    """The oracle-sized workload (n = 4096 random CSR code, 64 frames, D_max
+    200): one frame's state is ~80 KB and all 64 frames plus the code's
+    indices (~100 KB) stay in L2, so throughput is reported against the
+    measured L2 copy bandwidth, with algorithmic bytes 8E + 12n plus the CSR
+    index bytes 8E per frame-iteration (algorithmic_bytes_per_frame_iter)."""
+    import torch
+    wl = gen.WORKLOADS[1]
+    code = gen.workload_code(1)
+    fr = gen.workload_frames(1, code)
+    g = ldpc.Graph.from_code(code)
+    llr, syn = torch.from_numpy(fr.llr).to(dev), torch.from_numpy(fr.syndrome).to(dev)
+    B = algorithmic_bytes_per_frame_iter(code)
+    l2 = l2_copy_gbs(dev)
+    out = {"workload": wl["name"], "frames": int(fr.llr.shape[0]), "n": code.n, "edges": int(code.edges),
+           "max_iter": wl["max_iter"], "bytes_per_frame_iter": B, "l2_copy_gbs_measured": l2, "rules": {}}
+    for rule in ("pce_vnr", "pce", "none"):
+        for _ in range(3):
+            ldpc.decode(g, llr, syn, wl["max_iter"], rule)
+        kms, tms, fi = [], [], 0
+        for _ in range(steps):
+            st = ldpc.ldpc_decode_stats()
+            bits, flags, iters = ldpc.decode(g, llr, syn, wl["max_iter"], rule, stats=st)
+            kms.append(st.kernel_ms)
+            tms.append(st.total_ms)
+            fi = st.frame_iterations
+        k = statistics.median(kms) * 1e-3
+        t = statistics.median(tms) * 1e-3
+        ok = ((flags.cpu().numpy() & 1) > 0) & (bits.cpu().numpy() == fr.x).all(1)
+        gbs = fi * B / k / 1e9
+        out["rules"][rule] = {"decoded_mbit_s": code.n * fr.llr.shape[0] / t / 1e6, "kernel_ms": k * 1e3,
+                              "total_ms": t * 1e3, "d_mean": fi / fr.llr.shape[0], "fer": float(1 - ok.mean()),
+                              "achieved_gbs": gbs, "frac_of_l2_copy": gbs / l2,
+                              "frac_of_hbm_peak": gbs / hbm_peak()[0]}
+    g.close()
+    return out
+
+
+def stream_measure(ldpc, dev):
+    """The streaming workload (512 frames of the n = 10^6 code at beta = 0.95,
+    D_max 1000), all frames in one call: PCE+VNR early termination with its
+    roofline fraction, PCE-ET alone and fixed-iteration decoding on the same
+    frames, and the learned-weight decoder next to both."""
+    import torch
+    number = 5
+    wl = gen.WORKLOADS[number]
+    code = gen.workload_code(number)
+    fr = gen.workload_frames(number, code)
+    F = fr.llr.shape[0]
+    g = ldpc.Graph.from_code(code)
+    llr, syn = torch.from_numpy(fr.llr).to(dev), torch.from_numpy(fr.syndrome).to(dev)
+    B = algorithmic_bytes_per_frame_iter(code)
+    ldpc.decode(g, llr, syn, 5, "pce")  # sizes the workspace for 512 slots
+    out = {"workload": wl["name"], "frames": F, "n": code.n, "beta": wl["beta"], "max_iter": wl["max_iter"]}
+    for rule in ("pce_vnr", "pce", "none"):
+        st = ldpc.ldpc_decode_stats()
+        bits, flags, iters = ldpc.decode(g, llr, syn, wl["max_iter"], rule, stats=st)
+        ok = ((flags.cpu().numpy() & 1) > 0) & (bits.cpu().numpy() == fr.x).all(1)
+        out[rule] = {"decoded_mbit_s": code.n * F / (st.total_ms * 1e-3) / 1e6, "ms": st.total_ms,
+                     "d_mean": st.frame_iterations / F, "fer": float(1 - ok.mean()),
+                     "hbm_frac": st.frame_iterations * B / (st.kernel_ms * 1e-3) / 1e9 / hbm_peak()[0]}
+    out["et_speedup"] = {"vs_pce": out["pce"]["ms"] / out["pce_vnr"]["ms"],
+                         "vs_none": out["none"]["ms"] / out["pce_vnr"]["ms"]}
+    del llr, syn
+    g.close()
+    out["learned_weights"] = learned_weights_comparison(ldpc, dev, number, code, fr, wl["max_iter"], warm=False)
+    torch.cuda.empty_cache()
+    return out
+
+
+def compact(line, keys):
+    """The named keys of a workload's bench line (a sub-object of the headline line)."""
+    return {k: line[k] for k in keys if k in line}
+
+
+def other_configurations(args, ctx):
+    """Short runs of the other configurations for the headline line: the
+    L2-resident oracle-sized workload, the 256-frame mixed batch (autotuned,
+    CUDA graph), one weighted-BP training step, and the 512-frame stream."""
+    import torch
+    ldpc, dev = ctx[0], ctx[1]
+    res = {"l2_resident_n4096": l2_resident(ldpc, dev)}
+    torch.cuda.empty_cache()
+    sub = argparse.Namespace(**{**vars(args), "steps": 3, "warmup": 3, "frames": None, "groups": 0, "slots": 0,
+                                "max_iter": None, "lean": False, "compare_steps": 1, "no_cpu_baseline": True})
+    sub.workload = 3
+    b = run_batch(sub, ctx, compact=True)
+    res["batch_mixed_256"] = compact(b, ("metric", "value", "unit", "ms_per_step", "d_mean", "fer", "et_speedup",
+                                         "fixed_iteration", "per_code", "roofline", "gpu_launches"))
+    res["batch_mixed_256"]["schedule"] = b["config"]["schedule"]
+    torch.cuda.empty_cache()
+    sub.workload = 4
+    sub.steps = 10
+    w = run_wbp(sub, ctx, compact=True)
+    res["wbp_training_step"] = compact(w, ("metric", "value", "unit", "ms_per_step", "loss_first_step",
+                                           "loss_after_steps", "forward_only", "roofline", "gpu_launches"))
+    torch.cuda.empty_cache()
+    res["stream_512"] = stream_measure(ldpc, dev)
+    return res
+
+
+ET_DMAX = (100, 150, 200, 250, 300, 400, 500, 1000)
+
+
+def wilson_interval(k: int, n: int, z: float = 1.959964):
+    """95 % Wilson score interval of a proportion k/n."""
+    if n == 0:
+        return (0.0, 1.0)
+    p = k / n
+    den = 1.0 + z * z / n
+    mid = (p + z * z / (2 * n)) / den
+    half = z * math.sqrt(p * (1 - p) / n + z * z / (4 * n * n)) / den
+    return (max(0.0, mid - half), min(1.0, mid + half))
+
+
+def pce_decoded_at(ok, iters):
+    """Iteration at which PCE-ET decoded each frame correctly (success with
+    x^ = x), or a value above any D_max for a frame it did not."""
+    return np.where(np.asarray(ok, dtype=bool), np.asarray(iters, dtype=np.int64), np.iinfo(np.int64).max)
+
+
+def fer_at(k_ok, dmax: int) -> float:
+    """FER of PCE-ET at D_max = dmax on the same frames: a frame that PCE-ET
+    decodes at iteration k follows the same trajectory, and stops with the
+    same bits, for every D_max >= k."""
+    return 1.0 - float((np.asarray(k_ok) <= dmax).mean())
+
+
+def matched_dmax(k_ok, fer_target: float, dmax_max: int) -> int:
+    """Smallest D_max (1 .. dmax_max) at which PCE-ET's FER is not above
+    fer_target (equal FER, up to a quarter frame of rounding)."""
+    F = np.asarray(k_ok).size
+    for D in range(1, dmax_max + 1):
+        if fer_at(k_ok, D) <= fer_target + 0.25 / F:
+            return D
+    return dmax_max
+
+
+def et_equal_fer(ldpc, dev, number, betas, frames=512, vnr_dmax=1000):
+    """Early termination against the D_max baselines at equal FER (paper,
+    section "Simulations" and Fig. 2 left), on the same frames at each beta:
+
+    * PCE-ET at every D_max in ET_DMAX and PCE+VNR-ET at vnr_dmax: FER with
+      its 95 % Wilson interval, mean iterations, CUDA-event time, decoded and
+      goodput Mbit/s, and K = N R (1 - FER) / D (Eq. 2);
+    * the matched baseline: under PCE-ET a frame decoded at iteration k is
+      decoded for every D_max >= k, so the D_max = 1000 run gives FER(D) for
+      every D exactly; D* is the smallest D_max with FER(D*) <= FER(VNR), and
+      PCE-ET at D_max = D* is decoded and timed as well.  Its time over the
+      time of PCE+VNR is the speed-up at equal FER;
+    * FER(500) against FER(1000) (the paper finds the two curves identical)."""
     import torch
     code = gen.workload_code(number)
     graph = ldpc.Graph.from_code(code)
-    out = {"workload": gen.WORKLOADS[number]["name"], "frames": frames, "points": []}
-    for beta in betas:
-        fr = gen.workload_frames(number, code, frames=frames, beta=beta)
+    wl = gen.WORKLOADS[number]
+    t0 = time.perf_counter()
+    frs = gen.workload_frames_betas(number, code, betas, frames=frames)
+    gen_s = time.perf_counter() - t0
+    out = {"workload": wl["name"], "n": code.n, "rate": code.rate, "frames": frames, "vnr_d_max": vnr_dmax,
+           "frame_generation_s": gen_s, "points": []}
+    for beta, fr in zip(betas, frs):
         llr = torch.from_numpy(fr.llr).to(dev)
         syn = torch.from_numpy(fr.syndrome).to(dev)
-        pt = {"beta": beta}
-        for rule, dmax in (("pce", 250), ("pce", 500), ("pce_vnr", 500)):
+        x_dev = torch.from_numpy(fr.x).to(dev)
+        bits = torch.empty((frames, code.n), dtype=torch.uint8, device=dev)
+        flg = torch.empty(frames, dtype=torch.uint8, device=dev)
+        its = torch.empty(frames, dtype=torch.int32, device=dev)
+
+        def run(rule, dmax):
             st = ldpc.ldpc_decode_stats()
-            bits, flags, iters = ldpc.decode(graph, llr, syn, dmax, rule, stats=st)
-            ok = ((flags.cpu().numpy() & 1) > 0) & (bits.cpu().numpy() == fr.x).all(1)
-            fer = float(1 - ok.mean())
-            d = float(iters.float().mean().item())
-            pt[f"{rule}_{dmax}"] = {"fer": fer, "d_mean": d, "ms": st.total_ms,
-                                    "K": code.n * code.rate * (1 - fer) / d}
-        kv = pt["pce_vnr_500"]["K"]
-        pt["K_vnr_over_pce500"] = kv / pt["pce_500"]["K"] if pt["pce_500"]["K"] > 0 else None
-        pt["K_vnr_over_pce250"] = kv / pt["pce_250"]["K"] if pt["pce_250"]["K"] > 0 else None
-        if pt["pce_vnr_500"]["fer"] == pt["pce_500"]["fer"]:
-            pt["speedup_at_equal_fer_vs_pce500"] = pt["pce_500"]["ms"] / pt["pce_vnr_500"]["ms"]
+            ldpc.decode(graph, llr, syn, dmax, rule, out=(bits, flg, its), stats=st)
+            ok = (((flg & 1) > 0) & (bits == x_dev).all(1)).cpu().numpy()
+            it = its.cpu().numpy()
+            k_ok = int(ok.sum())
+            fer = 1.0 - k_ok / frames
+            d = float(it.mean())
+            t = st.total_ms * 1e-3
+            return {"fer": fer, "fer_ci95": wilson_interval(frames - k_ok, frames), "d_mean": d,
+                    "aborted": int(((flg.cpu().numpy() & 2) > 0).sum()), "ms": st.total_ms,
+                    "decoded_mbit_s": code.n * frames / t / 1e6,
+                    "goodput_mbit_s": k_ok * code.n * code.rate / t / 1e6,
+                    "K": code.n * code.rate * (1.0 - fer) / d}, ok, it
+
+        ldpc.decode(graph, llr, syn, 20, "pce", out=(bits, flg, its))  # workspace for these frames
+        pce, k_ok = {}, None
+        for dmax in ET_DMAX:
+            r, ok, it = run("pce", dmax)
+            pce[str(dmax)] = r
+            if dmax == max(ET_DMAX):
+                k_ok = pce_decoded_at(ok, it)
+        vnr, _, _ = run("pce_vnr", vnr_dmax)
+        # the curve must reproduce every measured D_max run (same frames, same trajectories)
+        curve_ok = all(abs(fer_at(k_ok, int(d)) - r["fer"]) < 0.5 / frames for d, r in pce.items())
+        d_star = matched_dmax(k_ok, vnr["fer"], max(ET_DMAX))
+        star, _, _ = run("pce", d_star)
+        pt = {"beta": beta, "pce": pce, "pce_vnr": vnr,
+              "equal_fer": {"d_max": d_star, **star, "speedup_vs_pce_vnr": star["ms"] / vnr["ms"],
+                            "goodput_ratio_vnr_over_pce": (vnr["goodput_mbit_s"] / star["goodput_mbit_s"]
+                                                           if star["goodput_mbit_s"] > 0 else None)},
+              "fer_curve_matches_runs": curve_ok,
+              "fer_500_vs_1000": {"fer_500": pce["500"]["fer"], "fer_1000": pce["1000"]["fer"],
+                                  "frames_decoded_after_500": int(round((pce["500"]["fer"] - pce["1000"]["fer"])
+                                                                        * frames))},
+              "K_ratio_vnr_over_pce": {d: (vnr["K"] / r["K"] if r["K"] > 0 else None) for d, r in pce.items()},
+              "time_ratio_pce_over_vnr": {d: r["ms"] / vnr["ms"] for d, r in pce.items()}}
         out["points"].append(pt)
+        del llr, syn, bits, flg, its
+        torch.cuda.empty_cache()
     graph.close()
     return out
 
@@ -552,9 +759,9 @@ def run_sweep(args):
     code = gen.workload_code(number)
     graph = ldpc.Graph.from_code(code)
     F = args.frames or wl["frames"]
-    runs = [("pce", 100), ("pce", 250), ("pce", 500), ("pce_vnr", 500)]
-    for beta in [float(b) for b in args.betas.split(",")]:
-        frames = gen.workload_frames(number, code, frames=F, beta=beta)
+    runs = [("pce", 100), ("pce", 250), ("pce", 500), ("pce", 1000), ("pce_vnr", 1000)]
+    betas = [float(b) for b in args.betas.split(",")]
+    for beta, frames in zip(betas, gen.workload_frames_betas(number, code, betas, frames=F)):
         llr = torch.from_numpy(frames.llr).to(dev)
         syn = torch.from_numpy(frames.syndrome).to(dev)
         row = {"experiment": "beta_sweep", "workload": wl["name"], "n": code.n, "rate": code.rate, "frames": F,
@@ -573,13 +780,14 @@ def run_sweep(args):
             fer = float(1.0 - ok.mean())
             dmean = float(iters.mean())
             row["runs"][f"{rule}_{dmax}"] = {
-                "fer": fer, "d_mean": dmean, "aborted": int(((flags & 2) > 0).sum()),
+                "fer": fer, "fer_ci95": wilson_interval(int(F - ok.sum()), F), "d_mean": dmean,
+                "aborted": int(((flags & 2) > 0).sum()),
                 "ms": t * 1e3, "decoded_mbit_s": code.n * F / t / 1e6,
                 "goodput_mbit_s": float(ok.sum()) * code.n * code.rate / t / 1e6,
                 "K_bits_per_iteration": code.n * code.rate * (1.0 - fer) / dmean}
-        kv = row["runs"]["pce_vnr_500"]["K_bits_per_iteration"]
+        kv = row["runs"]["pce_vnr_1000"]["K_bits_per_iteration"]
         row["K_ratio_vnr_over"] = {k: (kv / v["K_bits_per_iteration"] if v["K_bits_per_iteration"] > 0 else None)
-                                   for k, v in row["runs"].items() if k != "pce_vnr_500"}
+                                   for k, v in row["runs"].items() if k != "pce_vnr_1000"}
         print(json.dumps(row), flush=True)
 
 
@@ -653,10 +861,9 @@ def run_batch_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_batch(args):
-    """One step = one replay of a CUDA graph holding a whole batch decode
-    (control init, syndrome packing, the persistent decoder, status word) of
-    the workload's frames, inputs resident in HBM; schedule from the autotuner."""
+def gpu_context():
+    """(ldpc binding, device, dist or None, world, rank, local rank) of this
+    process: one rank per GPU under torchrun, NCCL only for timing."""
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -670,6 +877,17 @@ def run_batch(args):
     from paper_2507_03509_gb300 import build
     build.build()
     from paper_2507_03509_gb300 import ldpc
+    return ldpc, dev, dist, world, rank, local
+
+
+def run_batch(args, ctx=None, compact=False):
+    """One step = one replay of a CUDA graph holding a whole batch decode
+    (control init, syndrome packing, the persistent decoder, status word) of
+    the workload's frames, inputs resident in HBM; schedule from the autotuner.
+    compact: no host-buffer (e2e) or CPU legs and only the PCE-ET baseline;
+    the line is returned (a sub-object of the headline line), not printed."""
+    import torch
+    ldpc, dev, dist, world, rank, local = ctx or gpu_context()
 
     wl = gen.WORKLOADS[args.workload]
     max_iter = args.max_iter or wl["max_iter"]
@@ -752,7 +970,7 @@ def run_batch(args):
 
     # fixed-iteration baselines (synchronous decodes of the same batch)
     comp = {}
-    for rule in (() if args.lean else ("pce", "none")):
+    for rule in (() if args.lean else (("pce",) if compact else ("pce", "none"))):
         batch.decode(llr, syn, max_iter, rule, out=out, **opt)
         t = []
         for _ in range(args.compare_steps):
@@ -769,7 +987,7 @@ def run_batch(args):
 
     # end to end: pinned host buffers copied in, graph replayed, results copied out, every step
     e2e = None
-    if not args.lean:
+    if not args.lean and not compact:
         h_llr = torch.from_numpy(bf.llr).pin_memory()
         h_syn = torch.from_numpy(bf.syndrome).pin_memory()
         h_out = [torch.empty(t.shape, dtype=t.dtype).pin_memory() for t in out]
@@ -791,7 +1009,7 @@ def run_batch(args):
                "d2h_bytes_per_step": int(sum(t.numel() * t.element_size() for t in out))}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.lean:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.lean and not compact:
         mbps, cores, sample = batch_oracle_rate(codes, bf, [int(i) for i in iters], args.cpu_seconds,
                                                 "D of this run")
         cpu = {"value": mbps, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
@@ -811,8 +1029,7 @@ def run_batch(args):
                    "cuda_graph": "init + pack + persistent decoder + status kernels, replayed once per step"},
         "d_mean": float(iters.mean()), "fer": float(1 - ok.mean()), "per_code": per_code,
         "fixed_iteration": comp,
-        "et_speedup": None if not comp else {"vs_pce": comp["pce"]["ms_per_step"] / (ms_total / args.steps),
-                                             "vs_none": comp["none"]["ms_per_step"] / (ms_total / args.steps)},
+        "et_speedup": None if not comp else {r: comp[r]["ms_per_step"] / (ms_total / args.steps) for r in comp},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": peak_src, "traffic": None, "algorithmic_bytes_per_launch": bytes_per_step,
                      "kernel": "bp_decode_kernel<float,QcDev>",
@@ -822,8 +1039,12 @@ def run_batch(args):
         "gpu_launches": 4 * args.steps,
         "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
     batch.close()
+    for g in graphs:
+        g.close()
+    if compact:
+        return line
+    print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 
@@ -896,24 +1117,13 @@ def run_wbp_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_wbp(args):
+def run_wbp(args, ctx=None, compact=False):
     """One step = one replay of a CUDA graph holding a whole training step of
     the weighted decoder on the workload's frames (inputs resident in HBM):
     forward over T iterations with checkpoints, BCE loss, adjoint with
-    recomputation, SGD update of the weights."""
+    recomputation, SGD update of the weights.  compact: as in run_batch."""
     import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    from paper_2507_03509_gb300 import build
-    build.build()
-    from paper_2507_03509_gb300 import ldpc
+    ldpc, dev, dist, world, rank, local = ctx or gpu_context()
 
     wl, code, nblk, cls_blk = wbp_setup(args.workload)
     F = args.frames or wl["frames"]
@@ -988,7 +1198,7 @@ def run_wbp(args):
 
     # context: the same step keeping every iteration (no recomputation; T x 117 MB more memory)
     keep_all = None
-    if not args.lean:
+    if not args.lean and not compact:
         plan1 = ldpc.WeightedBP(graph, F, T, cls_blk, nblk, checkpoint_every=1)
         w1 = torch.ones_like(w)
         gw1 = torch.empty_like(w)
@@ -1023,7 +1233,7 @@ def run_wbp(args):
     # end to end: inputs copied in from pinned host memory, the step replayed,
     # loss and weights read back, every step
     e2e = None
-    if not args.lean:
+    if not args.lean and not compact:
         h_llr = torch.from_numpy(fr.llr).pin_memory()
         h_syn = torch.from_numpy(fr.syndrome).pin_memory()
         h_x = torch.from_numpy(fr.x).pin_memory()
@@ -1048,7 +1258,7 @@ def run_wbp(args):
                "d2h_bytes_per_step": int(4 + w.numel() * 4)}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.lean:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.lean and not compact:
         cls_csr = cls_blk[gen.qc_csr_edge_blocks(code)]
         v, cores, sample = wbp_oracle_rate(code, cls_csr, nblk, fr, T, args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
@@ -1078,8 +1288,11 @@ def run_wbp(args):
         "gpu_launches": n_launch * args.steps,
         "clocks": clk,
     }
-    print(json.dumps(line), flush=True)
     plan.close()
+    graph.close()
+    if compact:
+        return line
+    print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
 

@@ -251,22 +251,58 @@ def syndrome(code, x: np.ndarray) -> np.ndarray:
     return out[0] if squeeze else out
 
 
+def _draw_frame(n: int, seed: int, sigmas, x_out, llr_outs, f: int) -> None:
+    """Frame f from its own generator: x ~ U{0,1}^n, z ~ N(0,1)^n, and for
+    each sigma Lch = 2y/sigma^2 with y = (1-2x) + sigma z, rounded once to
+    float32."""
+    rng = np.random.Generator(np.random.PCG64(int(seed)))
+    xf = rng.integers(0, 2, size=n, dtype=np.uint8)
+    z = rng.standard_normal(n)
+    x_out[f] = xf
+    bpsk = 1.0 - 2.0 * xf.astype(np.float64)
+    for sigma, llr in zip(sigmas, llr_outs):
+        y = bpsk + sigma * z
+        llr[f] = (2.0 * y / (sigma ** 2)).astype(np.float32)
+
+
+def _frame_threads(frames: int, n: int) -> int:
+    """Host threads for drawing frames (numpy's generators release the GIL);
+    one thread for small jobs."""
+    import os
+    if frames * n < 4_000_000:
+        return 1
+    return max(1, min(16, os.cpu_count() or 1, frames))
+
+
+def make_frames_sigmas(code, sigma_sets, seeds) -> list[Frames]:
+    """make_frames for several noise levels at once: frame f uses the same
+    generator (seed) and hence the same x and z at every level, so the frames
+    of level i equal make_frames(code, sigma_sets[i], seeds).  Frames are
+    drawn by a thread pool; each has its own generator, so the result does not
+    depend on the threads."""
+    sets = [np.asarray(sg, dtype=np.float64) for sg in sigma_sets]
+    F = len(seeds)
+    n = code.n
+    x = np.empty((F, n), dtype=np.uint8)
+    llrs = [np.empty((F, n), dtype=np.float32) for _ in sets]
+    work = lambda f: _draw_frame(n, seeds[f], [sg[f] for sg in sets], x, llrs, f)
+    threads = _frame_threads(F, n)
+    if threads == 1:
+        for f in range(F):
+            work(f)
+    else:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(work, range(F)))
+    s = syndrome(code, x)
+    return [Frames(x, llr, s, sg) for llr, sg in zip(llrs, sets)]
+
+
 def make_frames(code, sigmas, seeds) -> Frames:
     """One frame per (sigma, seed): x ~ U{0,1}^n, y = (1-2x) + sigma z,
     Lch = 2y/sigma^2 rounded once to float32, s = H x."""
     sigmas = np.asarray(sigmas, dtype=np.float64)
-    F = sigmas.size
-    n = code.n
-    x = np.empty((F, n), dtype=np.uint8)
-    llr = np.empty((F, n), dtype=np.float32)
-    for f in range(F):
-        rng = np.random.Generator(np.random.PCG64(int(seeds[f])))
-        xf = rng.integers(0, 2, size=n, dtype=np.uint8)
-        z = rng.standard_normal(n)
-        y = (1.0 - 2.0 * xf.astype(np.float64)) + sigmas[f] * z
-        x[f] = xf
-        llr[f] = (2.0 * y / (sigmas[f] ** 2)).astype(np.float32)
-    return Frames(x, llr, syndrome(code, x), sigmas)
+    return make_frames_sigmas(code, [sigmas], [int(sd) for sd in seeds][:sigmas.size])[0]
 
 
 # --------------------------------------------------------------------------
@@ -460,11 +496,20 @@ def workload_batch(number: int, codes, frames: int | None = None, first: int = 0
     x = np.empty(var_off[-1], dtype=np.uint8)
     llr = np.empty(var_off[-1], dtype=np.float32)
     syn = np.empty(syn_off[-1], dtype=np.uint8)
-    for i in range(F):
+    def one(i):
         fr = make_frames(codes[fc[i]], [sigma[i]], [2000 * number + first + i])
         x[var_off[i]:var_off[i + 1]] = fr.x[0]
         llr[var_off[i]:var_off[i + 1]] = fr.llr[0]
         syn[syn_off[i]:syn_off[i + 1]] = fr.syndrome[0]
+
+    threads = _frame_threads(F, int(var_off[-1]) // max(1, F))
+    if threads == 1:
+        for i in range(F):
+            one(i)
+    else:  # each frame has its own generator, so the threads do not change the result
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(threads) as ex:
+            list(ex.map(one, range(F)))
     return BatchFrames(fc, beta, sigma, var_off, syn_off, x, llr, syn)
 
 
@@ -472,14 +517,21 @@ def workload_frames(number: int, code, frames: int | None = None, first: int = 0
                     beta: float | None = None) -> Frames:
     """Frames first..first+frames-1 of a named workload at efficiency beta."""
     w = WORKLOADS[number]
+    return workload_frames_betas(number, code, [w["beta"] if beta is None else beta], frames, first)[0]
+
+
+def workload_frames_betas(number: int, code, betas, frames: int | None = None, first: int = 0) -> list[Frames]:
+    """workload_frames at several efficiencies: the same frames (bits, noise
+    draws, syndromes), each at its own sigma; element i equals
+    workload_frames(number, code, frames, first, betas[i])."""
+    w = WORKLOADS[number]
     F = w["frames"] if frames is None else frames
-    b = w["beta"] if beta is None else beta
     rate = w["rate"]
-    sigma = sigma_for_capacity(rate / b)
     seeds = [2000 * number + f for f in range(first, first + F)]
-    fr = make_frames(code, np.full(F, sigma), seeds)
+    sets = [np.full(F, sigma_for_capacity(rate / b)) for b in betas]
+    out = make_frames_sigmas(code, sets, seeds)
     if w.get("punctured_cols"):
         Z = code.Z
         punct = np.concatenate([np.arange(j * Z, (j + 1) * Z) for j in w["punctured_cols"]])
-        fr = rate_adapt(fr, punct, [])
-    return fr
+        out = [rate_adapt(fr, punct, []) for fr in out]
+    return out
