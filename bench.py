@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--slots", type=int, default=0, help="max_active_frames (0 = automatic)")
     ap.add_argument("--grid", type=int, default=0, help="grid_ctas (0 = all that fit)")
     ap.add_argument("--groups", type=int, default=0, help="independent CTA groups (0 = automatic)")
+    ap.add_argument("--schedule", default="auto", choices=["auto", "lockstep", "dataflow"],
+                    help="persistent kernel schedule (auto: lock-step)")
+    ap.add_argument("--flow-lag", type=int, default=0, help="dataflow schedule lag (0 = default)")
     ap.add_argument("--compare-steps", type=int, default=2, help="timed steps of each fixed-iteration rule")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
@@ -89,7 +92,16 @@ def algorithmic_bytes_per_frame_iter(code) -> int:
     return 8 * int(code.edges) + 12 * int(code.n) + csr_index_bytes_per_frame_iter(code)
 
 
-DECODER_SOURCES = ("bp_kernels.cuh", "cn_math.cuh", "device_types.h", "host_common.h", "ldpc_api.cu")
+def decoder_kernel_name(code, schedule="auto") -> str:
+    """The persistent kernel a decode of this code runs (FP32)."""
+    qc = hasattr(code, "shifts")
+    if qc and schedule == "dataflow":
+        return "bp_flow_kernel<float>"
+    return "bp_decode_kernel<float,%s>" % ("QcDev" if qc else "CsrDev")
+
+
+DECODER_SOURCES = ("bp_kernels.cuh", "flow_kernel.cuh", "cn_math.cuh", "device_types.h", "host_common.h",
+                   "ldpc_api.cu")
 
 
 def kernel_source_hash() -> str:
@@ -298,7 +310,8 @@ def run_ours(args):
 
     def one(rule, stats):
         return ldpc.decode(graph, llr, syn, wl["max_iter"], rule, out=out, stats=stats,
-                           max_active_frames=args.slots, grid_ctas=args.grid, groups=args.groups)
+                           max_active_frames=args.slots, grid_ctas=args.grid, groups=args.groups,
+                           schedule=args.schedule, flow_lag=args.flow_lag)
 
     def timed(rule, steps, warmup):
         for _ in range(warmup):
@@ -368,13 +381,15 @@ def run_ours(args):
     for _ in range(1 if e2e_steps else 0):
         ldpc.decode_host(graph, h_llr.numpy(), h_syn.numpy(), wl["max_iter"], "pce_vnr",
                          out=(h_bits.numpy(), h_flags.numpy(), h_iters.numpy()), stream=stream.cuda_stream,
-                         max_active_frames=args.slots, grid_ctas=args.grid, groups=args.groups)
+                         max_active_frames=args.slots, grid_ctas=args.grid, groups=args.groups,
+                         schedule=args.schedule, flow_lag=args.flow_lag)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
         ldpc.decode_host(graph, h_llr.numpy(), h_syn.numpy(), wl["max_iter"], "pce_vnr",
                          out=(h_bits.numpy(), h_flags.numpy(), h_iters.numpy()), stream=stream.cuda_stream,
-                         max_active_frames=args.slots, grid_ctas=args.grid, groups=args.groups)
+                         max_active_frames=args.slots, grid_ctas=args.grid, groups=args.groups,
+                         schedule=args.schedule, flow_lag=args.flow_lag)
     e2e_s = time.perf_counter() - t0
     e2e = None if not e2e_steps else {"value": code.n * F * e2e_steps / e2e_s / 1e6, "unit": UNIT,
            "h2d_bytes_per_step": int(frames.llr.nbytes + frames.syndrome.nbytes),
@@ -429,7 +444,7 @@ def run_ours(args):
                      "frac": achieved / peak, "peak_source": peak_src,
                      "traffic": (traffic_fi * per_launch_fi) if traffic_fi else None,
                      "algorithmic_bytes_per_launch": per_launch_fi * B,
-                     "kernel": "bp_decode_kernel<float,QcDev>",
+                     "kernel": decoder_kernel_name(code, args.schedule),
                      "kernel_ms_per_launch": main["kernel_ms"] / main["steps"]},
         "cpu_baseline": cpu,
         "e2e": e2e,

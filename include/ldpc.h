@@ -115,7 +115,29 @@ typedef struct ldpc_decode_opts {
                                   advances its own frames in lock-step between its own
                                   barriers, and frames that stop are replaced from one shared
                                   queue.  Results are bit-identical for any value.             */
+    int32_t schedule;          /* LDPC_SCHEDULE_*: how the persistent kernel orders its work.
+                                  0 = automatic (lock-step).  Results are bit-identical for
+                                  every schedule.                                             */
+    int32_t flow_lag;          /* dataflow schedule only: how many slot-steps after a frame's
+                                  check pass its variable pass is scheduled (0 = 2; at most the
+                                  number of frames in flight).                                */
 } ldpc_decode_opts;
+
+/* Values of ldpc_decode_opts.schedule.  On GB300 at n = 10^6 with 32 frames the
+ * dataflow schedule measured half the lock-step rate (its items wait on each
+ * frame's decision, a join over all of the frame's check items, every
+ * iteration), so automatic selection takes lock-step. */
+#define LDPC_SCHEDULE_AUTO 0
+/* Lock-step: CTA groups advance their frames between grid-wide barriers
+ * (check pass of every frame in flight, barrier, decisions, variable pass,
+ * barrier).  Any code, FP32 or FP64. */
+#define LDPC_SCHEDULE_LOCKSTEP 1
+/* Dataflow (QC codes only): no grid barriers.  Every CTA takes a fixed share
+ * of one endless list of work items -- the variable pass of one frame and the
+ * check pass of another, slot by slot -- and starts an item as soon as the
+ * items of the previous pass that it reads are done (per-item completion
+ * words), so one frame's new check messages are read back while still in L2. */
+#define LDPC_SCHEDULE_DATAFLOW 2
 
 /* Fill *opts with the defaults (vnr_first_iter 2, clamp 25, FP32, automatic
  * concurrency and grid, no trace, no stats).  NULL is ignored. */

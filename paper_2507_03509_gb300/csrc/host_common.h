@@ -24,6 +24,10 @@ struct Workspace {
     // staging for ldpc_decode_host
     void* stage = nullptr;
     size_t stage_cap = 0;
+    // dependency lists of the dataflow schedule, for the codes and item sizes in deps_key
+    void* deps = nullptr;
+    std::vector<long long> deps_key;
+    std::vector<size_t> deps_off;  // per code: cn_ptr, cn_dep, vn_ptr, vn_dep (int offsets into deps)
 };
 
 }  // namespace ldpcgb
@@ -41,6 +45,8 @@ struct ldpc_graph {
     ldpcgb::CsrDev csr{};
     int vn_tiles = 0, cn_tiles = 0;
     std::vector<int> row_deg, col_deg;  // QC base-matrix row and column weights
+    // host copies of the QC tables (as QcDev holds them on the device)
+    std::vector<int> h_row_ptr, h_blk_col, h_blk_shift, h_col_ptr, h_col_blk, h_blk_row;
     ldpcgb::Workspace ws;
 };
 

@@ -12,10 +12,12 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/ldpc.h"
 #include "bp_kernels.cuh"
+#include "flow_kernel.cuh"
 #include "host_common.h"
 
 using namespace ldpcgb;
@@ -57,6 +59,7 @@ void free_workspace(Workspace& ws) {
     if (ws.host_err) cudaFreeHost(ws.host_err);
     if (ws.host_iters) cudaFreeHost(ws.host_iters);
     if (ws.stage) cudaFree(ws.stage);
+    if (ws.deps) cudaFree(ws.deps);
     for (auto& e : ws.ev)
         if (e) cudaEventDestroy(e);
     ws = Workspace{};
@@ -165,6 +168,356 @@ void pick_chunks(const ldpc_graph* g, int gsize, int slots_per_group, int* cn_ch
     pick(g->col_deg, vn_cand, 4, vn_chunk, vn_tiles);
 }
 
+// Largest sizes over a job's codes: slots are sized for the largest code.
+struct SlotSizes {
+    long long E;
+    int n, nqb, cn_max, vn_max;
+};
+
+// Per-code sizes of a job (item sizes from the model for a group of gsize CTAs
+// and slots_per_group slots, unless the job fixes them) and the pack table.
+template <class Code>
+void code_set(const Job& job, int gsize, int slots_per_group, CodeSet<Code>& cs, SlotSizes& sz, PackInfo& pi) {
+    cs.count = job.ngraphs;
+    long long slot_E = 0;
+    int slot_n = 0, slot_nqb = 0, cn_max = 0, vn_max = 0;
+    for (int c = 0; c < job.ngraphs; ++c) {
+        const ldpc_graph* g = job.graphs[c];
+        CodeInfo<Code>& ci = cs.c[c];
+        ci.code = code_of(g, (Code*)nullptr);
+        ci.n = g->n;
+        ci.m = g->m;
+        ci.E = g->E;
+        ci.swords = (g->m + 31) / 32;
+        ci.cn_tiles = g->cn_tiles;
+        ci.vn_tiles = g->vn_tiles;
+        ci.cn_chunk = kQcCnChunk;
+        ci.vn_chunk = kQcVnChunk;
+        ci.nqb = g->vn_tiles;
+        ci.vec4 = 0;
+        if (g->kind == 1) {
+            pick_chunks(g, gsize, slots_per_group, &ci.cn_chunk, &ci.cn_tiles, &ci.vn_chunk, &ci.vn_tiles);
+            if (job.cn_chunk[c] > 0) {  // measured by the batch autotuner
+                ci.cn_chunk = job.cn_chunk[c];
+                ci.cn_tiles = g->mb * ((g->Z + ci.cn_chunk - 1) / ci.cn_chunk);
+            }
+            if (job.vn_chunk[c] > 0) {
+                ci.vn_chunk = job.vn_chunk[c];
+                ci.vn_tiles = g->nb * ((g->Z + ci.vn_chunk - 1) / ci.vn_chunk);
+            }
+            ci.nqb = g->nb * ((g->Z + kQBlock - 1) / kQBlock);
+            // 16-byte variable-side loads: Z % 4 == 0 and every frame's Lch and
+            // decisions 16-byte aligned (the buffer aligned, every frame of the
+            // code at an offset that is a multiple of 4)
+            ci.vec4 = ((g->Z % 4) == 0 && ((uintptr_t)job.llr % 16) == 0 && !job.var_unaligned[c]) ? 1 : 0;
+        }
+        // slot strides rounded up to 64 elements, so every slot's messages and
+        // APP values start 256-byte aligned whatever the codes' sizes
+        slot_E = std::max(slot_E, (long long)align_up((size_t)ci.E, 64));
+        slot_n = std::max(slot_n, (int)align_up((size_t)ci.n, 64));
+        slot_nqb = std::max(slot_nqb, ci.nqb);
+        cn_max = std::max(cn_max, ci.cn_tiles);
+        vn_max = std::max(vn_max, ci.vn_tiles);
+        pi.m[c] = ci.m;
+        pi.swords[c] = ci.swords;
+    }
+    pi.frame_code = job.frame_code;
+    pi.syn_off = job.syn_off;
+    pi.sb_off = job.sb_off;
+    sz.E = slot_E;
+    sz.n = slot_n;
+    sz.nqb = slot_nqb;
+    sz.cn_max = cn_max;
+    sz.vn_max = vn_max;
+}
+
+// The end of every decode launch.  Asynchronous (status_out set): the device
+// status word is written by a kernel, nothing waits.  Synchronous: the error
+// word and the iteration total are read back, stats filled from the events
+// ev[0] (start), ev[1]/ev[2] (around the persistent kernel) and ev[3] (end).
+ldpc_status finish_decode(Workspace& ws, const ldpc_decode_opts& o, cudaStream_t stream, int32_t* status_out,
+                          int grid, int slots) {
+    const bool timing = o.stats != nullptr && status_out == nullptr;
+    if (status_out) {
+        status_kernel<<<1, 1, 0, stream>>>(ws.ctrl, status_out);
+        LDPC_TRY(cudaGetLastError());
+        return LDPC_OK;
+    }
+    LDPC_TRY(cudaMemcpyAsync(ws.host_err, &ws.ctrl->err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    LDPC_TRY(cudaMemcpyAsync(ws.host_iters, &ws.ctrl->frame_iters, sizeof(unsigned long long),
+                             cudaMemcpyDeviceToHost, stream));
+    if (timing) LDPC_TRY(cudaEventRecord(ws.ev[3], stream));
+    LDPC_TRY(cudaStreamSynchronize(stream));
+    const int err = *ws.host_err;
+    if (timing) {
+        ldpc_decode_stats* sst = o.stats;
+        cudaEventElapsedTime(&sst->kernel_ms, ws.ev[1], ws.ev[2]);
+        cudaEventElapsedTime(&sst->total_ms, ws.ev[0], ws.ev[3]);
+        sst->kernel_launches = 3;
+        sst->grid_ctas = grid;
+        sst->threads_per_cta = kThreads;
+        sst->active_frames = slots;
+        sst->frame_iterations = (int64_t)*ws.host_iters;
+    }
+    if (err == kErrSyndrome) return LDPC_ERR_INVALID_ARG;
+    if (err == kErrTimeout) return LDPC_ERR_TIMEOUT;
+    if (err != kErrNone) return LDPC_ERR_CUDA;
+    return LDPC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Dataflow schedule (flow_kernel.cuh): dependency lists and launcher.
+// ---------------------------------------------------------------------------
+
+// Items of the other pass that each item of a QC code waits for.  A check item
+// (row i, checks [t0, t1)) reads APP at (t + shift_b) mod Z of each block b's
+// column: the variable items of those columns covering that (wrapping) range.
+// A variable item (column j, variables [u0, u1)) reads the messages of each
+// block b of the column at offsets u, written by the check items of the block's
+// row covering (u - shift_b) mod Z.
+void flow_deps(const ldpc_graph* g, int cn_chunk, int vn_chunk, std::vector<int>& cn_ptr, std::vector<int>& cn_dep,
+               std::vector<int>& vn_ptr, std::vector<int>& vn_dep) {
+    const int Z = g->Z, mb = g->mb, nb = g->nb;
+    const int per_row = (Z + cn_chunk - 1) / cn_chunk, per_col = (Z + vn_chunk - 1) / vn_chunk;
+    const std::vector<int>&rp = g->h_row_ptr, &bc = g->h_blk_col, &bs = g->h_blk_shift, &cp = g->h_col_ptr,
+                      &cbk = g->h_col_blk, &br = g->h_blk_row;
+    // tiles of `chunk` covering the cyclic range [a, a + len) mod Z, offset by base
+    auto cover = [&](int a, int len, int chunk, int base, std::vector<int>& out) {
+        const int end = a + len;
+        auto add = [&](int lo, int hi) {  // [lo, hi), 0 <= lo < hi <= Z
+            for (int q = lo / chunk; q <= (hi - 1) / chunk; ++q) out.push_back(base + q);
+        };
+        if (end <= Z) {
+            add(a, end);
+        } else {
+            add(a, Z);
+            add(0, end - Z);
+        }
+    };
+    cn_ptr.assign(1, 0);
+    cn_dep.clear();
+    for (int i = 0; i < mb; ++i)
+        for (int q = 0; q < per_row; ++q) {
+            const int t0 = q * cn_chunk, len = std::min(cn_chunk, Z - t0);
+            std::vector<int> d;
+            for (int b = rp[i]; b < rp[i + 1]; ++b) cover((t0 + bs[b]) % Z, len, vn_chunk, bc[b] * per_col, d);
+            std::sort(d.begin(), d.end());
+            d.erase(std::unique(d.begin(), d.end()), d.end());
+            cn_dep.insert(cn_dep.end(), d.begin(), d.end());
+            cn_ptr.push_back((int)cn_dep.size());
+        }
+    vn_ptr.assign(1, 0);
+    vn_dep.clear();
+    for (int j = 0; j < nb; ++j)
+        for (int q = 0; q < per_col; ++q) {
+            const int u0 = q * vn_chunk, len = std::min(vn_chunk, Z - u0);
+            std::vector<int> d;
+            for (int x = cp[j]; x < cp[j + 1]; ++x) {
+                const int b = cbk[x];
+                cover(((u0 - bs[b]) % Z + Z) % Z, len, cn_chunk, br[b] * per_row, d);
+            }
+            std::sort(d.begin(), d.end());
+            d.erase(std::unique(d.begin(), d.end()), d.end());
+            vn_dep.insert(vn_dep.end(), d.begin(), d.end());
+            vn_ptr.push_back((int)vn_dep.size());
+        }
+}
+
+// Device lists of every code of the job for its item sizes, cached in the
+// workspace (rebuilt only when the codes or sizes change; not while capturing).
+ldpc_status flow_upload_deps(Workspace& ws, const Job& job, const CodeSet<QcDev>& cs, bool capturing,
+                             FlowParams& fp) {
+    std::vector<long long> key;
+    for (int c = 0; c < job.ngraphs; ++c) {
+        key.push_back((long long)(intptr_t)job.graphs[c]);
+        key.push_back(cs.c[c].cn_chunk);
+        key.push_back(cs.c[c].vn_chunk);
+    }
+    if (ws.deps_key != key || !ws.deps) {
+        if (capturing) return LDPC_ERR_INVALID_ARG;  // run one decode of this configuration before capturing
+        std::vector<int> all;
+        std::vector<size_t> off;
+        for (int c = 0; c < job.ngraphs; ++c) {
+            std::vector<int> a, b, d, e;
+            flow_deps(job.graphs[c], cs.c[c].cn_chunk, cs.c[c].vn_chunk, a, b, d, e);
+            for (const std::vector<int>* v : {&a, &b, &d, &e}) {
+                off.push_back(all.size());
+                all.insert(all.end(), v->begin(), v->end());
+                all.resize(align_up(all.size(), 64), 0);
+            }
+        }
+        if (ws.deps) cudaFree(ws.deps);
+        ws.deps = nullptr;
+        ws.deps_key.clear();
+        LDPC_TRY(cudaMalloc(&ws.deps, std::max<size_t>(all.size(), 1) * sizeof(int)));
+        LDPC_TRY(cudaMemcpy(ws.deps, all.data(), all.size() * sizeof(int), cudaMemcpyHostToDevice));
+        ws.deps_key = key;
+        ws.deps_off = off;
+    }
+    const int* d = (const int*)ws.deps;
+    for (int c = 0; c < job.ngraphs; ++c) {
+        fp.dep[c].cn_ptr = d + ws.deps_off[4 * c];
+        fp.dep[c].cn_dep = d + ws.deps_off[4 * c + 1];
+        fp.dep[c].vn_ptr = d + ws.deps_off[4 * c + 2];
+        fp.dep[c].vn_dep = d + ws.deps_off[4 * c + 3];
+    }
+    return LDPC_OK;
+}
+
+// One decode with the dataflow schedule (QC codes): one group over the whole
+// grid, every frame in flight up to max_active_frames, the lag from the options.
+template <typename T>
+ldpc_status launch_flow(Workspace& ws, const Job& job, const ldpc_decode_opts& o, cudaStream_t stream,
+                        int32_t* status_out) {
+    const int frames = job.frames;
+    auto kernel = job.wts ? bp_flow_kernel<T, true> : bp_flow_kernel<T, false>;
+    int dev = 0, sms = 0, per_sm = 0, coop = 0;
+    LDPC_TRY(cudaGetDevice(&dev));
+    LDPC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    LDPC_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) return LDPC_ERR_CUDA;
+    LDPC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0));
+    if (per_sm < 1) return LDPC_ERR_CUDA;
+    int grid = std::min(per_sm * sms, kMaxGrid);
+    if (o.grid_ctas > 0) grid = std::min(grid, o.grid_ctas);
+    int slots = o.max_active_frames > 0 ? o.max_active_frames : frames;
+    slots = std::max(1, std::min(std::min(slots, job.max_slot_frames), kMaxSlots));
+    const int lag = std::max(1, std::min(o.flow_lag > 0 ? o.flow_lag : 2, slots));
+
+    CodeSet<QcDev> cs{};
+    SlotSizes sz{};
+    PackInfo pi{};
+    code_set(job, grid, slots, cs, sz, pi);
+
+    cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+    LDPC_TRY(cudaStreamIsCapturing(stream, &capturing));
+    const bool cap = capturing != cudaStreamCaptureStatusNone;
+    FlowParams fp{};
+    ldpc_status st = flow_upload_deps(ws, job, cs, cap, fp);
+    if (st != LDPC_OK) return st;
+
+    const Layout L = make_layout(slots, sizeof(T), sz.E, sz.n, sz.nqb, job.sbits_words);
+    size_t off = L.total;
+    auto carve = [&](size_t bytes) {
+        const size_t at = off;
+        off = align_up(off + bytes, 256);
+        return at;
+    };
+    const size_t o_cnf = carve((size_t)slots * sz.cn_max * sizeof(int));
+    const size_t o_vnf = carve((size_t)slots * sz.vn_max * sizeof(int));
+    const size_t o_cnt = carve(2 * (size_t)slots * sizeof(unsigned));
+    const size_t o_uns = carve(2 * (size_t)slots * sizeof(int));
+    const size_t o_dec = carve((size_t)slots * sizeof(int));
+    const size_t o_rec = carve((size_t)slots * sizeof(unsigned long long));
+    const size_t o_prv = carve((size_t)slots * sizeof(int));
+    const size_t o_qpv = carve((size_t)slots * sizeof(double));
+    const size_t o_ret = carve(sizeof(int));
+    const size_t o_prg = carve(sizeof(unsigned));
+    if (cap && (ws.cap < off || !ws.ctrl)) return LDPC_ERR_INVALID_ARG;  // run one decode of this size first
+    st = ensure_workspace(ws, off);
+    if (st != LDPC_OK) return st;
+    char* base = (char*)ws.buf;
+
+    Params<T> p{};
+    p.frames = frames;
+    p.max_iter = job.max_iter;
+    p.rule = job.rule;
+    p.vnr_first_iter = o.vnr_first_iter;
+    p.lmax = T(o.clamp);
+    p.frame_code = job.frame_code;
+    p.var_off = job.var_off;
+    p.sb_off = job.sb_off;
+    p.llr = job.llr;
+    p.sbits = (const unsigned*)(base + L.sbits);
+    p.bits_out = job.bits_out;
+    p.flags_out = job.flags_out;
+    p.iters_out = job.iters_out;
+    p.slots = slots;
+    p.slot_E = sz.E;
+    p.slot_n = sz.n;
+    p.slot_nqb = sz.nqb;
+    p.cn_tiles_max = sz.cn_max;
+    p.vn_tiles_max = sz.vn_max;
+    p.c2v = (T*)(base + L.c2v);
+    p.app = (T*)(base + L.app);
+    p.qpart = (double*)(base + L.qpart);
+    p.q0part = (double*)(base + L.q0part);
+    p.qval = (double*)(base + L.qval);
+    p.q0val = (double*)(base + L.q0val);
+    p.unsat = (int*)(base + L.unsat);
+    p.ctrl = ws.ctrl;
+    p.trace_iters = o.trace_iters;
+    p.trace_c2v = (T*)o.trace_c2v;
+    p.trace_app = (T*)o.trace_app;
+    p.trace_q = o.trace_q;
+    p.timeout_ns = o.barrier_timeout_ms > 0 ? (unsigned long long)o.barrier_timeout_ms * 1000000ull
+                                            : kBarrierTimeoutNs;
+    p.bar_extra = o.test_unreachable_barrier ? 1u : 0u;
+    p.groups = 1;
+    p.slots_per_group = slots;
+    p.new_frame = (int*)(base + L.new_frame);
+    p.wts = job.wts;
+    p.wcls = job.wcls;
+    p.w_iters = job.w_iters;
+    p.w_classes = job.w_classes;
+
+    fp.lag = lag;
+    fp.cn_items = sz.cn_max;
+    fp.vn_items = sz.vn_max;
+    fp.cn_flag = (int*)(base + o_cnf);
+    fp.vn_flag = (int*)(base + o_vnf);
+    fp.cn_count = (unsigned*)(base + o_cnt);
+    fp.unsat = (int*)(base + o_uns);
+    fp.dec = (int*)(base + o_dec);
+    fp.rec = (unsigned long long*)(base + o_rec);
+    fp.prev = (int*)(base + o_prv);
+    fp.qprev = (double*)(base + o_qpv);
+    fp.retired = (int*)(base + o_ret);
+    fp.progress = (unsigned*)(base + o_prg);
+
+    const bool timing = o.stats != nullptr && status_out == nullptr;
+    if (timing) LDPC_TRY(cudaEventRecord(ws.ev[0], stream));
+    {
+        const long long words = (long long)slots * (sz.cn_max + sz.vn_max);
+        const int blocks = (int)std::max(1LL, std::min(1024LL, (words + 255) / 256));
+        flow_init_kernel<<<blocks, 256, 0, stream>>>(fp, slots, frames, ws.ctrl);
+        LDPC_TRY(cudaGetLastError());
+    }
+    {
+        int max_words = 1;
+        for (int c = 0; c < job.ngraphs; ++c) max_words = std::max(max_words, pi.swords[c]);
+        const dim3 pgrid((unsigned)std::min((max_words + 31) / 32, 4096), (unsigned)std::max(1, std::min(frames, 65535)));
+        pack_syndrome_kernel<<<pgrid, 256, 0, stream>>>(job.syndrome, frames, pi, (unsigned*)(base + L.sbits),
+                                                        ws.ctrl);
+        LDPC_TRY(cudaGetLastError());
+    }
+    if (timing) LDPC_TRY(cudaEventRecord(ws.ev[1], stream));
+    {
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(grid);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = 0;
+        cfg.stream = stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;  // all CTAs resident: the item waits need it
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        LDPC_TRY(cudaLaunchKernelEx(&cfg, kernel, p, cs, fp));
+    }
+    if (timing) LDPC_TRY(cudaEventRecord(ws.ev[2], stream));
+    return finish_decode(ws, o, stream, status_out, grid, slots);
+}
+
+// Schedule of a job: lock-step unless the caller asks for dataflow (QC only).
+// Measured at n = 1e6 with 32 frames, the dataflow schedule ran at half the
+// lock-step rate: its items wait on the per-frame decision, a join over every
+// check item of the frame, once per iteration.
+template <typename T, class Code>
+bool use_flow(const ldpc_decode_opts& o) {
+    return std::is_same<Code, QcDev>::value && o.schedule == LDPC_SCHEDULE_DATAFLOW;
+}
+
 // Synchronous (status_out == NULL): reads the status back and fills stats.
 // Asynchronous: copies the device status word to status_out and returns at
 // once; nothing in it waits for the host, so it can be captured in a graph
@@ -172,6 +525,9 @@ void pick_chunks(const ldpc_graph* g, int gsize, int slots_per_group, int* cn_ch
 template <typename T, class Code>
 ldpc_status launch_decode(Workspace& ws, const Job& job, const ldpc_decode_opts& o, cudaStream_t stream,
                           int32_t* status_out = nullptr) {
+    if constexpr (std::is_same<Code, QcDev>::value) {
+        if (use_flow<T, Code>(o)) return launch_flow<T>(ws, job, o, stream, status_out);
+    }
     const int frames = job.frames;
     // the weighted kernel is a separate instantiation: the unweighted one carries no weight code
     auto kernel = job.wts ? bp_decode_kernel<T, Code, true> : bp_decode_kernel<T, Code, false>;
@@ -201,53 +557,11 @@ ldpc_status launch_decode(Workspace& ws, const Job& job, const ldpc_decode_opts&
 
     // per-code sizes; slots are sized for the largest code
     CodeSet<Code> cs{};
-    cs.count = job.ngraphs;
-    long long slot_E = 0;
-    int slot_n = 0, slot_nqb = 0, cn_max = 0, vn_max = 0;
+    SlotSizes sz{};
     PackInfo pi{};
-    for (int c = 0; c < job.ngraphs; ++c) {
-        const ldpc_graph* g = job.graphs[c];
-        CodeInfo<Code>& ci = cs.c[c];
-        ci.code = code_of(g, (Code*)nullptr);
-        ci.n = g->n;
-        ci.m = g->m;
-        ci.E = g->E;
-        ci.swords = (g->m + 31) / 32;
-        ci.cn_tiles = g->cn_tiles;
-        ci.vn_tiles = g->vn_tiles;
-        ci.cn_chunk = kQcCnChunk;
-        ci.vn_chunk = kQcVnChunk;
-        ci.nqb = g->vn_tiles;
-        ci.vec4 = 0;
-        if (g->kind == 1) {
-            pick_chunks(g, grid / groups, slots_per_group, &ci.cn_chunk, &ci.cn_tiles, &ci.vn_chunk, &ci.vn_tiles);
-            if (job.cn_chunk[c] > 0) {  // measured by the batch autotuner
-                ci.cn_chunk = job.cn_chunk[c];
-                ci.cn_tiles = g->mb * ((g->Z + ci.cn_chunk - 1) / ci.cn_chunk);
-            }
-            if (job.vn_chunk[c] > 0) {
-                ci.vn_chunk = job.vn_chunk[c];
-                ci.vn_tiles = g->nb * ((g->Z + ci.vn_chunk - 1) / ci.vn_chunk);
-            }
-            ci.nqb = g->nb * ((g->Z + kQBlock - 1) / kQBlock);
-            // 16-byte variable-side loads: Z % 4 == 0 and every frame's Lch and
-            // decisions 16-byte aligned (the buffer aligned, every frame of the
-            // code at an offset that is a multiple of 4)
-            ci.vec4 = ((g->Z % 4) == 0 && ((uintptr_t)job.llr % 16) == 0 && !job.var_unaligned[c]) ? 1 : 0;
-        }
-        // slot strides rounded up to 64 elements, so every slot's messages and
-        // APP values start 256-byte aligned whatever the codes' sizes
-        slot_E = std::max(slot_E, (long long)align_up((size_t)ci.E, 64));
-        slot_n = std::max(slot_n, (int)align_up((size_t)ci.n, 64));
-        slot_nqb = std::max(slot_nqb, ci.nqb);
-        cn_max = std::max(cn_max, ci.cn_tiles);
-        vn_max = std::max(vn_max, ci.vn_tiles);
-        pi.m[c] = ci.m;
-        pi.swords[c] = ci.swords;
-    }
-    pi.frame_code = job.frame_code;
-    pi.syn_off = job.syn_off;
-    pi.sb_off = job.sb_off;
+    code_set(job, grid / groups, slots_per_group, cs, sz, pi);
+    const long long slot_E = sz.E;
+    const int slot_n = sz.n, slot_nqb = sz.nqb, cn_max = sz.cn_max, vn_max = sz.vn_max;
 
     const Layout L = make_layout(slots, sizeof(T), slot_E, slot_n, slot_nqb, job.sbits_words);
     cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
@@ -330,31 +644,7 @@ ldpc_status launch_decode(Workspace& ws, const Job& job, const ldpc_decode_opts&
         LDPC_TRY(cudaLaunchKernelEx(&cfg, kernel, p, cs));
     }
     if (timing) LDPC_TRY(cudaEventRecord(ws.ev[2], stream));
-    if (status_out) {
-        status_kernel<<<1, 1, 0, stream>>>(ws.ctrl, status_out);
-        LDPC_TRY(cudaGetLastError());
-        return LDPC_OK;
-    }
-    LDPC_TRY(cudaMemcpyAsync(ws.host_err, &ws.ctrl->err, sizeof(int), cudaMemcpyDeviceToHost, stream));
-    LDPC_TRY(cudaMemcpyAsync(ws.host_iters, &ws.ctrl->frame_iters, sizeof(unsigned long long),
-                             cudaMemcpyDeviceToHost, stream));
-    if (timing) LDPC_TRY(cudaEventRecord(ws.ev[3], stream));
-    LDPC_TRY(cudaStreamSynchronize(stream));
-    const int err = *ws.host_err;
-    if (timing) {
-        ldpc_decode_stats* sst = o.stats;
-        cudaEventElapsedTime(&sst->kernel_ms, ws.ev[1], ws.ev[2]);
-        cudaEventElapsedTime(&sst->total_ms, ws.ev[0], ws.ev[3]);
-        sst->kernel_launches = 3;
-        sst->grid_ctas = grid;
-        sst->threads_per_cta = kThreads;
-        sst->active_frames = slots;
-        sst->frame_iterations = (int64_t)*ws.host_iters;
-    }
-    if (err == kErrSyndrome) return LDPC_ERR_INVALID_ARG;
-    if (err == kErrTimeout) return LDPC_ERR_TIMEOUT;
-    if (err != kErrNone) return LDPC_ERR_CUDA;
-    return LDPC_OK;
+    return finish_decode(ws, o, stream, status_out, grid, slots);
 }
 
 template <typename T, class Code>
@@ -393,6 +683,9 @@ ldpc_status check_decode_args(const ldpc_graph* graph, int32_t frames, const voi
     if (o.fp64 != 0 && o.fp64 != 1) return LDPC_ERR_INVALID_ARG;
     if (o.max_active_frames < 0 || o.max_active_frames > kMaxSlots || o.grid_ctas < 0 || o.trace_iters < 0 ||
         o.barrier_timeout_ms < 0 || o.groups < 0 || o.groups > kMaxGroups)
+        return LDPC_ERR_INVALID_ARG;
+    if (o.schedule < LDPC_SCHEDULE_AUTO || o.schedule > LDPC_SCHEDULE_DATAFLOW || o.flow_lag < 0 ||
+        (o.schedule == LDPC_SCHEDULE_DATAFLOW && graph->kind != 1))
         return LDPC_ERR_INVALID_ARG;
     if ((long long)frames * graph->n > (1LL << 40)) return LDPC_ERR_INVALID_ARG;
     return LDPC_OK;
@@ -528,6 +821,12 @@ ldpc_status ldpc_graph_create_qc(int32_t mb, int32_t nb, int32_t Z, const int32_
         return st;
     }
     g->qc = QcDev{mb, nb, Z, nblk, d[0], d[1], d[2], d[3], d[4], d[5]};
+    g->h_row_ptr = row_ptr;
+    g->h_blk_col = blk_col;
+    g->h_blk_shift = blk_shift;
+    g->h_col_ptr = col_ptr;
+    g->h_col_blk = col_blk;
+    g->h_blk_row = blk_row;
     g->row_deg.resize(mb);
     for (int i = 0; i < mb; ++i) g->row_deg[i] = row_ptr[i + 1] - row_ptr[i];
     g->col_deg.assign(col_cnt.begin(), col_cnt.end());

@@ -60,7 +60,9 @@ class ldpc_decode_opts(ctypes.Structure):
                 ("trace_c2v", ctypes.c_void_p), ("trace_app", ctypes.c_void_p),
                 ("trace_q", ctypes.c_void_p), ("stats", ctypes.POINTER(ldpc_decode_stats)),
                 ("barrier_timeout_ms", ctypes.c_int32), ("test_unreachable_barrier", ctypes.c_int32),
-                ("groups", ctypes.c_int32)]
+                ("groups", ctypes.c_int32), ("schedule", ctypes.c_int32), ("flow_lag", ctypes.c_int32)]
+
+SCHEDULES = {"auto": 0, "lockstep": 1, "dataflow": 2}
 
 
 def _load():
@@ -257,9 +259,11 @@ class Graph:
 
 def make_opts(vnr_first_iter=2, clamp=25.0, fp64=False, max_active_frames=0, grid_ctas=0,
               trace_iters=0, trace_c2v=None, trace_app=None, trace_q=None, stats=None,
-              barrier_timeout_ms=0, test_unreachable_barrier=False, groups=0):
+              barrier_timeout_ms=0, test_unreachable_barrier=False, groups=0, schedule="auto", flow_lag=0):
     o = ldpc_decode_opts_init()
     o.groups = int(groups)
+    o.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
+    o.flow_lag = int(flow_lag)
     o.barrier_timeout_ms = barrier_timeout_ms
     o.test_unreachable_barrier = 1 if test_unreachable_barrier else 0
     o.vnr_first_iter = vnr_first_iter

@@ -42,12 +42,13 @@ def test_library_exports_every_declared_symbol(ldpc):
 
 
 def test_struct_layout_matches_header(ldpc):
-    # opts: 6 x 4-byte fields, 4 pointers, 3 x 4-byte fields (+4 padding); stats: 2 floats, 4 ints, 1 int64
-    assert ctypes.sizeof(ldpc.ldpc_decode_opts) == 24 + 4 * 8 + 12 + 4
+    # opts: 6 x 4-byte fields, 4 pointers, 5 x 4-byte fields (+4 padding); stats: 2 floats, 4 ints, 1 int64
+    assert ctypes.sizeof(ldpc.ldpc_decode_opts) == 24 + 4 * 8 + 20 + 4
     assert ctypes.sizeof(ldpc.ldpc_decode_stats) == 32
     o = ldpc.ldpc_decode_opts_init()
     assert o.vnr_first_iter == 2 and o.clamp == 25.0 and o.fp64 == 0 and o.trace_iters == 0
     assert o.barrier_timeout_ms == 0 and o.test_unreachable_barrier == 0 and o.groups == 0
+    assert o.schedule == 0 and o.flow_lag == 0
 
 
 def test_status_strings(ldpc):
