@@ -1209,7 +1209,10 @@ def run_wbp(args, ctx=None, compact=False):
     Bf = algorithmic_bytes_per_frame_iter(code) * F * T
     fwd_achieved = Bf / (statistics.mean(fwd_ms) * 1e-3) / 1e9
     every = wl["checkpoint"]
-    n_launch = (2 * T + 2) + (1 + 3 * T + 2 * (T - (T + every - 1) // every)) + 1
+    # forward 2T (+1 interleaving Lch and the syndrome), loss 2, backward 1 + 3T + 2 per recomputed
+    # iteration (+1 interleaving), SGD 1; FP32 QC plans interleave four frames per message
+    x4 = 1
+    n_launch = (2 * T + x4 + 2) + (1 + x4 + 3 * T + 2 * (T - (T + every - 1) // every)) + 1
 
     # context: the same step keeping every iteration (no recomputation; T x 117 MB more memory)
     keep_all = None

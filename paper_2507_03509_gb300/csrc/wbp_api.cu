@@ -51,6 +51,15 @@ struct ldpc_wbp {
     double* wpart = nullptr;     // [groups_cn][nblk][tiles_cn]
     const int* cblk_ptr = nullptr;
     const int* cblk = nullptr;
+    // FP32 QC plans: state interleaved by frame quads (wbp_kernels.cuh, Args4);
+    // F4 = ceil(F / 4) quads, the state arrays hold 4 * F4 frames
+    bool x4 = false;
+    int F4 = 0;
+    int fpq_cn = 1, fpq_vn = 1;  // quads per CTA group, check / variable side
+    float* llr4 = nullptr;       // [F4][n][4] interleaved Lch
+    unsigned char* syn4 = nullptr;  // [F4][m] syndrome bits of the quad's frames
+    float* grad4 = nullptr;      // [F4][n][4] accumulated dloss/dLch
+    int grid_pack = 1;
 };
 
 namespace {
@@ -103,7 +112,116 @@ struct Runner {
     T* ck_c2v(int i) const { return (T*)p->ck_c2v[i]; }
     T* ck_app(int i) const { return (T*)p->ck_app[i]; }
 
+    // ---- interleaved (x4) path of FP32 QC plans -------------------------
+    wbp::Args4 base4() const {
+        wbp::Args4 a{};
+        a.F = p->F;
+        a.F4 = p->F4;
+        a.m = p->m;
+        a.n = p->n;
+        a.E = p->E;
+        a.lmax = 25.0f;
+        a.llr4 = (const float4*)p->llr4;
+        a.syn4 = p->syn4;
+        a.cls = p->cls;
+        return a;
+    }
+    ldpc_status pack4(const float* llr, const uint8_t* syn) const {
+        wbp::pack4_kernel<<<p->grid_pack, wbp::kThreads, 0, s>>>(llr, syn, p->F, p->F4, p->n, p->m,
+                                                                 (float4*)p->llr4, p->syn4);
+        LDPC_TRY(cudaGetLastError());
+        return LDPC_OK;
+    }
+    // iteration k forward on the interleaved state; app_rows (the caller's
+    // frame-major buffer) receives APP^(k) instead of app_dst when given
+    ldpc_status fwd4(const float* w, int k, const float* c2v_prev, const float* app_prev, float* c2v_dst,
+                     float* app_dst, float* app_rows) const {
+        if constexpr (kQc) {
+            wbp::Args4 a = base4();
+            a.w = w + (size_t)(k - 1) * p->C;
+            a.c2v_prev = (const float4*)c2v_prev;
+            a.app_prev = (const float4*)app_prev;
+            a.c2v_out = (float4*)c2v_dst;
+            a.app_out = app_rows ? nullptr : (float4*)app_dst;
+            a.app_rows = app_rows;
+            wbp::qc_cn4_kernel<false><<<(unsigned)p->grid_qcn, wbp::kThreads, 0, s>>>(a, code, p->tiles_cn,
+                                                                                       p->fpq_cn, nullptr);
+            LDPC_TRY(cudaGetLastError());
+            wbp::qc_vn4_kernel<wbp::kVnFwd><<<(unsigned)p->grid_qvn, wbp::kThreads, 0, s>>>(a, code, p->fpq_vn);
+            LDPC_TRY(cudaGetLastError());
+        }
+        return LDPC_OK;
+    }
+    ldpc_status forward4(const float* llr, const uint8_t* syn, const float* w, float* app_out, bool save) {
+        ldpc_status st = pack4(llr, syn);
+        if (st != LDPC_OK) return st;
+        const float* cprev = nullptr;
+        const float* aprev = nullptr;
+        for (int k = 1; k <= p->T; ++k) {
+            float* cdst = (float*)p->c2v_work;
+            float* adst = (float*)p->app_work;
+            if (save && k % p->every == 0 && k < p->T) {
+                cdst = (float*)ck_c2v(k / p->every - 1);
+                adst = (float*)ck_app(k / p->every - 1);
+            }
+            st = fwd4(w, k, cprev, aprev, cdst, adst, k == p->T ? app_out : nullptr);
+            if (st != LDPC_OK) return st;
+            cprev = cdst;
+            aprev = adst;
+        }
+        return LDPC_OK;
+    }
+    ldpc_status backward4(const float* llr, const uint8_t* syn, const float* w, const float* grad_app, float* gw,
+                          float* gl) {
+        if constexpr (kQc) {
+            ldpc_status st = pack4(llr, syn);
+            if (st != LDPC_OK) return st;
+            wbp::Args4 a = base4();
+            a.G = (float4*)p->G;
+            a.grad4 = gl ? (float4*)p->grad4 : nullptr;
+            a.grad_app = grad_app;
+            wbp::qc_vn4_kernel<wbp::kVnSeed><<<(unsigned)p->grid_qvn, wbp::kThreads, 0, s>>>(a, code, p->fpq_vn);
+            LDPC_TRY(cudaGetLastError());
+            const int every = p->every;
+            const int nseg_total = (p->T + every - 1) / every;
+            for (int sg = nseg_total - 1; sg >= 0; --sg) {
+                const int k0 = sg * every, k1 = std::min((sg + 1) * every, p->T);
+                const float* c0 = k0 == 0 ? nullptr : (const float*)ck_c2v(sg - 1);
+                const float* a0 = k0 == 0 ? nullptr : (const float*)ck_app(sg - 1);
+                for (int k = k0 + 1; k < k1; ++k) {
+                    const float* cp = k - 1 == k0 ? c0 : (const float*)p->seg_c2v[k - 1 - k0 - 1];
+                    const float* ap = k - 1 == k0 ? a0 : (const float*)p->seg_app[k - 1 - k0 - 1];
+                    st = fwd4(w, k, cp, ap, (float*)p->seg_c2v[k - k0 - 1], (float*)p->seg_app[k - k0 - 1], nullptr);
+                    if (st != LDPC_OK) return st;
+                }
+                for (int k = k1; k > k0; --k) {
+                    a.w = w + (size_t)(k - 1) * p->C;
+                    a.c2v_prev = (const float4*)(k - 1 == k0 ? c0 : (const float*)p->seg_c2v[k - 1 - k0 - 1]);
+                    a.app_prev = (const float4*)(k - 1 == k0 ? a0 : (const float*)p->seg_app[k - 1 - k0 - 1]);
+                    wbp::qc_cn4_kernel<true><<<(unsigned)p->grid_qcn, wbp::kThreads, 0, s>>>(a, code, p->tiles_cn,
+                                                                                             p->fpq_cn, p->wpart);
+                    LDPC_TRY(cudaGetLastError());
+                    wbp::class_reduce_kernel<float><<<p->grid_w, wbp::kThreads, 0, s>>>(
+                        p->wpart, p->groups_cn, p->graph->nblk, p->tiles_cn, p->cblk_ptr, p->cblk, p->C,
+                        gw + (size_t)(k - 1) * p->C);
+                    LDPC_TRY(cudaGetLastError());
+                    wbp::qc_vn4_kernel<wbp::kVnBwd><<<(unsigned)p->grid_qvn, wbp::kThreads, 0, s>>>(a, code,
+                                                                                                    p->fpq_vn);
+                    LDPC_TRY(cudaGetLastError());
+                }
+            }
+            if (gl) {
+                wbp::unpack4_kernel<<<p->grid_pack, wbp::kThreads, 0, s>>>((const float4*)p->grad4, p->F, p->n, gl);
+                LDPC_TRY(cudaGetLastError());
+            }
+        }
+        return LDPC_OK;
+    }
+
     ldpc_status forward(const float* llr, const uint8_t* syn, const T* w, T* app_out, bool save) {
+        if constexpr (kQc && std::is_same_v<T, float>) {
+            if (p->x4) return forward4(llr, syn, w, app_out, save);
+        }
         const T* cprev = nullptr;
         const T* aprev = nullptr;
         for (int k = 1; k <= p->T; ++k) {
@@ -122,6 +240,9 @@ struct Runner {
     }
 
     ldpc_status backward(const float* llr, const uint8_t* syn, const T* w, const T* grad_app, T* gw, T* gl) {
+        if constexpr (kQc && std::is_same_v<T, float>) {
+            if (p->x4) return backward4(llr, syn, w, grad_app, gw, gl);
+        }
         wbp::Args<T> a = base(llr, syn);
         a.G = (T*)p->G;
         a.pbuf = (T*)p->pbuf;
@@ -289,11 +410,31 @@ ldpc_status ldpc_wbp_create(const ldpc_graph* graph, int32_t frames, int32_t ite
         p->cblk = (const int*)(t + tb_cls + 2 * tb_ptr + tb_slot);
     }
     // workspace: work c2v/APP, checkpoints, recompute segment, adjoint state, loss partials
-    const size_t sE = align_up((size_t)frames * (size_t)graph->E * p->elem, 256);
-    const size_t sN = align_up((size_t)frames * (size_t)graph->n * p->elem, 256);
-    p->loss_blocks = grid_for((long long)frames * graph->n, std::max(sms, 1));
     const bool qc = graph->kind == 1;
-    if (qc) {
+    p->x4 = qc && !fp64;
+    p->F4 = (frames + 3) / 4;
+    const long long sframes = p->x4 ? 4LL * p->F4 : frames;  // frames the state arrays hold
+    const size_t sE = align_up((size_t)sframes * (size_t)graph->E * p->elem, 256);
+    const size_t sN = align_up((size_t)sframes * (size_t)graph->n * p->elem, 256);
+    p->loss_blocks = grid_for((long long)frames * graph->n, std::max(sms, 1));
+    if (p->x4) {
+        // check side: quad groups for about four waves of resident CTAs (4 per SM);
+        // variable side: about 2048 (quad, variable) pairs per CTA
+        const long long waves = 4LL * std::max(sms, 1) * 4;
+        p->tiles_cn = (Z + wbp::kQcCnTile - 1) / wbp::kQcCnTile;
+        const long long cn_items = (long long)p->F4 * graph->mb * p->tiles_cn;
+        p->fpq_cn = (int)std::max(1LL, std::min<long long>(p->F4, (cn_items + waves - 1) / waves));
+        p->groups_cn = (p->F4 + p->fpq_cn - 1) / p->fpq_cn;
+        if ((long long)p->groups_cn * graph->mb * p->tiles_cn >= (1LL << 31)) {
+            release(p);
+            delete p;
+            return LDPC_ERR_INVALID_ARG;
+        }
+        p->grid_qcn = std::min<long long>((long long)p->groups_cn * graph->mb * p->tiles_cn, 1LL << 24);
+        p->fpq_vn = std::max(1, std::min(p->F4, 2048 / std::max(Z, 1)));
+        p->grid_qvn = std::min<long long>((long long)((p->F4 + p->fpq_vn - 1) / p->fpq_vn) * graph->nb, 1LL << 24);
+        p->grid_pack = grid_for((long long)p->F4 * (graph->n + graph->m), std::max(sms, 1));
+    } else if (qc) {
         // frame groups sized for about four waves of resident CTAs (4 per SM)
         const long long waves = 4LL * std::max(sms, 1) * 4;
         p->tiles_cn = (Z + wbp::kQcCnTile - 1) / wbp::kQcCnTile;
@@ -307,8 +448,11 @@ ldpc_status ldpc_wbp_create(const ldpc_graph* graph, int32_t frames, int32_t ite
     }
     const size_t sP = qc ? 0 : sE;  // per-edge G * t (CSR plans only)
     const size_t sW = qc ? align_up((size_t)p->groups_cn * graph->nblk * p->tiles_cn * sizeof(double), 256) : 0;
+    // interleaved plans: Lch copy, syndrome bits, accumulated dloss/dLch
+    const size_t s4n = p->x4 ? align_up((size_t)p->F4 * graph->n * 4 * sizeof(float), 256) : 0;
+    const size_t s4m = p->x4 ? align_up((size_t)p->F4 * graph->m, 256) : 0;
     const size_t total = sE + sN + (size_t)p->nckpt * (sE + sN) + (size_t)p->nseg * (sE + sN) + sE + sP + sW +
-                         align_up((size_t)p->loss_blocks * sizeof(double), 256);
+                         align_up((size_t)p->loss_blocks * sizeof(double), 256) + 2 * s4n + s4m;
     if (ce == cudaSuccess) ce = cudaMalloc(&p->buf, total);
     if (ce != cudaSuccess) {
         release(p);
@@ -323,7 +467,12 @@ ldpc_status ldpc_wbp_create(const ldpc_graph* graph, int32_t frames, int32_t ite
     p->G = b; b += sE;
     p->pbuf = sP ? b : nullptr; b += sP;
     p->wpart = sW ? (double*)b : nullptr; b += sW;
-    p->partial = (double*)b;
+    p->partial = (double*)b; b += align_up((size_t)p->loss_blocks * sizeof(double), 256);
+    if (p->x4) {
+        p->llr4 = (float*)b; b += s4n;
+        p->grad4 = (float*)b; b += s4n;
+        p->syn4 = (unsigned char*)b; b += s4m;
+    }
     p->grid_cn = grid_for((long long)frames * graph->m, sms);
     p->grid_vn = grid_for((long long)frames * graph->n, sms);
     p->grid_w = std::min(n_classes, sms * 16);

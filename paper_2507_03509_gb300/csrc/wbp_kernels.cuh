@@ -829,5 +829,403 @@ __global__ void __launch_bounds__(kThreads) class_reduce_kernel(const double* wp
     }
 }
 
+// ---------------------------------------------------------------------------
+// Four-frame interleaved QC kernels (FP32 plans).  A plan's own state -- c2v,
+// APP, their checkpoints, the adjoint state G, an interleaved copy of Lch and
+// the accumulated dloss/dLch -- is stored by frame quads: element (f, e) at
+// ((f / 4) * E + e) * 4 + f % 4.  A thread then moves the four frames of one
+// message with one 16-byte access and one address computation.  The caller's
+// buffers stay frame-major; pack4_kernel / unpack4_kernel convert at the
+// plan's edges (frames past F are zero: they add exact zeros everywhere).
+// Each frame's arithmetic, and every sum's order over blocks and frames, is
+// the one of the frame-major kernels above.
+// ---------------------------------------------------------------------------
+struct Args4 {
+    int F, F4, m, n;
+    long long E;
+    float lmax;
+    const float4* llr4;            // [F4][n] interleaved Lch
+    const unsigned char* syn4;     // [F4][m] bit f of byte (q, c): syndrome of frame 4q + f at check c
+    const float* w;                // [C] weights of this iteration
+    const int* cls;                // class of each base block
+    const float4* c2v_prev;        // [F4][E] c2v^(k-1), NULL in iteration 1
+    const float4* app_prev;        // [F4][n] APP^(k-1), NULL in iteration 1 (then Lch)
+    float4* c2v_out;               // [F4][E]
+    float4* app_out;               // [F4][n] (NULL: only app_rows)
+    float* app_rows;               // [F][n] frame-major APP output of the last iteration, or NULL
+    float4* G;                     // [F4][E]
+    float4* grad4;                 // [F4][n] accumulated dloss/dLch, or NULL
+    const float* grad_app;         // [F][n] frame-major dloss/dAPP (seed pass)
+};
+
+__device__ __forceinline__ float f4get(const float4& v, int f) {
+    return f == 0 ? v.x : (f == 1 ? v.y : (f == 2 ? v.z : v.w));
+}
+__device__ __forceinline__ void f4set(float4& v, int f, float x) {
+    if (f == 0) v.x = x;
+    else if (f == 1) v.y = x;
+    else if (f == 2) v.z = x;
+    else v.w = x;
+}
+
+// Interleave the caller's Lch and syndrome bytes of every frame quad.
+__global__ void __launch_bounds__(kThreads) pack4_kernel(const float* llr, const unsigned char* syn, int F, int F4,
+                                                         int n, int m, float4* llr4, unsigned char* syn4) {
+    const long long tn = (long long)F4 * n, tm = (long long)F4 * m;
+    for (long long id = (long long)blockIdx.x * kThreads + threadIdx.x; id < tn + tm;
+         id += (long long)gridDim.x * kThreads) {
+        if (id < tn) {
+            const int q = (int)(id / n), v = (int)(id - (long long)q * n);
+            float4 x = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+            for (int f = 0; f < 4; ++f)
+                if (4 * q + f < F) f4set(x, f, __ldg(llr + (size_t)(4 * q + f) * n + v));
+            llr4[id] = x;
+        } else {
+            const long long j = id - tn;
+            const int q = (int)(j / m), c = (int)(j - (long long)q * m);
+            unsigned b = 0;
+#pragma unroll
+            for (int f = 0; f < 4; ++f)
+                if (4 * q + f < F && __ldg(syn + (size_t)(4 * q + f) * m + c) != 0) b |= 1u << f;
+            syn4[j] = (unsigned char)b;
+        }
+    }
+}
+
+// Frame-major copy of an interleaved [F4][n] array (frames < F).
+__global__ void __launch_bounds__(kThreads) unpack4_kernel(const float4* src, int F, int n, float* dst) {
+    const long long total = (long long)F * n;
+    for (long long id = (long long)blockIdx.x * kThreads + threadIdx.x; id < total;
+         id += (long long)gridDim.x * kThreads) {
+        const int f = (int)(id / n), v = (int)(id - (long long)f * n);
+        dst[id] = f4get(src[(size_t)(f >> 2) * n + v], f & 3);
+    }
+}
+
+// One check of degree D for the four frames of quad q: the frame-major
+// kernel's per-frame arithmetic (qc_cn_frame), four times.
+template <int D, bool BWD>
+__device__ __forceinline__ void qc_cn4_quad(const Args4& a, int q, const int (&ia)[D], const int (&im)[D],
+                                            const float (&wk)[D], int c_global, float (&acc)[D]) {
+    const size_t qe = (size_t)q * (size_t)a.E, qn = (size_t)q * (size_t)a.n;
+    float4 x[D], cv[D], G[D];
+    if (a.app_prev) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            x[k] = a.app_prev[qn + ia[k]];
+            cv[k] = a.c2v_prev[qe + im[k]];
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            x[k] = __ldg(a.llr4 + qn + ia[k]);
+            cv[k] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+    }
+    if constexpr (BWD) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) G[k] = a.G[qe + im[k]];
+    }
+    const unsigned sb4 = __ldg(a.syn4 + (size_t)q * a.m + c_global);
+    float4 out[D];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const unsigned sb = (sb4 >> f) & 1u;
+        float u[D], av[D], o[D];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            u[k] = f4get(x[k], f) - f4get(cv[k], f);
+            av[k] = clampm(u[k], a.lmax);
+        }
+        cn_core<D>(av, sb, a.lmax, o);
+        if constexpr (!BWD) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) f4set(out[k], f, wk[k] * o[k]);
+        } else {
+            float dt[D], da[D];
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const float Gk = f4get(G[k], f);
+                acc[k] += Gk * o[k];
+                dt[k] = D == 1 ? 0.0f : Gk * wk[k];
+            }
+            const float sg = sb ? -1.0f : 1.0f;
+            if constexpr (D == 1) {
+                da[0] = 0.0f;
+            } else {
+                float rr[D];
+                bool ng[D];
+#pragma unroll
+                for (int k = 0; k < D; ++k) {
+                    rr[k] = __expf(-fabsf(av[k]));
+                    ng[k] = av[k] < 0.0f;
+                }
+#pragma unroll
+                for (int j = 0; j < D; ++j) {
+                    float s = 0.0f;
+#pragma unroll
+                    for (int e = 0; e < D; ++e)
+                        if (e != j) s = fmaf(dt[e], dbox<D>(rr, ng, e, j), s);
+                    da[j] = sg * s;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < D; ++j) f4set(out[j], f, fabsf(u[j]) <= a.lmax ? da[j] : 0.0f);
+        }
+    }
+    float4* dst = BWD ? a.G + qe : a.c2v_out + qe;
+#pragma unroll
+    for (int k = 0; k < D; ++k) dst[im[k]] = out[k];
+}
+
+// Rows of weight > 4: per frame of the quad, scalar loads from the
+// interleaved arrays and the generic check (as check_n), FP64 sums of G * t.
+template <bool BWD>
+__device__ __noinline__ void qc_cn4_quad_n(const Args4 a, const QcDev q, int qd, int i, int t, int b0, int d,
+                                           double* acc) {
+    const int Z = q.Z;
+    const size_t qe = (size_t)qd * (size_t)a.E, qn = (size_t)qd * (size_t)a.n;
+    const float* xs = a.app_prev ? (const float*)a.app_prev : (const float*)a.llr4;
+    const float* cs = (const float*)a.c2v_prev;
+    float* gs = (float*)a.G;
+    float* os = (float*)a.c2v_out;
+    const unsigned sb4 = __ldg(a.syn4 + (size_t)qd * a.m + (size_t)i * Z + t);
+    for (int f = 0; f < 4; ++f) {
+        int slot[kMaxDeg];
+        float u[kMaxDeg], av[kMaxDeg], o[kMaxDeg];
+        for (int k = 0; k < d; ++k) {
+            int p = t + __ldg(q.blk_shift + b0 + k);
+            if (p >= Z) p -= Z;
+            const size_t iv = qn + (size_t)__ldg(q.blk_col + b0 + k) * Z + p;
+            slot[k] = (b0 + k) * Z + p;
+            const float xv = xs[iv * 4 + f];
+            const float cv = a.app_prev ? cs[(qe + slot[k]) * 4 + f] : 0.0f;
+            u[k] = xv - cv;
+            av[k] = clampm(u[k], a.lmax);
+        }
+        const unsigned sb = (sb4 >> f) & 1u;
+        cn_core_n(av, d, sb, a.lmax, o);
+        if constexpr (!BWD) {
+            for (int k = 0; k < d; ++k) os[(qe + slot[k]) * 4 + f] = a.w[__ldg(a.cls + b0 + k)] * o[k];
+        } else {
+            float dt[kMaxDeg];
+            for (int k = 0; k < d; ++k) {
+                const float Gk = gs[(qe + slot[k]) * 4 + f];
+                acc[k] += (double)(Gk * o[k]);
+                dt[k] = Gk * a.w[__ldg(a.cls + b0 + k)];
+            }
+            const float sg = sb ? -1.0f : 1.0f;
+            for (int j = 0; j < d; ++j) {
+                float sum = 0.0f;
+                for (int e = 0; e < d; ++e) {
+                    if (e == j) continue;
+                    float rb = 0.0f;
+                    bool neg = false;
+                    for (int r = 0; r < d; ++r) {
+                        if (r == e || r == j) continue;
+                        rb = rcomb(rb, __expf(-fabsf(av[r])));
+                        neg ^= av[r] < 0.0f;
+                    }
+                    const float rj = __expf(-fabsf(av[j]));
+                    float dv = __fdividef(rj * fmaf(-rb, rb, 1.0f), (rj + rb) * fmaf(rj, rb, 1.0f));
+                    if (neg) dv = -dv;
+                    sum += dt[e] * sg * dv;
+                }
+                o[j] = sum;  // reuse o for da
+            }
+            for (int j = 0; j < d; ++j) gs[(qe + slot[j]) * 4 + f] = fabsf(u[j]) <= a.lmax ? o[j] : 0.0f;
+        }
+    }
+}
+
+// Check tile of base row i for the quads of group g (one check per thread,
+// quads in ascending order), and in the adjoint the tile's sums of G * t per
+// block into wpart[(g * nblk + b) * tiles + tile] (fixed order).
+template <int D, bool BWD>
+__device__ __forceinline__ void qc_cn4_rows(const Args4& a, const QcDev& q, int g, int fpq, int i, int tile, int b0,
+                                            double* wpart, int tiles, double* sm) {
+    const int Z = q.Z;
+    const int t = tile * kQcCnTile + (int)threadIdx.x;
+    int ia[D], im[D];
+    float wk[D], acc[D];
+#pragma unroll
+    for (int k = 0; k < D; ++k) {
+        int p = t + __ldg(q.blk_shift + b0 + k);
+        if (p >= Z) p -= Z;
+        ia[k] = __ldg(q.blk_col + b0 + k) * Z + p;
+        im[k] = (b0 + k) * Z + p;
+        wk[k] = a.w[__ldg(a.cls + b0 + k)];
+        acc[k] = 0.0f;
+    }
+    const int q0 = g * fpq, q_end = min(a.F4, q0 + fpq);
+    if (t < Z)
+        for (int qd = q0; qd < q_end; ++qd) qc_cn4_quad<D, BWD>(a, qd, ia, im, wk, i * Z + t, acc);
+    if constexpr (BWD) {
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const double s = block_sum((double)acc[k], sm);
+            if (threadIdx.x == 0) wpart[((size_t)g * q.nblk + b0 + k) * tiles + tile] = s;
+        }
+    }
+}
+
+template <bool BWD>
+__device__ __noinline__ void qc_cn4_rows_n(const Args4 a, const QcDev q, int g, int fpq, int i, int tile, int b0,
+                                           int d, double* wpart, int tiles, double* sm) {
+    double acc[kMaxDeg];
+    for (int k = 0; k < d; ++k) acc[k] = 0.0;
+    const int t = tile * kQcCnTile + (int)threadIdx.x;
+    const int q_end = min(a.F4, (g + 1) * fpq);
+    if (t < q.Z)
+        for (int qd = g * fpq; qd < q_end; ++qd) qc_cn4_quad_n<BWD>(a, q, qd, i, t, b0, d, acc);
+    if constexpr (BWD) {
+        for (int k = 0; k < d; ++k) {
+            const double s = block_sum(acc[k], sm);
+            if (threadIdx.x == 0) wpart[((size_t)g * q.nblk + b0 + k) * tiles + tile] = s;
+        }
+    }
+}
+
+// Each thread moves four frames per message, so fewer resident warps keep as
+// many bytes in flight as the frame-major kernels at 5-8 CTAs per SM.
+template <bool BWD>
+__global__ void __launch_bounds__(kThreads, BWD ? 3 : 4) qc_cn4_kernel(Args4 a, QcDev q, int tiles, int fpq,
+                                                                      double* wpart) {
+    __shared__ double sm[kThreads / 32];
+    const int groups = (a.F4 + fpq - 1) / fpq;
+    const long long total = (long long)groups * q.mb * tiles;
+    for (long long blk = blockIdx.x; blk < total; blk += gridDim.x) {
+        const int b = (int)blk, rt = b / groups;  // the host keeps total below 2^31
+        const int g = b - rt * groups;
+        const int i = rt / tiles, tile = rt - i * tiles;
+        const int b0 = __ldg(q.row_ptr + i), d = __ldg(q.row_ptr + i + 1) - b0;
+        switch (d) {
+            case 0: break;
+            case 1: qc_cn4_rows<1, BWD>(a, q, g, fpq, i, tile, b0, wpart, tiles, sm); break;
+            case 2: qc_cn4_rows<2, BWD>(a, q, g, fpq, i, tile, b0, wpart, tiles, sm); break;
+            case 3: qc_cn4_rows<3, BWD>(a, q, g, fpq, i, tile, b0, wpart, tiles, sm); break;
+            case 4: qc_cn4_rows<4, BWD>(a, q, g, fpq, i, tile, b0, wpart, tiles, sm); break;
+            default: qc_cn4_rows_n<BWD>(a, q, g, fpq, i, tile, b0, d, wpart, tiles, sm); break;
+        }
+    }
+}
+
+// Variable side, interleaved: the (quad, variable) pairs of base column j for
+// the quads of group g, one pair (four frames, 16-byte accesses) per thread.
+// Modes as qc_vn_one: kVnFwd APP = Lch + sum of c2v (block order; the last
+// iteration also writes the caller's frame-major rows), kVnBwd S = sum G,
+// dloss/dLch += S, G = S - G; kVnSeed G = dloss/dAPP, dloss/dLch = dloss/dAPP.
+template <int MODE, int DV>
+__device__ __forceinline__ void qc_vn4_cols(const Args4& a, const QcDev& q, int g, int fpq, int j, int cb0, int dv) {
+    constexpr bool kFixed = DV > 0;
+    const int Z = q.Z;
+    const int nd = kFixed ? DV : dv;
+    int blk[kFixed ? DV : 1];
+    if constexpr (kFixed) {
+#pragma unroll
+        for (int b = 0; b < DV; ++b) blk[b] = __ldg(q.col_blk + cb0 + b);
+    }
+    auto block_of = [&](int b) { if constexpr (kFixed) return blk[b]; else return __ldg(q.col_blk + cb0 + b); };
+    const int q0 = g * fpq, nq = min(a.F4, q0 + fpq) - q0;
+    const int count = nq * Z;
+    for (int idx = (int)threadIdx.x; idx < count; idx += kThreads) {
+        const int ql = idx / Z, p = idx - ql * Z;
+        const int qd = q0 + ql;
+        const size_t qe = (size_t)qd * (size_t)a.E;
+        const size_t vi = (size_t)qd * (size_t)a.n + (size_t)j * Z + p;
+        if constexpr (MODE == kVnFwd) {
+            float4 sum = __ldg(a.llr4 + vi);
+            if constexpr (kFixed) {
+                float4 m[DV];
+#pragma unroll
+                for (int b = 0; b < DV; ++b) m[b] = a.c2v_out[qe + (size_t)blk[b] * Z + p];
+#pragma unroll
+                for (int b = 0; b < DV; ++b) {
+                    sum.x += m[b].x;
+                    sum.y += m[b].y;
+                    sum.z += m[b].z;
+                    sum.w += m[b].w;
+                }
+            } else {
+                for (int b = 0; b < nd; ++b) {
+                    const float4 m = a.c2v_out[qe + (size_t)block_of(b) * Z + p];
+                    sum.x += m.x;
+                    sum.y += m.y;
+                    sum.z += m.z;
+                    sum.w += m.w;
+                }
+            }
+            if (a.app_out) a.app_out[vi] = sum;
+            if (a.app_rows) {
+                const size_t v = (size_t)j * Z + p;
+#pragma unroll
+                for (int f = 0; f < 4; ++f)
+                    if (4 * qd + f < a.F) a.app_rows[(size_t)(4 * qd + f) * a.n + v] = f4get(sum, f);
+            }
+        } else if constexpr (MODE == kVnBwd) {
+            float4 sum = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            float4 m[kFixed ? DV : 1];
+            if constexpr (kFixed) {
+#pragma unroll
+                for (int b = 0; b < DV; ++b) m[b] = a.G[qe + (size_t)blk[b] * Z + p];
+#pragma unroll
+                for (int b = 0; b < DV; ++b) {
+                    sum.x += m[b].x;
+                    sum.y += m[b].y;
+                    sum.z += m[b].z;
+                    sum.w += m[b].w;
+                }
+            } else {
+                for (int b = 0; b < nd; ++b) {
+                    const float4 mb = a.G[qe + (size_t)block_of(b) * Z + p];
+                    sum.x += mb.x;
+                    sum.y += mb.y;
+                    sum.z += mb.z;
+                    sum.w += mb.w;
+                }
+            }
+            if (a.grad4) {
+                float4 gl = a.grad4[vi];
+                gl.x += sum.x;
+                gl.y += sum.y;
+                gl.z += sum.z;
+                gl.w += sum.w;
+                a.grad4[vi] = gl;
+            }
+            for (int b = 0; b < nd; ++b) {
+                float4* gp = a.G + qe + (size_t)block_of(b) * Z + p;
+                const float4 old = kFixed ? m[kFixed ? b : 0] : *gp;
+                *gp = make_float4(sum.x - old.x, sum.y - old.y, sum.z - old.z, sum.w - old.w);
+            }
+        } else {
+            float4 gv = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            const size_t v = (size_t)j * Z + p;
+#pragma unroll
+            for (int f = 0; f < 4; ++f)
+                if (4 * qd + f < a.F) f4set(gv, f, __ldg(a.grad_app + (size_t)(4 * qd + f) * a.n + v));
+            if (a.grad4) a.grad4[vi] = gv;
+            for (int b = 0; b < nd; ++b) a.G[qe + (size_t)block_of(b) * Z + p] = gv;
+        }
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 6) qc_vn4_kernel(Args4 a, QcDev q, int fpq) {
+    const int groups = (a.F4 + fpq - 1) / fpq;
+    const long long total = (long long)groups * q.nb;
+    for (long long blk = blockIdx.x; blk < total; blk += gridDim.x) {
+        const int g = (int)(blk % groups), j = (int)(blk / groups);
+        const int cb0 = __ldg(q.col_ptr + j), dv = __ldg(q.col_ptr + j + 1) - cb0;
+        switch (dv) {
+            case 1: qc_vn4_cols<MODE, 1>(a, q, g, fpq, j, cb0, 1); break;
+            case 2: qc_vn4_cols<MODE, 2>(a, q, g, fpq, j, cb0, 2); break;
+            case 3: qc_vn4_cols<MODE, 3>(a, q, g, fpq, j, cb0, 3); break;
+            case 4: qc_vn4_cols<MODE, 4>(a, q, g, fpq, j, cb0, 4); break;
+            default: qc_vn4_cols<MODE, 0>(a, q, g, fpq, j, cb0, dv); break;
+        }
+    }
+}
+
 }  // namespace wbp
 }  // namespace ldpcgb
