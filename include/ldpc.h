@@ -50,7 +50,9 @@ typedef enum ldpc_status {
     LDPC_ERR_OOM = 3,           /* device or pinned-host allocation failed */
     LDPC_ERR_CUDA = 4,          /* a CUDA runtime call failed (no device, launch error, ...) */
     LDPC_ERR_TIMEOUT = 5,       /* a grid-wide wait inside the decoder ran out; results invalid */
-    LDPC_ERR_TOO_LARGE = 6      /* the problem does not fit ldpc_decode_qc_noalloc's fixed scratch */
+    LDPC_ERR_TOO_LARGE = 6,     /* the problem does not fit ldpc_decode_qc_noalloc's fixed scratch */
+    LDPC_ERR_BOUNDS = 7         /* debug aids: the index-checking build found an index outside its
+                                   array, or a guard word around the decoder's arrays was overwritten */
 } ldpc_status;
 
 /* Termination rule (paper section "Early Termination"; the baselines of
@@ -121,6 +123,11 @@ typedef struct ldpc_decode_opts {
     int32_t flow_lag;          /* dataflow schedule only: how many slot-steps after a frame's
                                   check pass its variable pass is scheduled (0 = 2; at most the
                                   number of frames in flight).                                */
+    int32_t debug_guards;      /* debug aid: nonzero places a 256-byte guard region before and
+                                  after each of the decoder's workspace arrays and fills it
+                                  before the decode; ldpc_graph_check_guards /
+                                  ldpc_batch_check_guards then tell whether the decode wrote
+                                  outside its arrays.  Default 0 (no guards).                 */
 } ldpc_decode_opts;
 
 /* Values of ldpc_decode_opts.schedule.  On GB300 at n = 10^6 with 32 frames the
@@ -365,6 +372,21 @@ LDPC_API ldpc_status ldpc_wbp_decode(const ldpc_wbp* plan, int32_t frames, const
 /* weights -= lr * grad over [iters][n_classes] (a plain gradient step). */
 LDPC_API ldpc_status ldpc_wbp_sgd_step(ldpc_wbp* plan, void* weights, const void* grad, double lr,
                                        void* cuda_stream);
+
+/* Debug aids.  After a decode (ldpc_decode, ldpc_decode_host, ldpc_wbp_decode
+ * on the graph's workspace; ldpc_batch_* on the batch's) run with
+ * opts->debug_guards set, report whether every guard region around the
+ * workspace's arrays still holds its fill: LDPC_OK, LDPC_ERR_BOUNDS if any
+ * byte changed, LDPC_ERR_INVALID_ARG if the last decode placed no guards.
+ * Waits for the device to finish.
+ *
+ * A library built with -DLDPC_BOUNDS_CHECK (the binding builds and loads one,
+ * libldpc_gb300_checked.so, when the environment sets LDPC_GB300_CHECKED=1)
+ * tests every index its decode kernels compute against the array it indexes;
+ * the first index outside ends the decode with LDPC_ERR_BOUNDS (the access
+ * itself is redirected to element 0, so nothing outside is touched). */
+LDPC_API ldpc_status ldpc_graph_check_guards(const ldpc_graph* graph);
+LDPC_API ldpc_status ldpc_batch_check_guards(const ldpc_batch* batch);
 
 /* Static, human-readable name of a status code. */
 LDPC_API const char* ldpc_status_str(ldpc_status status);

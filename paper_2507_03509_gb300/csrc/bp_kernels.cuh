@@ -35,7 +35,37 @@ constexpr int kCnTile = kThreads * kCPT;
 constexpr int kVnTile = kThreads * kVPT;
 constexpr int kMaxSlots = 1024;
 
-enum : int { kErrNone = 0, kErrTimeout = 1, kErrSyndrome = 2 };
+enum : int { kErrNone = 0, kErrTimeout = 1, kErrSyndrome = 2, kErrBounds = 3 };
+
+// Index checking (a build with -DLDPC_BOUNDS_CHECK): LDPC_IX(ctrl, i, len, site)
+// yields i when 0 <= i < len; otherwise it records the first such index and
+// its site in the control words, sets the error word (the decode returns
+// LDPC_ERR_BOUNDS at its next synchronisation) and yields 0, an index inside
+// every array, so the access stays in bounds.  Other builds: plain i.
+#ifdef LDPC_BOUNDS_CHECK
+static __device__ __noinline__ long long bounds_fail(Ctrl* c, long long i, int site) {
+    if (atomicCAS(&c->err, kErrNone, kErrBounds) == kErrNone) {
+        c->bad_site = site;
+        c->bad_index = i;
+    }
+    return 0;
+}
+#define LDPC_IX(ctrl, i, len, site) \
+    (((unsigned long long)(long long)(i) < (unsigned long long)(long long)(len)) ? (long long)(i) \
+                                                                               : ldpcgb::bounds_fail((ctrl), (i), (site)))
+// LDPC_IXN(ctrl, i, cnt, len, site): the same for the cnt elements i .. i + cnt - 1.
+#define LDPC_IXN(ctrl, i, cnt, len, site) \
+    (((long long)(i) >= 0 && (long long)(i) + (cnt) <= (long long)(len)) ? (long long)(i) \
+                                                                         : ldpcgb::bounds_fail((ctrl), (i), (site)))
+#else
+#define LDPC_IX(ctrl, i, len, site) (i)
+#define LDPC_IXN(ctrl, i, cnt, len, site) (i)
+#endif
+// Sites of the checks (reported with the bad index).
+enum : int {
+    kIxCnLlr = 1, kIxCnApp, kIxCnMsg, kIxCnSyn, kIxVnLlr, kIxVnMsg, kIxVnApp, kIxVnPart, kIxBits,
+    kIxCsrVar, kIxCsrMsg, kIxSlot, kIxFrame, kIxFlowFlag, kIxFlowSlot
+};
 enum : int { kModeFirst = 0, kModeFull = 1, kModeSynd = 2 };
 enum : int { kRuleNone = 0, kRulePce = 1, kRulePceVnr = 2 };
 
@@ -128,7 +158,9 @@ struct FrameCtx {
     int f, n;
     long long E;
     int cn_chunk, vn_chunk, nqb, vec4;
+    int swords;                    // packed syndrome words of the frame
     const float* wrow;             // weights of the iteration the check pass computes (NULL: none)
+    Ctrl* ctrl;                    // control words (error reports of the index-checking build)
 };
 
 // A check message scaled by its learned weight (W: the weighted kernel); the
@@ -141,6 +173,8 @@ __device__ __forceinline__ T weighted(const Params<T>& p, const FrameCtx<T>& fc,
 
 template <typename T, class Code>
 __device__ __forceinline__ FrameCtx<T> frame_ctx(const Params<T>& p, const CodeInfo<Code>& ci, int s, int f) {
+    s = (int)LDPC_IX(p.ctrl, s, p.slots, kIxSlot);
+    f = (int)LDPC_IX(p.ctrl, f, p.frames, kIxFrame);
     FrameCtx<T> c;
     c.c2v = p.c2v + (size_t)s * (size_t)p.slot_E;
     c.app = p.app + (size_t)s * (size_t)p.slot_n;
@@ -158,7 +192,9 @@ __device__ __forceinline__ FrameCtx<T> frame_ctx(const Params<T>& p, const CodeI
     c.vn_chunk = ci.vn_chunk;
     c.nqb = ci.nqb;
     c.vec4 = ci.vec4;
+    c.swords = ci.swords;
     c.wrow = nullptr;
+    c.ctrl = p.ctrl;
     return c;
 }
 
@@ -269,6 +305,7 @@ __device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, c
     // positions): fire-and-forget requests that hold no registers, so many more
     // lines are in flight than the loads below could keep.  APP needs none: each
     // APP value is read by every block of its column and mostly hits in L2.
+#ifndef LDPC_BOUNDS_CHECK  // the index-checking build issues no unchecked prefetches
     if constexpr (MODE != kModeSynd) {
         const int len = t_end - t0;
         for (int off = 32 * (int)threadIdx.x; off < len; off += 32 * kThreads) {
@@ -284,6 +321,7 @@ __device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, c
             }
         }
     }
+#endif
     // checks in flight per thread
     constexpr int NC = 2;
     bool unsat = false;
@@ -302,11 +340,11 @@ __device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, c
                 pp = ok[c] ? pp : 0;  // in-bounds dummy position for the guarded tail
                 pos[c][j] = pp;
                 if constexpr (MODE == kModeFirst) {
-                    a[c][j] = T(__ldg(llr + vo[j] + pp));
+                    a[c][j] = T(__ldg(llr + LDPC_IX(p.ctrl, vo[j] + pp, fc.n, kIxCnLlr)));
                     o[c][j] = T(0);
                 } else {
-                    a[c][j] = app[vo[j] + pp];
-                    o[c][j] = MODE == kModeFull ? c2v[mo[j] + pp] : T(0);
+                    a[c][j] = app[LDPC_IX(p.ctrl, vo[j] + pp, fc.n, kIxCnApp)];
+                    o[c][j] = MODE == kModeFull ? c2v[LDPC_IX(p.ctrl, mo[j] + pp, fc.E, kIxCnMsg)] : T(0);
                 }
             }
         }
@@ -315,7 +353,9 @@ __device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, c
             if (!ok[c]) continue;
             const int t = tb + c * kThreads;
             const int bit = sbit0 + t;
-            const unsigned sbit = (__ldg(sb + (bit >> 5)) >> (bit & 31)) & 1u;
+            const unsigned sbit =
+                (__ldg(sb + LDPC_IX(p.ctrl, (sb - fc.sbits) + (bit >> 5), fc.swords, kIxCnSyn) - (sb - fc.sbits)) >>
+                 (bit & 31)) & 1u;
             if constexpr (SYND) {
                 unsigned pr = sbit;
 #pragma unroll
@@ -328,7 +368,8 @@ __device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, c
                 for (int j = 0; j < D; ++j) v[j] = clampm(a[c][j] - o[c][j], p.lmax);
                 cn_core<D>(v, sbit, p.lmax, out);
 #pragma unroll
-                for (int j = 0; j < D; ++j) c2v[mo[j] + pos[c][j]] = weighted<W>(p, fc, out[j], b0 + j);
+                for (int j = 0; j < D; ++j)
+                    c2v[LDPC_IX(p.ctrl, mo[j] + pos[c][j], fc.E, kIxCnMsg)] = weighted<W>(p, fc, out[j], b0 + j);
             }
         }
     }
@@ -347,19 +388,20 @@ __device__ bool qc_cn_item_n(const Params<T>& p, const QcDev& q, const FrameCtx<
     const unsigned* sb = fc.sbits;
     bool unsat = false;
     for (int t = t0 + (int)threadIdx.x; t < t_end; t += kThreads) {
+        (void)LDPC_IX(p.ctrl, (i * Z + t) >> 5, fc.swords, kIxCnSyn);
         const unsigned sbit = syndrome_bit(sb, i * Z + t);
         T v[kMaxDeg], out[kMaxDeg];
         unsigned pr = sbit;
         for (int j = 0; j < d; ++j) {
             int pp = t + __ldg(q.blk_shift + b0 + j);
             pp = pp >= Z ? pp - Z : pp;
-            const int vi = __ldg(q.blk_col + b0 + j) * Z + pp;
+            const int vi = (int)LDPC_IX(p.ctrl, __ldg(q.blk_col + b0 + j) * Z + pp, fc.n, kIxCnApp);
             T a, o = T(0);
             if (MODE == kModeFirst) {
                 a = T(__ldg(llr + vi));
             } else {
                 a = app[vi];
-                if (MODE == kModeFull) o = c2v[(b0 + j) * Z + pp];
+                if (MODE == kModeFull) o = c2v[LDPC_IX(p.ctrl, (b0 + j) * Z + pp, fc.E, kIxCnMsg)];
             }
             pr ^= (unsigned)(a < T(0));
             v[j] = clampm(a - o, p.lmax);
@@ -370,7 +412,7 @@ __device__ bool qc_cn_item_n(const Params<T>& p, const QcDev& q, const FrameCtx<
             for (int j = 0; j < d; ++j) {
                 int pp = t + __ldg(q.blk_shift + b0 + j);
                 pp = pp >= Z ? pp - Z : pp;
-                c2v[(b0 + j) * Z + pp] = weighted<W>(p, fc, out[j], b0 + j);
+                c2v[LDPC_IX(p.ctrl, (b0 + j) * Z + pp, fc.E, kIxCnMsg)] = weighted<W>(p, fc, out[j], b0 + j);
             }
         }
     }
@@ -428,13 +470,13 @@ __device__ __forceinline__ bool csr_cn_check(const Params<T>& p, const CsrDev& g
     T a[D], o[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
-        const int vi = __ldg(g.col_idx + e0 + j);
+        const int vi = (int)LDPC_IX(p.ctrl, __ldg(g.col_idx + e0 + j), fc.n, kIxCsrVar);
         o[j] = T(0);
         if (mode == kModeFirst) {
             a[j] = T(__ldg(llr + vi));
         } else {
             a[j] = app[vi];
-            if (mode == kModeFull) o[j] = c2v[e0 + j];
+            if (mode == kModeFull) o[j] = c2v[LDPC_IX(p.ctrl, e0 + j, fc.E, kIxCsrMsg)];
         }
     }
     bool unsat = false;
@@ -450,7 +492,7 @@ __device__ __forceinline__ bool csr_cn_check(const Params<T>& p, const CsrDev& g
     for (int j = 0; j < D; ++j) v[j] = clampm(a[j] - o[j], p.lmax);
     cn_core<D>(v, sbit, p.lmax, out);
 #pragma unroll
-    for (int j = 0; j < D; ++j) c2v[e0 + j] = weighted<W>(p, fc, out[j], e0 + j);
+    for (int j = 0; j < D; ++j) c2v[LDPC_IX(p.ctrl, e0 + j, fc.E, kIxCsrMsg)] = weighted<W>(p, fc, out[j], e0 + j);
     return unsat;
 }
 
@@ -465,13 +507,13 @@ __device__ bool csr_cn_check_n(const Params<T>& p, const CsrDev& g, const FrameC
     T v[kMaxDeg], out[kMaxDeg];
     unsigned pr = sbit;
     for (int j = 0; j < d; ++j) {
-        const int vi = __ldg(g.col_idx + e0 + j);
+        const int vi = (int)LDPC_IX(p.ctrl, __ldg(g.col_idx + e0 + j), fc.n, kIxCsrVar);
         T a, o = T(0);
         if (mode == kModeFirst) {
             a = T(__ldg(llr + vi));
         } else {
             a = app[vi];
-            if (mode == kModeFull) o = c2v[e0 + j];
+            if (mode == kModeFull) o = c2v[LDPC_IX(p.ctrl, e0 + j, fc.E, kIxCsrMsg)];
         }
         pr ^= (unsigned)(a < T(0));
         v[j] = clampm(a - o, p.lmax);
@@ -479,7 +521,7 @@ __device__ bool csr_cn_check_n(const Params<T>& p, const CsrDev& g, const FrameC
     const bool unsat = want_synd && pr != 0u;
     if (mode == kModeSynd) return unsat;
     cn_core_n(v, d, sbit, p.lmax, out);
-    for (int j = 0; j < d; ++j) c2v[e0 + j] = weighted<W>(p, fc, out[j], e0 + j);
+    for (int j = 0; j < d; ++j) c2v[LDPC_IX(p.ctrl, e0 + j, fc.E, kIxCsrMsg)] = weighted<W>(p, fc, out[j], e0 + j);
     return unsat;
 }
 
@@ -572,23 +614,29 @@ __device__ __forceinline__ void qc_vn_cols(const Params<T>& p, const QcDev& q, c
     bool vec = false;
     if constexpr (sizeof(T) == 4) vec = fc.vec4 != 0;
     const int qb_per_col = (Z + kQBlock - 1) / kQBlock;
+#ifndef LDPC_BOUNDS_CHECK
     // L2 prefetch of the item's message blocks and channel values (contiguous)
     for (int off = u0 + 32 * (int)threadIdx.x; off < u_end; off += 32 * kThreads) {
         prefetch_l2(llr + off);
         for (int b = 0; b < nd; ++b) prefetch_l2(c2v + __ldg(q.col_blk + cb0 + b) * Z + off);
     }
+#endif
     for (int ub = u0; ub < u_end; ub += kQBlock) {
         const int u = ub + 4 * (int)threadIdx.x;
         T acc = T(0), acc0 = T(0);
         if (u < u_end) {
             T L[4], sum[4];
             if (vec) {
+                (void)LDPC_IXN(p.ctrl, (long long)j * Z + u, 4, fc.n, kIxVnLlr);
                 const float4 l4 = __ldg(reinterpret_cast<const float4*>(llr + u));
                 float4 s4 = l4;
                 if constexpr (kFixed) {
                     float4 m[DV];
 #pragma unroll
-                    for (int b = 0; b < DV; ++b) m[b] = *reinterpret_cast<const float4*>(cb[b] + u);
+                    for (int b = 0; b < DV; ++b) {
+                        (void)LDPC_IXN(p.ctrl, (cb[b] - c2v) + u, 4, fc.E, kIxVnMsg);
+                        m[b] = *reinterpret_cast<const float4*>(cb[b] + u);
+                    }
 #pragma unroll
                     for (int b = 0; b < DV; ++b) {
                         s4.x += m[b].x;
@@ -598,8 +646,9 @@ __device__ __forceinline__ void qc_vn_cols(const Params<T>& p, const QcDev& q, c
                     }
                 } else {
                     for (int b = 0; b < nd; ++b) {
-                        const float4 m =
-                            *reinterpret_cast<const float4*>(c2v + __ldg(q.col_blk + cb0 + b) * Z + u);
+                        const long long mi =
+                            LDPC_IXN(p.ctrl, (long long)__ldg(q.col_blk + cb0 + b) * Z + u, 4, fc.E, kIxVnMsg);
+                        const float4 m = *reinterpret_cast<const float4*>(c2v + mi);
                         s4.x += m.x;
                         s4.y += m.y;
                         s4.z += m.z;
@@ -613,13 +662,17 @@ __device__ __forceinline__ void qc_vn_cols(const Params<T>& p, const QcDev& q, c
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     if (u + e < u_end) {
+                        (void)LDPC_IX(p.ctrl, (long long)j * Z + u + e, fc.n, kIxVnApp);
                         L[e] = T(__ldg(llr + u + e));
                         T t = L[e];
                         if constexpr (kFixed) {
 #pragma unroll
-                            for (int b = 0; b < DV; ++b) t += cb[b][u + e];
+                            for (int b = 0; b < DV; ++b)
+                                t += cb[b][LDPC_IX(p.ctrl, (cb[b] - c2v) + u + e, fc.E, kIxVnMsg) - (cb[b] - c2v)];
                         } else {
-                            for (int b = 0; b < nd; ++b) t += c2v[__ldg(q.col_blk + cb0 + b) * Z + u + e];
+                            for (int b = 0; b < nd; ++b)
+                                t += c2v[LDPC_IX(p.ctrl, (long long)__ldg(q.col_blk + cb0 + b) * Z + u + e, fc.E,
+                                                 kIxVnMsg)];
                         }
                         sum[e] = t;
                         app[u + e] = t;
@@ -640,7 +693,8 @@ __device__ __forceinline__ void qc_vn_cols(const Params<T>& p, const QcDev& q, c
                 }
             }
         }
-        const size_t part = ((size_t)j * qb_per_col + ub / kQBlock) * kWarps;
+        const size_t part = (size_t)LDPC_IXN(p.ctrl, ((long long)j * qb_per_col + ub / kQBlock) * kWarps, kWarps,
+                                             (long long)p.slot_nqb * kWarps, kIxVnPart);
         warp_sum_store(acc, fc.qpart + part);
         if (want_q0) warp_sum_store(acc0, fc.q0part + part);
     }
@@ -676,7 +730,7 @@ __device__ __forceinline__ void vn_tile(const Params<T>& p, const CsrDev& g, con
             const int a0 = __ldg(g.var_ptr + v), a1 = __ldg(g.var_ptr + v + 1);
             const T L = T(__ldg(llr + v));
             T sum = L;
-            for (int a = a0; a < a1; ++a) sum += c2v[__ldg(g.var_edge + a)];
+            for (int a = a0; a < a1; ++a) sum += c2v[LDPC_IX(p.ctrl, __ldg(g.var_edge + a), fc.E, kIxCsrMsg)];
             app[v] = sum;
             if (a1 - a0 > 1) {
                 acc += absm(sum);
@@ -714,7 +768,10 @@ __device__ __forceinline__ void final_tile(const QcDev& q, const FrameCtx<T>& fc
     const int u_end = min(u0 + fc.vn_chunk, q.Z);
     const T* app = fc.app + j * q.Z;
     unsigned char* bits = fc.bits + j * q.Z;
-    for (int u = u0 + (int)threadIdx.x; u < u_end; u += kThreads) bits[u] = (unsigned char)(app[u] < T(0));
+    for (int u = u0 + (int)threadIdx.x; u < u_end; u += kThreads) {
+        (void)LDPC_IX(fc.ctrl, (long long)j * q.Z + u, fc.n, kIxBits);
+        bits[u] = (unsigned char)(app[u] < T(0));
+    }
 }
 template <typename T>
 __device__ __forceinline__ void final_tile(const CsrDev&, const FrameCtx<T>& fc, int tile) {
@@ -998,10 +1055,11 @@ __global__ void init_ctrl_kernel(Ctrl* ctrl, int groups, int next_frame, int* un
     for (int i = threadIdx.x; i < unsat_words; i += blockDim.x) unsat[i] = 0;
 }
 
-// The decode's outcome as an ldpc_status code (0 ok, 1 bad syndrome byte, 5 timeout).
+// The decode's outcome as an ldpc_status code (0 ok, 1 bad syndrome byte, 5 timeout,
+// 7 an index check of the index-checking build failed).
 __global__ void status_kernel(const Ctrl* ctrl, int* out) {
     const int e = ctrl->err;
-    *out = e == kErrNone ? 0 : (e == kErrSyndrome ? 1 : (e == kErrTimeout ? 5 : 4));
+    *out = e == kErrNone ? 0 : (e == kErrSyndrome ? 1 : (e == kErrTimeout ? 5 : (e == kErrBounds ? 7 : 4)));
 }
 
 }  // namespace ldpcgb

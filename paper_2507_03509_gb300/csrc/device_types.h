@@ -13,6 +13,8 @@ struct alignas(128) Ctrl {
     int err;
     int next_frame;                  // frames handed out so far
     unsigned long long frame_iters;  // sum over frames of D
+    int bad_site;                    // index-checking build: where the first bad index was seen
+    long long bad_index;             // ... and its value
 };
 
 // Quasi-cyclic code: nonzero base blocks in row-major order (block id b).

@@ -110,13 +110,18 @@ struct Spin {
 // for every i < n (idx NULL: flag[i] for i < n).  Lanes check disjoint entries
 // with acquire loads; false on error or timeout.
 __device__ __forceinline__ bool warp_wait_flags(const int* flag, const int* idx, int n, int want, int* err,
-                                                unsigned long long timeout_ns) {
+                                                unsigned long long timeout_ns, Ctrl* ctrl = nullptr, int len = 0) {
     const int lane = threadIdx.x & 31;
     Spin sp;
+    (void)ctrl;
+    (void)len;
     for (;;) {
         bool ok = true;
         for (int i = lane; i < n; i += 32) {
-            const int f = idx ? __ldg(idx + i) : i;
+            int f = idx ? __ldg(idx + i) : i;
+#ifdef LDPC_BOUNDS_CHECK
+            if (ctrl) f = (int)LDPC_IX(ctrl, f, len, kIxFlowFlag);
+#endif
             ok &= ld_acquire_s32(flag + f) >= want;
         }
         if (__all_sync(0xffffffffu, ok)) return true;
@@ -299,11 +304,11 @@ __device__ FlowItem flow_next_item(const Params<T>& p, const CodeSet<QcDev>& cs,
             // a new frame: the previous frame's variable items (its write-out) must be done,
             // whatever the two codes' item geometries
             if (m.prev_code >= 0) ok = warp_wait_flags(flags, nullptr, cs.c[m.prev_code].vn_tiles, m.c, err,
-                                                        p.timeout_ns);
+                                                        p.timeout_ns, p.ctrl, fp.vn_items);
         } else {
             const FlowDeps& dp = fp.dep[m.code];
             const int a = __ldg(dp.cn_ptr + m.tile), b = __ldg(dp.cn_ptr + m.tile + 1);
-            ok = warp_wait_flags(flags, dp.cn_dep + a, b - a, m.c, err, p.timeout_ns);
+            ok = warp_wait_flags(flags, dp.cn_dep + a, b - a, m.c, err, p.timeout_ns, p.ctrl, fp.vn_items);
         }
         m.kind = 1;
     } else if (f >= 0 && start <= m.c) {
@@ -314,7 +319,7 @@ __device__ FlowItem flow_next_item(const Params<T>& p, const CodeSet<QcDev>& cs,
         const FlowDeps& dp = fp.dep[m.code];
         const int a = __ldg(dp.vn_ptr + m.tile), b = __ldg(dp.vn_ptr + m.tile + 1);
         ok = warp_wait_flags(fp.cn_flag + (size_t)m.s * fp.cn_items, dp.vn_dep + a, b - a, m.c + 1, err,
-                             p.timeout_ns);
+                             p.timeout_ns, p.ctrl, fp.cn_items);
         m.kind = 2;
     } else if (start == m.c + 1) {
         // the frame stopped at cycle c: write its decision out
@@ -399,7 +404,8 @@ __global__ void __launch_bounds__(kThreads, 4) bp_flow_kernel(Params<T> p, CodeS
                 __syncthreads();
                 if (threadIdx.x == 0) {
                     const int sl = vit->s, cy = vit->c;
-                    st_release_s32(fp.cn_flag + (size_t)sl * fp.cn_items + vit->tile, cy + 1);
+                    st_release_s32(fp.cn_flag + (size_t)sl * fp.cn_items +
+                                       LDPC_IX(p.ctrl, vit->tile, fp.cn_items, kIxFlowFlag), cy + 1);
                     const unsigned old = atom_add_acq_rel(&fp.cn_count[2 * sl + (cy & 1)], 1u);
                     s_dec = old + 1u == (unsigned)cs.c[vit->code].cn_tiles;
                 }
@@ -415,7 +421,8 @@ __global__ void __launch_bounds__(kThreads, 4) bp_flow_kernel(Params<T> p, CodeS
                     final_tile<T>(ci.code, fc, tile);
                 __syncthreads();
                 if (threadIdx.x == 0)
-                    st_release_s32(fp.vn_flag + (size_t)vit->s * fp.vn_items + vit->tile, vit->c + 1);
+                    st_release_s32(fp.vn_flag + (size_t)vit->s * fp.vn_items +
+                                       LDPC_IX(p.ctrl, vit->tile, fp.vn_items, kIxFlowFlag), vit->c + 1);
             }
         }
         // every few items: once no slot has a frame left, find the last pair that

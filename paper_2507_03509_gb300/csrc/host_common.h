@@ -9,6 +9,8 @@
 #include <cstdint>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/ldpc.h"
 #include "device_types.h"
 
@@ -28,6 +30,8 @@ struct Workspace {
     void* deps = nullptr;
     std::vector<long long> deps_key;
     std::vector<size_t> deps_off;  // per code: cn_ptr, cn_dep, vn_ptr, vn_dep (int offsets into deps)
+    // guard regions of the last decode that asked for them (debug_guards), byte offsets into buf
+    std::vector<size_t> guard_off;
 };
 
 }  // namespace ldpcgb
@@ -69,6 +73,15 @@ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // Graph, device class map (validated at plan creation), iterations and
 // classes of a weighted-BP plan, for decoding with its learned weights.
 bool wbp_plan_classes(const ldpc_wbp* plan, const ldpc_graph** graph, const int** cls, int* iters, int* classes);
+
+// An NVTX range around one library call (visible in Nsight Systems / Compute;
+// costs a few nanoseconds when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Restores the caller's current device on scope exit.
 struct DeviceGuard {

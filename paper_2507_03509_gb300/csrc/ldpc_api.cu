@@ -68,22 +68,77 @@ void free_workspace(Workspace& ws) {
 // Device layout of one decode's state.
 struct Layout {
     size_t c2v, app, qpart, q0part, qval, q0val, unsat, sbits, new_frame, total;
+    std::vector<size_t> guards;  // offsets of the guard regions (debug_guards), kGuardBytes each
 };
 
-Layout make_layout(int slots, size_t elem, long long slot_E, int slot_n, int slot_nqb, long long sbits_words) {
+constexpr size_t kGuardBytes = 256;          // guard region before and after every array (debug_guards)
+constexpr unsigned char kGuardByte = 0xA5;   // its fill byte
+
+// Carves consecutive 256-byte aligned regions; with guards, a guard region
+// precedes every region and one follows the last.
+struct Carver {
+    size_t off = 0;
+    bool guard = false;
+    std::vector<size_t>* guards = nullptr;
+    size_t take(size_t bytes) {
+        if (guard) {
+            guards->push_back(off);
+            off += kGuardBytes;
+        }
+        const size_t at = off;
+        off = align_up(off + bytes, 256);
+        return at;
+    }
+    size_t end() {
+        if (guard) {
+            guards->push_back(off);
+            off += kGuardBytes;
+        }
+        return off;
+    }
+};
+
+Layout make_layout(int slots, size_t elem, long long slot_E, int slot_n, int slot_nqb, long long sbits_words,
+                   bool guard) {
     Layout L{};
-    size_t o = 0;
-    L.c2v = o;    o = align_up(o + (size_t)slots * (size_t)slot_E * elem, 256);
-    L.app = o;    o = align_up(o + (size_t)slots * (size_t)slot_n * elem, 256);
-    L.qpart = o;  o = align_up(o + (size_t)slots * slot_nqb * kWarps * sizeof(double), 256);
-    L.q0part = o; o = align_up(o + (size_t)slots * slot_nqb * kWarps * sizeof(double), 256);
-    L.qval = o;   o = align_up(o + (size_t)slots * kQParts * sizeof(double), 256);
-    L.q0val = o;  o = align_up(o + (size_t)slots * kQParts * sizeof(double), 256);
-    L.unsat = o;  o = align_up(o + 2 * (size_t)slots * sizeof(int), 256);
-    L.sbits = o;  o = align_up(o + (size_t)sbits_words * sizeof(unsigned), 256);
-    L.new_frame = o; o = align_up(o + (size_t)slots * sizeof(int), 256);
-    L.total = o;
+    Carver cv;
+    cv.guard = guard;
+    cv.guards = &L.guards;
+    L.c2v = cv.take((size_t)slots * (size_t)slot_E * elem);
+    L.app = cv.take((size_t)slots * (size_t)slot_n * elem);
+    L.qpart = cv.take((size_t)slots * slot_nqb * kWarps * sizeof(double));
+    L.q0part = cv.take((size_t)slots * slot_nqb * kWarps * sizeof(double));
+    L.qval = cv.take((size_t)slots * kQParts * sizeof(double));
+    L.q0val = cv.take((size_t)slots * kQParts * sizeof(double));
+    L.unsat = cv.take(2 * (size_t)slots * sizeof(int));
+    L.sbits = cv.take((size_t)sbits_words * sizeof(unsigned));
+    L.new_frame = cv.take((size_t)slots * sizeof(int));
+    L.total = cv.off;  // the dataflow schedule carves on from here; end() closes the last guard
     return L;
+}
+
+// Fill the guard regions of this launch's layout (debug_guards) and remember
+// them for ldpc_*_check_guards.
+ldpc_status fill_guards(Workspace& ws, const std::vector<size_t>& guards, cudaStream_t stream) {
+    ws.guard_off = guards;
+    for (size_t off : guards)
+        LDPC_TRY(cudaMemsetAsync((char*)ws.buf + off, kGuardByte, kGuardBytes, stream));
+    return LDPC_OK;
+}
+
+// Whether every guard region of the last guarded launch still holds its fill.
+ldpc_status check_guards(Workspace& ws, int device) {
+    if (ws.guard_off.empty() || !ws.buf) return LDPC_ERR_INVALID_ARG;
+    DeviceGuard guard;
+    LDPC_TRY(guard.enter(device));
+    LDPC_TRY(cudaDeviceSynchronize());
+    std::vector<unsigned char> h(kGuardBytes);
+    for (size_t off : ws.guard_off) {
+        LDPC_TRY(cudaMemcpy(h.data(), (char*)ws.buf + off, kGuardBytes, cudaMemcpyDeviceToHost));
+        for (unsigned char b : h)
+            if (b != kGuardByte) return LDPC_ERR_BOUNDS;
+    }
+    return LDPC_OK;
 }
 
 ldpc_status ensure_workspace(Workspace& ws, size_t bytes) {
@@ -261,6 +316,7 @@ ldpc_status finish_decode(Workspace& ws, const ldpc_decode_opts& o, cudaStream_t
     }
     if (err == kErrSyndrome) return LDPC_ERR_INVALID_ARG;
     if (err == kErrTimeout) return LDPC_ERR_TIMEOUT;
+    if (err == kErrBounds) return LDPC_ERR_BOUNDS;
     if (err != kErrNone) return LDPC_ERR_CUDA;
     return LDPC_OK;
 }
@@ -396,27 +452,31 @@ ldpc_status launch_flow(Workspace& ws, const Job& job, const ldpc_decode_opts& o
     ldpc_status st = flow_upload_deps(ws, job, cs, cap, fp);
     if (st != LDPC_OK) return st;
 
-    const Layout L = make_layout(slots, sizeof(T), sz.E, sz.n, sz.nqb, job.sbits_words);
-    size_t off = L.total;
-    auto carve = [&](size_t bytes) {
-        const size_t at = off;
-        off = align_up(off + bytes, 256);
-        return at;
-    };
-    const size_t o_cnf = carve((size_t)slots * sz.cn_max * sizeof(int));
-    const size_t o_vnf = carve((size_t)slots * sz.vn_max * sizeof(int));
-    const size_t o_cnt = carve(2 * (size_t)slots * sizeof(unsigned));
-    const size_t o_uns = carve(2 * (size_t)slots * sizeof(int));
-    const size_t o_dec = carve((size_t)slots * sizeof(int));
-    const size_t o_rec = carve((size_t)slots * sizeof(unsigned long long));
-    const size_t o_prv = carve((size_t)slots * sizeof(int));
-    const size_t o_qpv = carve((size_t)slots * sizeof(double));
-    const size_t o_ret = carve(sizeof(int));
-    const size_t o_prg = carve(sizeof(unsigned));
+    Layout L = make_layout(slots, sizeof(T), sz.E, sz.n, sz.nqb, job.sbits_words, o.debug_guards != 0);
+    Carver cv;
+    cv.off = L.total;
+    cv.guard = o.debug_guards != 0;
+    cv.guards = &L.guards;
+    const size_t o_cnf = cv.take((size_t)slots * sz.cn_max * sizeof(int));
+    const size_t o_vnf = cv.take((size_t)slots * sz.vn_max * sizeof(int));
+    const size_t o_cnt = cv.take(2 * (size_t)slots * sizeof(unsigned));
+    const size_t o_uns = cv.take(2 * (size_t)slots * sizeof(int));
+    const size_t o_dec = cv.take((size_t)slots * sizeof(int));
+    const size_t o_rec = cv.take((size_t)slots * sizeof(unsigned long long));
+    const size_t o_prv = cv.take((size_t)slots * sizeof(int));
+    const size_t o_qpv = cv.take((size_t)slots * sizeof(double));
+    const size_t o_ret = cv.take(sizeof(int));
+    const size_t o_prg = cv.take(sizeof(unsigned));
+    const size_t off = cv.end();
     if (cap && (ws.cap < off || !ws.ctrl)) return LDPC_ERR_INVALID_ARG;  // run one decode of this size first
     st = ensure_workspace(ws, off);
     if (st != LDPC_OK) return st;
     char* base = (char*)ws.buf;
+    ws.guard_off.clear();
+    if (o.debug_guards) {
+        st = fill_guards(ws, L.guards, stream);
+        if (st != LDPC_OK) return st;
+    }
 
     Params<T> p{};
     p.frames = frames;
@@ -563,7 +623,11 @@ ldpc_status launch_decode(Workspace& ws, const Job& job, const ldpc_decode_opts&
     const long long slot_E = sz.E;
     const int slot_n = sz.n, slot_nqb = sz.nqb, cn_max = sz.cn_max, vn_max = sz.vn_max;
 
-    const Layout L = make_layout(slots, sizeof(T), slot_E, slot_n, slot_nqb, job.sbits_words);
+    Layout L = make_layout(slots, sizeof(T), slot_E, slot_n, slot_nqb, job.sbits_words, o.debug_guards != 0);
+    if (o.debug_guards) {
+        L.guards.push_back(L.total);  // the guard after the last array
+        L.total += kGuardBytes;
+    }
     cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
     LDPC_TRY(cudaStreamIsCapturing(stream, &capturing));
     if (capturing != cudaStreamCaptureStatusNone && (ws.cap < L.total || !ws.ctrl))
@@ -571,6 +635,11 @@ ldpc_status launch_decode(Workspace& ws, const Job& job, const ldpc_decode_opts&
     ldpc_status st = ensure_workspace(ws, L.total);
     if (st != LDPC_OK) return st;
     char* base = (char*)ws.buf;
+    ws.guard_off.clear();
+    if (o.debug_guards) {
+        st = fill_guards(ws, L.guards, stream);
+        if (st != LDPC_OK) return st;
+    }
 
     Params<T> p{};
     p.frames = frames;
@@ -684,6 +753,7 @@ ldpc_status check_decode_args(const ldpc_graph* graph, int32_t frames, const voi
     if (o.max_active_frames < 0 || o.max_active_frames > kMaxSlots || o.grid_ctas < 0 || o.trace_iters < 0 ||
         o.barrier_timeout_ms < 0 || o.groups < 0 || o.groups > kMaxGroups)
         return LDPC_ERR_INVALID_ARG;
+    if (o.debug_guards != 0 && o.debug_guards != 1) return LDPC_ERR_INVALID_ARG;
     if (o.schedule < LDPC_SCHEDULE_AUTO || o.schedule > LDPC_SCHEDULE_DATAFLOW || o.flow_lag < 0 ||
         (o.schedule == LDPC_SCHEDULE_DATAFLOW && graph->kind != 1))
         return LDPC_ERR_INVALID_ARG;
@@ -716,6 +786,7 @@ const char* ldpc_status_str(ldpc_status s) {
         case LDPC_ERR_CUDA: return "CUDA error";
         case LDPC_ERR_TIMEOUT: return "grid synchronisation timed out";
         case LDPC_ERR_TOO_LARGE: return "problem too large for the fixed no-allocation scratch";
+        case LDPC_ERR_BOUNDS: return "an index or guard check of the debug aids failed";
     }
     return "unknown status";
 }
@@ -856,6 +927,7 @@ ldpc_status ldpc_graph_info(const ldpc_graph* g, int32_t* m, int32_t* n, int64_t
 ldpc_status ldpc_decode(const ldpc_graph* graph, int32_t frames, const float* llr, const uint8_t* syndrome,
                         int32_t max_iter, ldpc_term_rule rule, uint8_t* bits_out, uint8_t* flags_out,
                         int32_t* iters_out, const ldpc_decode_opts* opts, void* cuda_stream) {
+    NvtxRange nvtx("ldpc_decode");
     return decode_weighted(graph, frames, llr, syndrome, max_iter, rule, bits_out, flags_out, iters_out, opts,
                            cuda_stream, nullptr, nullptr, 0, 0);
 }
@@ -863,6 +935,7 @@ ldpc_status ldpc_decode(const ldpc_graph* graph, int32_t frames, const float* ll
 ldpc_status ldpc_wbp_decode(const ldpc_wbp* plan, int32_t frames, const float* llr, const uint8_t* syndrome,
                             const float* weights, int32_t max_iter, ldpc_term_rule rule, uint8_t* bits_out,
                             uint8_t* flags_out, int32_t* iters_out, const ldpc_decode_opts* opts, void* cuda_stream) {
+    NvtxRange nvtx("ldpc_wbp_decode");
     const ldpc_graph* graph = nullptr;
     const int* cls = nullptr;
     int iters = 0, classes = 0;
@@ -915,6 +988,7 @@ extern "C" {
 ldpc_status ldpc_decode_host(const ldpc_graph* graph, int32_t frames, const float* llr, const uint8_t* syndrome,
                              int32_t max_iter, ldpc_term_rule rule, uint8_t* bits_out, uint8_t* flags_out,
                              int32_t* iters_out, const ldpc_decode_opts* opts, void* cuda_stream) {
+    NvtxRange nvtx("ldpc_decode_host");
     ldpc_decode_opts o;
     ldpc_decode_opts_init(&o);
     if (opts) o = *opts;
@@ -1114,6 +1188,7 @@ ldpc_status ldpc_batch_info(const ldpc_batch* b, int32_t* frames, int64_t* llr_l
 ldpc_status ldpc_batch_decode(ldpc_batch* b, const float* llr, const uint8_t* syndrome, int32_t max_iter,
                               ldpc_term_rule rule, uint8_t* bits_out, uint8_t* flags_out, int32_t* iters_out,
                               const ldpc_decode_opts* opts, void* cuda_stream) {
+    NvtxRange nvtx("ldpc_batch_decode");
     if (!b) return LDPC_ERR_INVALID_ARG;
     const ldpc_decode_opts o = batch_opts(b, opts);
     ldpc_status st = check_batch_args(b, llr, syndrome, max_iter, (int)rule, bits_out, flags_out, iters_out, o);
@@ -1127,6 +1202,7 @@ ldpc_status ldpc_batch_decode(ldpc_batch* b, const float* llr, const uint8_t* sy
 ldpc_status ldpc_batch_decode_async(ldpc_batch* b, const float* llr, const uint8_t* syndrome, int32_t max_iter,
                                     ldpc_term_rule rule, uint8_t* bits_out, uint8_t* flags_out, int32_t* iters_out,
                                     int32_t* status_out, const ldpc_decode_opts* opts, void* cuda_stream) {
+    NvtxRange nvtx("ldpc_batch_decode_async");
     if (!b || !status_out) return LDPC_ERR_INVALID_ARG;
     ldpc_decode_opts o = batch_opts(b, opts);
     o.stats = nullptr;
@@ -1141,6 +1217,7 @@ ldpc_status ldpc_batch_decode_async(ldpc_batch* b, const float* llr, const uint8
 ldpc_status ldpc_batch_autotune(ldpc_batch* b, const float* llr, const uint8_t* syndrome, int32_t max_iter,
                                 ldpc_term_rule rule, uint8_t* bits_out, uint8_t* flags_out, int32_t* iters_out,
                                 void* cuda_stream, int32_t* best_groups, int32_t* best_slots) {
+    NvtxRange nvtx("ldpc_batch_autotune");
     if (!b) return LDPC_ERR_INVALID_ARG;
     ldpc_decode_opts o;
     ldpc_decode_opts_init(&o);
@@ -1216,6 +1293,16 @@ ldpc_status ldpc_batch_autotune(ldpc_batch* b, const float* llr, const uint8_t* 
     if (best_groups) *best_groups = bg;
     if (best_slots) *best_slots = bs;
     return LDPC_OK;
+}
+
+ldpc_status ldpc_graph_check_guards(const ldpc_graph* graph) {
+    if (!graph) return LDPC_ERR_INVALID_ARG;
+    return check_guards(const_cast<ldpc_graph*>(graph)->ws, graph->device);
+}
+
+ldpc_status ldpc_batch_check_guards(const ldpc_batch* batch) {
+    if (!batch) return LDPC_ERR_INVALID_ARG;
+    return check_guards(const_cast<ldpc_batch*>(batch)->ws, batch->device);
 }
 
 }  // extern "C"
@@ -1428,6 +1515,7 @@ extern "C" ldpc_status ldpc_decode_qc_noalloc(int32_t mb, int32_t nb, int32_t Z,
     LDPC_TRY(cudaStreamSynchronize(stream));
     if (err == kErrSyndrome) return LDPC_ERR_INVALID_ARG;
     if (err == kErrTimeout) return LDPC_ERR_TIMEOUT;
+    if (err == kErrBounds) return LDPC_ERR_BOUNDS;
     if (err != kErrNone) return LDPC_ERR_CUDA;
     return LDPC_OK;
 }

@@ -490,6 +490,7 @@ void ldpc_wbp_destroy(ldpc_wbp* p) {
 
 ldpc_status ldpc_wbp_forward(ldpc_wbp* p, const float* llr, const uint8_t* syndrome, const void* weights,
                              void* app_out, int32_t save_for_backward, void* cuda_stream) {
+    NvtxRange nvtx("ldpc_wbp_forward");
     if (!p || !llr || !syndrome || !weights || !app_out) return LDPC_ERR_INVALID_ARG;
     DeviceGuard guard;
     LDPC_TRY(guard.enter(p->device));
@@ -504,6 +505,7 @@ ldpc_status ldpc_wbp_forward(ldpc_wbp* p, const float* llr, const uint8_t* syndr
 
 ldpc_status ldpc_wbp_loss(ldpc_wbp* p, const void* app, const uint8_t* x, void* loss_out, void* grad_app,
                           void* cuda_stream) {
+    NvtxRange nvtx("ldpc_wbp_loss");
     if (!p || !app || !x || !loss_out) return LDPC_ERR_INVALID_ARG;
     DeviceGuard guard;
     LDPC_TRY(guard.enter(p->device));
@@ -527,6 +529,7 @@ ldpc_status ldpc_wbp_loss(ldpc_wbp* p, const void* app, const uint8_t* x, void* 
 
 ldpc_status ldpc_wbp_backward(ldpc_wbp* p, const float* llr, const uint8_t* syndrome, const void* weights,
                               const void* grad_app, void* grad_weights, void* grad_llr, void* cuda_stream) {
+    NvtxRange nvtx("ldpc_wbp_backward");
     if (!p || !llr || !syndrome || !weights || !grad_app || !grad_weights) return LDPC_ERR_INVALID_ARG;
     if (p->nckpt > 0 && !p->saved) return LDPC_ERR_INVALID_ARG;
     DeviceGuard guard;
@@ -538,6 +541,7 @@ ldpc_status ldpc_wbp_backward(ldpc_wbp* p, const float* llr, const uint8_t* synd
 }
 
 ldpc_status ldpc_wbp_sgd_step(ldpc_wbp* p, void* weights, const void* grad, double lr, void* cuda_stream) {
+    NvtxRange nvtx("ldpc_wbp_sgd_step");
     if (!p || !weights || !grad) return LDPC_ERR_INVALID_ARG;
     DeviceGuard guard;
     LDPC_TRY(guard.enter(p->device));

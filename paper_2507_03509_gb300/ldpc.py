@@ -17,7 +17,10 @@ import os
 
 import numpy as np
 
-_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libldpc_gb300.so")
+# LDPC_GB300_CHECKED=1 selects the index-checking build (a debug aid, compiled with -DLDPC_BOUNDS_CHECK)
+_CHECKED = os.environ.get("LDPC_GB300_CHECKED", "0") not in ("", "0")
+_LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                         "libldpc_gb300_checked.so" if _CHECKED else "libldpc_gb300.so")
 
 LDPC_OK = 0
 LDPC_ERR_INVALID_ARG = 1
@@ -26,6 +29,7 @@ LDPC_ERR_OOM = 3
 LDPC_ERR_CUDA = 4
 LDPC_ERR_TIMEOUT = 5
 LDPC_ERR_TOO_LARGE = 6
+LDPC_ERR_BOUNDS = 7
 
 LDPC_TERM_NONE = 0
 LDPC_TERM_PCE = 1
@@ -41,7 +45,7 @@ EXPORTED = ("ldpc_decode_opts_init", "ldpc_graph_create_csr", "ldpc_graph_create
             "ldpc_status_str", "ldpc_decode_qc_noalloc", "ldpc_batch_create", "ldpc_batch_destroy",
             "ldpc_batch_info", "ldpc_batch_decode", "ldpc_batch_decode_async", "ldpc_batch_autotune",
             "ldpc_wbp_create", "ldpc_wbp_destroy", "ldpc_wbp_forward", "ldpc_wbp_loss", "ldpc_wbp_backward",
-            "ldpc_wbp_sgd_step", "ldpc_wbp_decode")
+            "ldpc_wbp_sgd_step", "ldpc_wbp_decode", "ldpc_graph_check_guards", "ldpc_batch_check_guards")
 
 NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 
@@ -60,7 +64,8 @@ class ldpc_decode_opts(ctypes.Structure):
                 ("trace_c2v", ctypes.c_void_p), ("trace_app", ctypes.c_void_p),
                 ("trace_q", ctypes.c_void_p), ("stats", ctypes.POINTER(ldpc_decode_stats)),
                 ("barrier_timeout_ms", ctypes.c_int32), ("test_unreachable_barrier", ctypes.c_int32),
-                ("groups", ctypes.c_int32), ("schedule", ctypes.c_int32), ("flow_lag", ctypes.c_int32)]
+                ("groups", ctypes.c_int32), ("schedule", ctypes.c_int32), ("flow_lag", ctypes.c_int32),
+                ("debug_guards", ctypes.c_int32)]
 
 SCHEDULES = {"auto": 0, "lockstep": 1, "dataflow": 2}
 
@@ -119,10 +124,22 @@ def _load():
     lib.ldpc_wbp_sgd_step.restype = ctypes.c_int
     lib.ldpc_wbp_decode.argtypes = [P, i32, P, P, P, i32, ctypes.c_int, P, P, P, ctypes.POINTER(ldpc_decode_opts), P]
     lib.ldpc_wbp_decode.restype = ctypes.c_int
+    lib.ldpc_graph_check_guards.argtypes = [P]
+    lib.ldpc_graph_check_guards.restype = ctypes.c_int
+    lib.ldpc_batch_check_guards.argtypes = [P]
+    lib.ldpc_batch_check_guards.restype = ctypes.c_int
     return lib
 
 
 _lib = _load()
+
+
+def ldpc_graph_check_guards(handle) -> int:
+    return _lib.ldpc_graph_check_guards(handle)
+
+
+def ldpc_batch_check_guards(handle) -> int:
+    return _lib.ldpc_batch_check_guards(handle)
 
 
 class LdpcError(RuntimeError):
@@ -259,8 +276,10 @@ class Graph:
 
 def make_opts(vnr_first_iter=2, clamp=25.0, fp64=False, max_active_frames=0, grid_ctas=0,
               trace_iters=0, trace_c2v=None, trace_app=None, trace_q=None, stats=None,
-              barrier_timeout_ms=0, test_unreachable_barrier=False, groups=0, schedule="auto", flow_lag=0):
+              barrier_timeout_ms=0, test_unreachable_barrier=False, groups=0, schedule="auto", flow_lag=0,
+              debug_guards=False):
     o = ldpc_decode_opts_init()
+    o.debug_guards = 1 if debug_guards else 0
     o.groups = int(groups)
     o.schedule = SCHEDULES[schedule] if isinstance(schedule, str) else int(schedule)
     o.flow_lag = int(flow_lag)

@@ -56,7 +56,9 @@ def lib():
 
 
 def gpu_decode(ldpc, graph, llr, syn, max_iter, rule, trace_iters=0, fp64=False, **opts):
-    """Decode numpy inputs on cuda:0; returns numpy outputs (+ traces)."""
+    """Decode numpy inputs on cuda:0; returns numpy outputs (+ traces).  The
+    decode places guard words around its workspace arrays (debug_guards) and
+    the guards are checked afterwards, unless debug_guards=False is passed."""
     import torch
     dev = torch.device("cuda:0")
     F = llr.shape[0]
@@ -69,9 +71,13 @@ def gpu_decode(ldpc, graph, llr, syn, max_iter, rule, trace_iters=0, fp64=False,
         ta = torch.full((trace_iters, F, graph.n), float("nan"), dtype=dt, device=dev)
         tq = torch.full((trace_iters, F), float("nan"), dtype=torch.float64, device=dev)
     stats = ldpc.ldpc_decode_stats()
+    opts.setdefault("debug_guards", True)
     bits, flags, iters = ldpc.decode(graph, t_llr, t_syn, max_iter, rule, fp64=fp64, trace_iters=trace_iters,
                                      trace_c2v=tc, trace_app=ta, trace_q=tq, stats=stats, **opts)
     torch.cuda.synchronize()
+    if opts["debug_guards"]:  # the decode wrote nothing outside its workspace arrays
+        st = ldpc.ldpc_graph_check_guards(graph.handle)
+        assert st == ldpc.LDPC_OK, ldpc.ldpc_status_str(st)
     out = dict(bits=bits.cpu().numpy(), flags=flags.cpu().numpy(), iters=iters.cpu().numpy(), stats=stats)
     if trace_iters:
         out.update(c2v=tc.cpu().numpy().astype(np.float64), app=ta.cpu().numpy().astype(np.float64),

@@ -42,13 +42,13 @@ def test_library_exports_every_declared_symbol(ldpc):
 
 
 def test_struct_layout_matches_header(ldpc):
-    # opts: 6 x 4-byte fields, 4 pointers, 5 x 4-byte fields (+4 padding); stats: 2 floats, 4 ints, 1 int64
-    assert ctypes.sizeof(ldpc.ldpc_decode_opts) == 24 + 4 * 8 + 20 + 4
+    # opts: 6 x 4-byte fields, 4 pointers, 6 x 4-byte fields; stats: 2 floats, 4 ints, 1 int64
+    assert ctypes.sizeof(ldpc.ldpc_decode_opts) == 24 + 4 * 8 + 24
     assert ctypes.sizeof(ldpc.ldpc_decode_stats) == 32
     o = ldpc.ldpc_decode_opts_init()
     assert o.vnr_first_iter == 2 and o.clamp == 25.0 and o.fp64 == 0 and o.trace_iters == 0
     assert o.barrier_timeout_ms == 0 and o.test_unreachable_barrier == 0 and o.groups == 0
-    assert o.schedule == 0 and o.flow_lag == 0
+    assert o.schedule == 0 and o.flow_lag == 0 and o.debug_guards == 0
 
 
 def test_status_strings(ldpc):
@@ -97,3 +97,21 @@ def test_decode_argument_errors_need_no_gpu(ldpc):
     # a null graph and bad sizes are refused before any CUDA call
     assert ldpc.ldpc_decode(None, 1, 1, 1, 10, 2, 1, 1, 1, None, None) == ldpc.LDPC_ERR_INVALID_ARG
     assert ldpc.ldpc_decode_host(None, 1, 1, 1, 10, 2, 1, 1, 1, None, None) == ldpc.LDPC_ERR_INVALID_ARG
+
+
+def test_guard_check_needs_a_guarded_decode(ldpc):
+    # no graph, and a graph whose workspace holds no guards yet: refused on the host
+    assert ldpc.ldpc_graph_check_guards(None) == ldpc.LDPC_ERR_INVALID_ARG
+    assert ldpc.ldpc_batch_check_guards(None) == ldpc.LDPC_ERR_INVALID_ARG
+    assert "guard" in ldpc.ldpc_status_str(ldpc.LDPC_ERR_BOUNDS)
+
+
+def test_index_checking_build_compiles_and_exports(ldpc):
+    """The debug build (-DLDPC_BOUNDS_CHECK) builds for sm_103a and exports the
+    same boundary."""
+    from paper_2507_03509_gb300 import build
+    path = build.build(checked=True)
+    assert path.endswith("libldpc_gb300_checked.so")
+    lib = ctypes.CDLL(path)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
