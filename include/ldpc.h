@@ -145,6 +145,12 @@ typedef struct ldpc_decode_opts {
  * items of the previous pass that it reads are done (per-item completion
  * words), so one frame's new check messages are read back while still in L2. */
 #define LDPC_SCHEDULE_DATAFLOW 2
+/* Frame per CTA (one CSR code whose frame fits a CTA's shared memory, about
+ * 4 bytes per edge and per variable up to 200 KB; FP32): each CTA takes whole
+ * frames from the queue and decodes them in shared memory with CTA barriers
+ * only.  At n = 4096 with 64 frames it measured slower than lock-step (one
+ * 8-warp CTA per SM waits on its dependent index loads), so it is opt-in. */
+#define LDPC_SCHEDULE_FRAME 3
 
 /* Fill *opts with the defaults (vnr_first_iter 2, clamp 25, FP32, automatic
  * concurrency and grid, no trace, no stats).  NULL is ignored. */

@@ -18,6 +18,7 @@
 #include "../../include/ldpc.h"
 #include "bp_kernels.cuh"
 #include "flow_kernel.cuh"
+#include "frame_kernel.cuh"
 #include "host_common.h"
 
 using namespace ldpcgb;
@@ -569,6 +570,104 @@ ldpc_status launch_flow(Workspace& ws, const Job& job, const ldpc_decode_opts& o
     return finish_decode(ws, o, stream, status_out, grid, slots);
 }
 
+// Shared memory a frame-per-CTA decode of this job's code needs, or 0 if the
+// schedule does not apply (one CSR code; FP32; its frame fits 200 KB).
+size_t frame_schedule_smem(const Job& job, bool fp64) {
+    if (job.ngraphs != 1 || fp64 || job.graphs[0]->kind != 0) return 0;
+    const ldpc_graph* g = job.graphs[0];
+    const size_t b = frame_smem_bytes(g->E, g->n, g->vn_tiles);
+    return b <= 200 * 1024 ? b : 0;
+}
+
+// One decode with the frame-per-CTA schedule (frame_kernel.cuh): every CTA
+// takes whole frames from the queue and decodes each in shared memory.
+ldpc_status launch_frame(Workspace& ws, const Job& job, const ldpc_decode_opts& o, cudaStream_t stream,
+                         int32_t* status_out, size_t smem) {
+    const int frames = job.frames;
+    auto kernel = job.wts ? csr_frame_kernel<true> : csr_frame_kernel<false>;
+    int dev = 0, sms = 0, per_sm = 0;
+    LDPC_TRY(cudaGetDevice(&dev));
+    LDPC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    LDPC_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // leave half of the unified L1 / shared memory to L1, which caches the code's index lists
+    LDPC_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 50));
+    LDPC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, smem));
+    if (per_sm < 1) return LDPC_ERR_CUDA;
+    int grid = std::min(std::min(per_sm * sms, kMaxGrid), frames);
+    if (o.grid_ctas > 0) grid = std::min(grid, o.grid_ctas);
+    CodeSet<CsrDev> cs{};
+    SlotSizes sz{};
+    PackInfo pi{};
+    code_set(job, grid, 1, cs, sz, pi);
+    Layout L = make_layout(1, sizeof(float), sz.E, sz.n, sz.nqb, job.sbits_words, o.debug_guards != 0);
+    if (o.debug_guards) {
+        L.guards.push_back(L.total);
+        L.total += kGuardBytes;
+    }
+    cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+    LDPC_TRY(cudaStreamIsCapturing(stream, &capturing));
+    if (capturing != cudaStreamCaptureStatusNone && (ws.cap < L.total || !ws.ctrl)) return LDPC_ERR_INVALID_ARG;
+    ldpc_status st = ensure_workspace(ws, L.total);
+    if (st != LDPC_OK) return st;
+    char* base = (char*)ws.buf;
+    ws.guard_off.clear();
+    if (o.debug_guards) {
+        st = fill_guards(ws, L.guards, stream);
+        if (st != LDPC_OK) return st;
+    }
+    Params<float> p{};
+    p.frames = frames;
+    p.max_iter = job.max_iter;
+    p.rule = job.rule;
+    p.vnr_first_iter = o.vnr_first_iter;
+    p.lmax = o.clamp;
+    p.frame_code = job.frame_code;
+    p.var_off = job.var_off;
+    p.sb_off = job.sb_off;
+    p.llr = job.llr;
+    p.sbits = (const unsigned*)(base + L.sbits);
+    p.bits_out = job.bits_out;
+    p.flags_out = job.flags_out;
+    p.iters_out = job.iters_out;
+    p.slots = 1;
+    p.slot_E = sz.E;
+    p.slot_n = sz.n;
+    p.slot_nqb = sz.nqb;
+    p.cn_tiles_max = sz.cn_max;
+    p.vn_tiles_max = sz.vn_max;
+    p.c2v = (float*)(base + L.c2v);
+    p.app = (float*)(base + L.app);
+    p.qpart = (double*)(base + L.qpart);
+    p.q0part = (double*)(base + L.q0part);
+    p.ctrl = ws.ctrl;
+    p.trace_iters = o.trace_iters;
+    p.trace_c2v = (float*)o.trace_c2v;
+    p.trace_app = (float*)o.trace_app;
+    p.trace_q = o.trace_q;
+    p.groups = 1;
+    p.slots_per_group = 1;
+    p.wts = job.wts;
+    p.wcls = job.wcls;
+    p.w_iters = job.w_iters;
+    p.w_classes = job.w_classes;
+    const bool timing = o.stats != nullptr && status_out == nullptr;
+    if (timing) LDPC_TRY(cudaEventRecord(ws.ev[0], stream));
+    init_ctrl_kernel<<<1, 256, 0, stream>>>(ws.ctrl, 1, 0, (int*)(base + L.unsat), 2);  // queue from frame 0
+    LDPC_TRY(cudaGetLastError());
+    {
+        const dim3 pgrid((unsigned)std::max(1, std::min((pi.swords[0] + 31) / 32, 4096)),
+                         (unsigned)std::max(1, std::min(frames, 65535)));
+        pack_syndrome_kernel<<<pgrid, 256, 0, stream>>>(job.syndrome, frames, pi, (unsigned*)(base + L.sbits),
+                                                        ws.ctrl);
+        LDPC_TRY(cudaGetLastError());
+    }
+    if (timing) LDPC_TRY(cudaEventRecord(ws.ev[1], stream));
+    kernel<<<grid, kThreads, smem, stream>>>(p, cs.c[0]);
+    LDPC_TRY(cudaGetLastError());
+    if (timing) LDPC_TRY(cudaEventRecord(ws.ev[2], stream));
+    return finish_decode(ws, o, stream, status_out, grid, grid);
+}
+
 // Schedule of a job: lock-step unless the caller asks for dataflow (QC only).
 // Measured at n = 1e6 with 32 frames, the dataflow schedule ran at half the
 // lock-step rate: its items wait on the per-frame decision, a join over every
@@ -588,6 +687,15 @@ ldpc_status launch_decode(Workspace& ws, const Job& job, const ldpc_decode_opts&
     if constexpr (std::is_same<Code, QcDev>::value) {
         if (use_flow<T, Code>(o)) return launch_flow<T>(ws, job, o, stream, status_out);
     }
+    if constexpr (std::is_same<Code, CsrDev>::value && std::is_same<T, float>::value) {
+        // frame per CTA (asked for; it applies to one small CSR code)
+        if (o.schedule == LDPC_SCHEDULE_FRAME) {
+            const size_t smem = frame_schedule_smem(job, false);
+            if (smem == 0) return LDPC_ERR_INVALID_ARG;
+            return launch_frame(ws, job, o, stream, status_out, smem);
+        }
+    }
+    if (o.schedule == LDPC_SCHEDULE_FRAME) return LDPC_ERR_INVALID_ARG;
     const int frames = job.frames;
     // the weighted kernel is a separate instantiation: the unweighted one carries no weight code
     auto kernel = job.wts ? bp_decode_kernel<T, Code, true> : bp_decode_kernel<T, Code, false>;
@@ -754,7 +862,7 @@ ldpc_status check_decode_args(const ldpc_graph* graph, int32_t frames, const voi
         o.barrier_timeout_ms < 0 || o.groups < 0 || o.groups > kMaxGroups)
         return LDPC_ERR_INVALID_ARG;
     if (o.debug_guards != 0 && o.debug_guards != 1) return LDPC_ERR_INVALID_ARG;
-    if (o.schedule < LDPC_SCHEDULE_AUTO || o.schedule > LDPC_SCHEDULE_DATAFLOW || o.flow_lag < 0 ||
+    if (o.schedule < LDPC_SCHEDULE_AUTO || o.schedule > LDPC_SCHEDULE_FRAME || o.flow_lag < 0 ||
         (o.schedule == LDPC_SCHEDULE_DATAFLOW && graph->kind != 1))
         return LDPC_ERR_INVALID_ARG;
     if ((long long)frames * graph->n > (1LL << 40)) return LDPC_ERR_INVALID_ARG;

@@ -1,4 +1,5 @@
-"""The dataflow schedule (no grid barriers) against the lock-step schedule.
+"""The dataflow schedule (no grid barriers) and the frame-per-CTA schedule
+(small CSR codes in shared memory) against the lock-step schedule.
 
 Both run the same check and variable items and take the same decisions with
 the same fixed-order q, so every result must be bit-identical: decided bits,
@@ -157,3 +158,81 @@ def test_dataflow_refused_for_csr(ldpc):
                     schedule="dataflow")
     assert ei.value.status == ldpc.LDPC_ERR_INVALID_ARG
     g.close()
+
+
+def degenerate_csr():
+    rows = [[0], [0, 1], [1, 2, 3], [], [2, 4, 5, 6, 7, 8, 9, 10], [3, 4], [5, 11]]
+    rowptr = np.cumsum([0] + [len(r) for r in rows]).astype(np.int32)
+    return gen.CSRCode(len(rows), 13, rowptr, np.concatenate([np.asarray(r, np.int32) for r in rows]))
+
+
+@pytest.mark.parametrize("case", ["csr_n4096", "fd_n256", "degenerate", "decodable"])
+def test_frame_schedule_equals_lockstep(ldpc, case):
+    if case == "csr_n4096":
+        code = gen.workload_code(1)
+        fr = gen.workload_frames(1, code, frames=20)
+    elif case == "fd_n256":
+        code = gen.wbp_fd_code()
+        fr = gen.make_frames(code, np.full(9, gen.sigma_for_capacity(code.rate / 0.9)), range(300, 309))
+    elif case == "degenerate":
+        code = degenerate_csr()
+        rng = np.random.default_rng(2)
+        x = rng.integers(0, 2, size=(11, code.n)).astype(np.uint8)
+        llr = ((1.0 - 2.0 * x) + 1.1 * rng.standard_normal(x.shape)).astype(np.float32) * 1.3
+        fr = gen.Frames(x, llr, gen.syndrome(code, x), np.full(11, 1.1))
+    else:
+        code = gen.random_csr_code(2000, 1000, 3, {6: 1000}, seed=4242)
+        fr = gen.make_frames(code, np.full(12, 0.78), seeds=range(800, 812))
+    g = ldpc.Graph.from_code(code)
+    for rule in ("pce_vnr", "pce", "none"):
+        ref = gpu_decode(ldpc, g, fr.llr, fr.syndrome, 60, rule, trace_iters=5, schedule="lockstep")
+        for opts in (dict(schedule="frame"), dict(schedule="frame", grid_ctas=2),
+                     dict(schedule="frame", vnr_first_iter=1)):
+            r = ref
+            if opts.get("vnr_first_iter") == 1:
+                r = gpu_decode(ldpc, g, fr.llr, fr.syndrome, 60, rule, trace_iters=5, schedule="lockstep",
+                               vnr_first_iter=1)
+            got = gpu_decode(ldpc, g, fr.llr, fr.syndrome, 60, rule, trace_iters=5, **opts)
+            same(got, r, (case, rule, opts), traces=True)
+    g.close()
+
+
+def test_frame_schedule_learned_weights_and_batch(ldpc):
+    import torch
+    code = gen.workload_code(1)
+    fr = gen.workload_frames(1, code, frames=10)
+    g = ldpc.Graph.from_code(code)
+    cls, C, _ = gen.edge_classes_by_check_degree(code)
+    plan = ldpc.WeightedBP(g, 2, 4, cls, C)
+    dev = torch.device("cuda:0")
+    w = torch.from_numpy(np.random.default_rng(5).uniform(0.7, 1.1, size=(4, C)).astype(np.float32)).to(dev)
+    llr, syn = torch.from_numpy(fr.llr).to(dev), torch.from_numpy(fr.syndrome).to(dev)
+    out = {}
+    for sched in ("lockstep", "frame"):
+        b, f, i = plan.decode(llr, syn, w, 80, "pce_vnr", schedule=sched)
+        out[sched] = dict(bits=b.cpu().numpy(), flags=f.cpu().numpy(), iters=i.cpu().numpy())
+    same(out["frame"], out["lockstep"], "weights")
+    plan.close()
+    batch = ldpc.Batch([g], np.zeros(10, dtype=np.int32))
+    res = {}
+    for sched in ("lockstep", "frame"):
+        o = batch.decode(llr.reshape(-1), syn.reshape(-1), 80, "pce_vnr", schedule=sched, debug_guards=True)
+        torch.cuda.synchronize()
+        assert ldpc.ldpc_batch_check_guards(batch.handle) == ldpc.LDPC_OK
+        res[sched] = dict(bits=o[0].cpu().numpy(), flags=o[1].cpu().numpy(), iters=o[2].cpu().numpy())
+    same(res["frame"], res["lockstep"], "batch")
+    batch.close()
+    g.close()
+
+
+def test_frame_schedule_refused_where_it_does_not_apply(ldpc):
+    import torch
+    dev = torch.device("cuda:0")
+    for code, kw in ((gen.workload_code(2, Z=64), {}), (gen.workload_code(1), dict(fp64=True))):
+        fr = gen.workload_frames(2 if hasattr(code, "shifts") else 1, code, frames=2)
+        g = ldpc.Graph.from_code(code)
+        with pytest.raises(ldpc.LdpcError) as ei:
+            ldpc.decode(g, torch.from_numpy(fr.llr).to(dev), torch.from_numpy(fr.syndrome).to(dev), 5, "pce",
+                        schedule="frame", **kw)
+        assert ei.value.status == ldpc.LDPC_ERR_INVALID_ARG
+        g.close()

@@ -186,11 +186,11 @@ def test_groups_concurrency_and_grid_do_not_change_results(ldpc, csr1, qc_small)
         g = ldpc.Graph.from_code(code)
         fr = gen.workload_frames(wl, code, frames=9)
         ref = gpu_decode(ldpc, g, fr.llr, fr.syndrome, 40, "pce_vnr", trace_iters=3, groups=1,
-                         max_active_frames=9)
+                         max_active_frames=9, schedule="lockstep")
         for slots, ctas, groups in ((0, 0, 0), (3, 0, 1), (3, 0, 3), (1, 0, 0), (9, 1, 0), (9, 0, 4),
                                     (4, 7, 0), (8, 0, 2), (0, 0, 8)):
             got = gpu_decode(ldpc, g, fr.llr, fr.syndrome, 40, "pce_vnr", trace_iters=3,
-                             max_active_frames=slots, grid_ctas=ctas, groups=groups)
+                             max_active_frames=slots, grid_ctas=ctas, groups=groups, schedule="lockstep")
             for key in ("bits", "flags", "iters"):
                 assert np.array_equal(got[key], ref[key]), (slots, ctas, groups, key)
             for key in ("c2v", "app", "q"):
