@@ -561,25 +561,32 @@ def l2_resident(ldpc, dev, steps=10):
     B = algorithmic_bytes_per_frame_iter(code)
     l2 = l2_copy_gbs(dev)
     out = {"workload": wl["name"], "frames": int(fr.llr.shape[0]), "n": code.n, "edges": int(code.edges),
-           "max_iter": wl["max_iter"], "bytes_per_frame_iter": B, "l2_copy_gbs_measured": l2, "rules": {}}
-    for rule in ("pce_vnr", "pce", "none"):
-        for _ in range(3):
-            ldpc.decode(g, llr, syn, wl["max_iter"], rule)
-        kms, tms, fi = [], [], 0
-        for _ in range(steps):
-            st = ldpc.ldpc_decode_stats()
-            bits, flags, iters = ldpc.decode(g, llr, syn, wl["max_iter"], rule, stats=st)
-            kms.append(st.kernel_ms)
-            tms.append(st.total_ms)
-            fi = st.frame_iterations
-        k = statistics.median(kms) * 1e-3
-        t = statistics.median(tms) * 1e-3
-        ok = ((flags.cpu().numpy() & 1) > 0) & (bits.cpu().numpy() == fr.x).all(1)
-        gbs = fi * B / k / 1e9
-        out["rules"][rule] = {"decoded_mbit_s": code.n * fr.llr.shape[0] / t / 1e6, "kernel_ms": k * 1e3,
-                              "total_ms": t * 1e3, "d_mean": fi / fr.llr.shape[0], "fer": float(1 - ok.mean()),
-                              "achieved_gbs": gbs, "frac_of_l2_copy": gbs / l2,
-                              "frac_of_hbm_peak": gbs / hbm_peak()[0]}
+           "max_iter": wl["max_iter"], "bytes_per_frame_iter": B, "l2_copy_gbs_measured": l2, "rules": {},
+           "schedules": {}}
+    for sched in ("auto", "lockstep", "frame"):
+        res = {}
+        for rule in ("pce_vnr", "pce", "none"):
+            for _ in range(3):
+                ldpc.decode(g, llr, syn, wl["max_iter"], rule, schedule=sched)
+            kms, tms, fi = [], [], 0
+            for _ in range(steps):
+                st = ldpc.ldpc_decode_stats()
+                bits, flags, iters = ldpc.decode(g, llr, syn, wl["max_iter"], rule, stats=st, schedule=sched)
+                kms.append(st.kernel_ms)
+                tms.append(st.total_ms)
+                fi = st.frame_iterations
+            k = statistics.median(kms) * 1e-3
+            t = statistics.median(tms) * 1e-3
+            ok = ((flags.cpu().numpy() & 1) > 0) & (bits.cpu().numpy() == fr.x).all(1)
+            gbs = fi * B / k / 1e9
+            res[rule] = {"decoded_mbit_s": code.n * fr.llr.shape[0] / t / 1e6, "kernel_ms": k * 1e3,
+                         "total_ms": t * 1e3, "d_mean": fi / fr.llr.shape[0], "fer": float(1 - ok.mean()),
+                         "achieved_gbs": gbs, "frac_of_l2_copy": gbs / l2, "frac_of_hbm_peak": gbs / hbm_peak()[0]}
+        if sched == "auto":
+            out["rules"] = res
+        else:
+            out["schedules"][sched] = {r: {key: v[key] for key in ("kernel_ms", "decoded_mbit_s", "frac_of_l2_copy")}
+                                       for r, v in res.items()}
     g.close()
     return out
 

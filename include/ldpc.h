@@ -118,8 +118,8 @@ typedef struct ldpc_decode_opts {
                                   barriers, and frames that stop are replaced from one shared
                                   queue.  Results are bit-identical for any value.             */
     int32_t schedule;          /* LDPC_SCHEDULE_*: how the persistent kernel orders its work.
-                                  0 = automatic (lock-step).  Results are bit-identical for
-                                  every schedule.                                             */
+                                  0 = automatic (frame per CTA where it applies, lock-step
+                                  otherwise).  Results are bit-identical for every schedule.  */
     int32_t flow_lag;          /* dataflow schedule only: how many slot-steps after a frame's
                                   check pass its variable pass is scheduled (0 = 2; at most the
                                   number of frames in flight).                                */
@@ -130,10 +130,12 @@ typedef struct ldpc_decode_opts {
                                   outside its arrays.  Default 0 (no guards).                 */
 } ldpc_decode_opts;
 
-/* Values of ldpc_decode_opts.schedule.  On GB300 at n = 10^6 with 32 frames the
- * dataflow schedule measured half the lock-step rate (its items wait on each
- * frame's decision, a join over all of the frame's check items, every
- * iteration), so automatic selection takes lock-step. */
+/* Values of ldpc_decode_opts.schedule.  Automatic selection takes frame per
+ * CTA for one small CSR code in FP32 (on GB300 at n = 4096 with 64 frames it
+ * ran 1.9-2.6x faster than lock-step) and lock-step otherwise: at n = 10^6
+ * with 32 frames the dataflow schedule measured half the lock-step rate (its
+ * items wait on each frame's decision, a join over all of the frame's check
+ * items, every iteration). */
 #define LDPC_SCHEDULE_AUTO 0
 /* Lock-step: CTA groups advance their frames between grid-wide barriers
  * (check pass of every frame in flight, barrier, decisions, variable pass,
@@ -145,11 +147,12 @@ typedef struct ldpc_decode_opts {
  * items of the previous pass that it reads are done (per-item completion
  * words), so one frame's new check messages are read back while still in L2. */
 #define LDPC_SCHEDULE_DATAFLOW 2
-/* Frame per CTA (one CSR code whose frame fits a CTA's shared memory, about
- * 4 bytes per edge and per variable up to 200 KB; FP32): each CTA takes whole
- * frames from the queue and decodes them in shared memory with CTA barriers
- * only.  At n = 4096 with 64 frames it measured slower than lock-step (one
- * 8-warp CTA per SM waits on its dependent index loads), so it is opt-in. */
+/* Frame per CTA (one CSR code in FP32 whose frame and index lists fit a CTA's
+ * shared memory: 16-bit indices, so n, m and E below 65536, and about
+ * 8 E + 12 n + 2 m bytes up to 220 KB): each 1024-thread CTA takes whole frames
+ * from the queue and decodes each in shared memory with CTA barriers only.
+ * max_active_frames and groups do not apply.  Asking for it where it does not
+ * apply returns LDPC_ERR_INVALID_ARG. */
 #define LDPC_SCHEDULE_FRAME 3
 
 /* Fill *opts with the defaults (vnr_first_iter 2, clamp 25, FP32, automatic

@@ -560,10 +560,14 @@ __device__ __forceinline__ bool cn_tile(const Params<T>& p, const CsrDev& g, con
 // (GB300's FP64 rate is a small fraction of its FP32 rate); q differs from the
 // oracle's by FP32 APP rounding far more than by this tree.
 template <typename T>
-__device__ __forceinline__ void warp_sum_store(T acc, double* dst) {
+__device__ __forceinline__ void warp_sum_to(T acc, double* slot) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if ((threadIdx.x & 31) == 0) dst[threadIdx.x >> 5] = double(acc);
+    if ((threadIdx.x & 31) == 0) *slot = double(acc);
+}
+template <typename T>
+__device__ __forceinline__ void warp_sum_store(T acc, double* dst) {
+    warp_sum_to(acc, dst + (threadIdx.x >> 5));
 }
 
 // Trace of c2v^(k+1) for variable j*Z + u, written from the variable side so

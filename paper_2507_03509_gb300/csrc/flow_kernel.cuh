@@ -133,26 +133,26 @@ __device__ __forceinline__ bool warp_wait_flags(const int* flag, const int* idx,
 // One warp computes block_sum_fixed(part, count) bit for bit: lane l plays
 // the threads w * 32 + l (w = 0 .. kWarps - 1) of that 256-thread sum, each
 // accumulating its elements in the same order, then each emulated warp's
-// butterfly, then the sum over the emulated warps in order.
+// butterfly, then the sum over the emulated warps in order.  Groups of
+// elements past `count` and emulated warps that hold none are skipped: their
+// additions add +0.0 to sums of non-negative terms, which changes nothing,
+// and FP64 instructions are scarce on this part (about two per clock per SM).
 __device__ __forceinline__ double warp_block_sum_fixed(const double* part, int count) {
     const int lane = threadIdx.x & 31;
-    double acc[kWarps];
-#pragma unroll
-    for (int w = 0; w < kWarps; ++w) acc[w] = 0.0;
-    for (int base = 0; base < count; base += 8 * kThreads) {
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-#pragma unroll
-            for (int w = 0; w < kWarps; ++w) {
-                const int t = base + u * kThreads + w * 32 + lane;
-                acc[w] += t < count ? part[t] : 0.0;
-            }
-        }
-    }
     double tot = 0.0;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) {
-        double a = acc[w];
+        if (w * 32 >= count) break;  // this and later emulated warps hold only zeros
+        double a = 0.0;
+        for (int base = 0; base < count; base += 8 * kThreads) {
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int t0 = base + u * kThreads + w * 32;
+                if (t0 >= count) break;  // uniform: later groups of this pass are past the end
+                const int t = t0 + lane;
+                a += t < count ? part[t] : 0.0;
+            }
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
         tot += a;

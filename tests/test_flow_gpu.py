@@ -186,7 +186,7 @@ def test_frame_schedule_equals_lockstep(ldpc, case):
     g = ldpc.Graph.from_code(code)
     for rule in ("pce_vnr", "pce", "none"):
         ref = gpu_decode(ldpc, g, fr.llr, fr.syndrome, 60, rule, trace_iters=5, schedule="lockstep")
-        for opts in (dict(schedule="frame"), dict(schedule="frame", grid_ctas=2),
+        for opts in (dict(schedule="frame"), dict(schedule="auto"), dict(schedule="frame", grid_ctas=2),
                      dict(schedule="frame", vnr_first_iter=1)):
             r = ref
             if opts.get("vnr_first_iter") == 1:
@@ -228,8 +228,12 @@ def test_frame_schedule_learned_weights_and_batch(ldpc):
 def test_frame_schedule_refused_where_it_does_not_apply(ldpc):
     import torch
     dev = torch.device("cuda:0")
-    for code, kw in ((gen.workload_code(2, Z=64), {}), (gen.workload_code(1), dict(fp64=True))):
-        fr = gen.workload_frames(2 if hasattr(code, "shifts") else 1, code, frames=2)
+    big = gen.random_csr_code(20000, 10000, 3, {6: 10000}, seed=77)  # 60000 edges: beyond shared memory
+    for code, kw in ((gen.workload_code(2, Z=64), {}), (gen.workload_code(1), dict(fp64=True)), (big, {})):
+        if code is big:
+            fr = gen.make_frames(code, np.full(2, 0.8), seeds=range(2))
+        else:
+            fr = gen.workload_frames(2 if hasattr(code, "shifts") else 1, code, frames=2)
         g = ldpc.Graph.from_code(code)
         with pytest.raises(ldpc.LdpcError) as ei:
             ldpc.decode(g, torch.from_numpy(fr.llr).to(dev), torch.from_numpy(fr.syndrome).to(dev), 5, "pce",
