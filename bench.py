@@ -45,8 +45,8 @@ def parse():
     ap.add_argument("--slots", type=int, default=0, help="max_active_frames (0 = automatic)")
     ap.add_argument("--grid", type=int, default=0, help="grid_ctas (0 = all that fit)")
     ap.add_argument("--groups", type=int, default=0, help="independent CTA groups (0 = automatic)")
-    ap.add_argument("--schedule", default="auto", choices=["auto", "lockstep", "dataflow"],
-                    help="persistent kernel schedule (auto: lock-step)")
+    ap.add_argument("--schedule", default="auto", choices=["auto", "lockstep", "dataflow", "frame"],
+                    help="decode schedule (auto: frame per CTA for small CSR codes, lock-step otherwise)")
     ap.add_argument("--flow-lag", type=int, default=0, help="dataflow schedule lag (0 = default)")
     ap.add_argument("--compare-steps", type=int, default=2, help="timed steps of each fixed-iteration rule")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -92,16 +92,32 @@ def algorithmic_bytes_per_frame_iter(code) -> int:
     return 8 * int(code.edges) + 12 * int(code.n) + csr_index_bytes_per_frame_iter(code)
 
 
+def frame_schedule_applies(code) -> bool:
+    """Whether the frame-per-CTA kernel takes a CSR code: 16-bit indices and its
+    shared memory (frame, q partials and index lists, 16-byte aligned pieces)
+    within 220 KB -- the library's own rule, restated for naming the kernel."""
+    n, m, E = code.n, code.m, int(code.edges)
+    if hasattr(code, "shifts") or max(n, m, E) > 65535:
+        return False
+    r16 = lambda b: (b + 15) // 16 * 16
+    nqb, swords = (n + 1023) // 1024, (m + 31) // 32
+    total = (2 * r16(nqb * 8 * 8) + r16(4 * E) + 2 * r16(4 * n) + r16(4 * swords) + 2 * r16(2 * E)
+             + r16(2 * (m + 1)) + r16(2 * m) + r16(2 * (n + 1)))
+    return total <= 220 * 1024
+
+
 def decoder_kernel_name(code, schedule="auto") -> str:
-    """The persistent kernel a decode of this code runs (FP32)."""
+    """The decode kernel a decode of this code runs (FP32)."""
     qc = hasattr(code, "shifts")
     if qc and schedule == "dataflow":
         return "bp_flow_kernel<float>"
+    if not qc and schedule in ("auto", "frame") and frame_schedule_applies(code):
+        return "csr_frame_kernel<false>"
     return "bp_decode_kernel<float,%s>" % ("QcDev" if qc else "CsrDev")
 
 
-DECODER_SOURCES = ("bp_kernels.cuh", "flow_kernel.cuh", "cn_math.cuh", "device_types.h", "host_common.h",
-                   "ldpc_api.cu")
+DECODER_SOURCES = ("bp_kernels.cuh", "flow_kernel.cuh", "frame_kernel.cuh", "cn_math.cuh", "device_types.h",
+                   "host_common.h", "ldpc_api.cu")
 
 
 def kernel_source_hash() -> str:

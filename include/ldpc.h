@@ -149,7 +149,7 @@ typedef struct ldpc_decode_opts {
 #define LDPC_SCHEDULE_DATAFLOW 2
 /* Frame per CTA (one CSR code in FP32 whose frame and index lists fit a CTA's
  * shared memory: 16-bit indices, so n, m and E below 65536, and about
- * 8 E + 12 n + 2 m bytes up to 220 KB): each 1024-thread CTA takes whole frames
+ * 8 E + 12 n + 4 m bytes up to 220 KB): each 1024-thread CTA takes whole frames
  * from the queue and decodes each in shared memory with CTA barriers only.
  * max_active_frames and groups do not apply.  Asking for it where it does not
  * apply returns LDPC_ERR_INVALID_ARG. */

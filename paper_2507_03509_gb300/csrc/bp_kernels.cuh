@@ -782,29 +782,45 @@ __device__ __forceinline__ void final_tile(const CsrDev&, const FrameCtx<T>& fc,
     final_tile(fc, tile);
 }
 
-// Deterministic FP64 sum of a frame's per-tile partials (fixed order).
+// Deterministic FP64 sum of a frame's per-tile partials (fixed order); the
+// result is valid in thread 0, its only reader.  Additions of a known +0.0 are
+// skipped: groups of kThreads elements that lie wholly past `count`, butterfly
+// steps and warps without elements.  They would add +0.0 to a sum of
+// non-negative terms, which changes nothing, and FP64 instructions are scarce
+// on this part (about two per clock per SM).
 __device__ __forceinline__ double block_sum_fixed(const double* part, int count, double* s_red) {
     double acc = 0.0;
     for (int base = 0; base < count; base += 8 * kThreads) {  // 8 loads in flight per thread
+        const int groups = min(8, (count - base + kThreads - 1) / kThreads);
         double v[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int t = base + u * kThreads + (int)threadIdx.x;
-            v[u] = t < count ? part[t] : 0.0;
+            v[u] = (u < groups && t < count) ? part[t] : 0.0;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc += v[u];
+        for (int u = 0; u < 8; ++u)
+            if (u < groups) acc += v[u];
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    // the warp's butterfly: step o adds nothing to lane 0 when lanes o .. 31 of
+    // the warp hold no element (live <= o), so it is skipped
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int live = count - warp * 32;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double b = __shfl_xor_sync(0xffffffffu, acc, o);
+        if (o < live) acc += b;
+    }
     __syncthreads();
     if (lane == 0) s_red[warp] = acc;
     __syncthreads();
     double t = 0.0;
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) t += s_red[w];
-    return t;  // same value in every thread
+        for (int w = 0; w < kWarps; ++w)
+            if (w * 32 < count) t += s_red[w];
+    }
+    return t;
 }
 
 // ---------------------------------------------------------------------------
@@ -938,9 +954,10 @@ __global__ void __launch_bounds__(kThreads, 4) bp_decode_kernel(Params<T> p, Cod
                         }
                         double qv = 0.0, q0 = 0.0;
 #pragma unroll
-                        for (int r = 0; r < kQParts; ++r) {
-                            qv += qr[r];
-                            q0 += q0r[r];
+                        for (int r = 0; r < kQParts; ++r) qv += qr[r];
+                        if (with_q0) {
+#pragma unroll
+                            for (int r = 0; r < kQParts; ++r) q0 += q0r[r];
                         }
                         if (lb == 0 && k <= p.trace_iters && p.trace_q)
                             p.trace_q[(long long)(k - 1) * p.frames + f] = qv;

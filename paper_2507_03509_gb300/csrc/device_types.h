@@ -38,6 +38,7 @@ struct CsrDev {
     const int* col_idx;            // [E]
     const int* var_ptr;            // [n+1]
     const int* var_edge;           // [E] edge ids of variable v, ascending
+    const int* row_order;          // [m] checks by ascending degree, ascending within a degree
 };
 
 }  // namespace ldpcgb

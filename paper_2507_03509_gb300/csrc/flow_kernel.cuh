@@ -133,31 +133,39 @@ __device__ __forceinline__ bool warp_wait_flags(const int* flag, const int* idx,
 // One warp computes block_sum_fixed(part, count) bit for bit: lane l plays
 // the threads w * 32 + l (w = 0 .. kWarps - 1) of that 256-thread sum, each
 // accumulating its elements in the same order, then each emulated warp's
-// butterfly, then the sum over the emulated warps in order.  Groups of
-// elements past `count` and emulated warps that hold none are skipped: their
-// additions add +0.0 to sums of non-negative terms, which changes nothing,
-// and FP64 instructions are scarce on this part (about two per clock per SM).
+// butterfly, then the sum over the emulated warps in order.  Additions whose
+// other operand is known to be +0.0 are skipped (they change nothing in a sum
+// of non-negative terms, and FP64 instructions are scarce on this part, about
+// two per clock per SM): element groups past `count`, emulated warps that hold
+// no element, and butterfly steps o whose partner lanes o .. 31 hold none.  The
+// skipped steps leave some lanes' partial sums unfinished, never lane 0's:
+// the result is valid in lane 0, the only reader.
 __device__ __forceinline__ double warp_block_sum_fixed(const double* part, int count) {
     const int lane = threadIdx.x & 31;
     double tot = 0.0;
 #pragma unroll
     for (int w = 0; w < kWarps; ++w) {
-        if (w * 32 >= count) break;  // this and later emulated warps hold only zeros
-        double a = 0.0;
+        const int live = count - w * 32;  // elements of the emulated warp's first group
+        if (live <= 0) break;             // this and later emulated warps hold only zeros
+        double a = lane < live ? part[w * 32 + lane] : 0.0;  // 0.0 + x == x
         for (int base = 0; base < count; base += 8 * kThreads) {
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const int t0 = base + u * kThreads + w * 32;
-                if (t0 >= count) break;  // uniform: later groups of this pass are past the end
+                if (base + u == 0) continue;  // the first group is loaded above
+                if (t0 >= count) break;       // uniform: later groups of this pass are past the end
                 const int t = t0 + lane;
                 a += t < count ? part[t] : 0.0;
             }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        tot += a;
+        for (int o = 16; o > 0; o >>= 1) {
+            const double b = __shfl_xor_sync(0xffffffffu, a, o);
+            if (o < live) a += b;  // lanes o .. 31 of this emulated warp hold elements
+        }
+        tot = w == 0 ? a : tot + a;  // 0.0 + a == a
     }
-    return tot;  // same value in every lane
+    return tot;  // valid in lane 0
 }
 
 // Shared-memory state of one CTA's current item (written by warp 0).

@@ -2,8 +2,8 @@
 // the code's index lists in shared memory).
 //
 // When a frame's messages, APP values and channel LLRs, and the code's edge
-// lists as 16-bit indices, fit one CTA's shared memory (about 8E + 12n + 2m
-// bytes; the n = 4096 workload code needs 148 KB), a CTA of kFrameThreads
+// lists as 16-bit indices, fit one CTA's shared memory (about 8E + 12n + 4m
+// bytes; the n = 4096 workload code needs 155 KB), a CTA of kFrameThreads
 // threads decodes whole frames on its own, taking them from the shared queue.
 // It runs the lock-step kernel's steps (check pass with the fused syndrome
 // test, q^(k), decision, variable pass), separated by CTA barriers instead of
@@ -33,7 +33,7 @@ __host__ __device__ constexpr long long frame_round(long long x, long long a) { 
 
 // Byte offsets of the pieces of csr_frame_kernel's shared memory (16-byte aligned).
 struct FrameSmem {
-    long long part, part0, c2v, app, lch, sbits, col, vedge, rptr, vptr, total;
+    long long part, part0, c2v, app, lch, sbits, col, vedge, rptr, rord, vptr, total;
 };
 
 __host__ __device__ constexpr FrameSmem frame_smem_layout(long long E, int n, int m, int nqb, int swords) {
@@ -48,6 +48,7 @@ __host__ __device__ constexpr FrameSmem frame_smem_layout(long long E, int n, in
     s.col = o;   o += frame_round(E * 2, 16);
     s.vedge = o; o += frame_round(E * 2, 16);
     s.rptr = o;  o += frame_round((long long)(m + 1) * 2, 16);
+    s.rord = o;  o += frame_round((long long)m * 2, 16);
     s.vptr = o;  o += frame_round((long long)(n + 1) * 2, 16);
     s.total = o;
     return s;
@@ -133,6 +134,7 @@ __global__ void __launch_bounds__(kFrameThreads, 1) csr_frame_kernel(Params<floa
     unsigned short* col = (unsigned short*)(smem_frame + L.col);      // [E] variable of each edge
     unsigned short* vedge = (unsigned short*)(smem_frame + L.vedge);  // [E] edges of each variable
     unsigned short* rptr = (unsigned short*)(smem_frame + L.rptr);    // [m + 1]
+    unsigned short* rord = (unsigned short*)(smem_frame + L.rord);    // [m] checks by degree
     unsigned short* vptr = (unsigned short*)(smem_frame + L.vptr);    // [n + 1]
     __shared__ double s_q[kQParts], s_q0[kQParts];
     __shared__ int s_frame, s_unsat[2], s_stop;
@@ -146,6 +148,7 @@ __global__ void __launch_bounds__(kFrameThreads, 1) csr_frame_kernel(Params<floa
         vedge[e] = (unsigned short)__ldg(g.var_edge + e);
     }
     for (int i = tid; i <= m; i += kFrameThreads) rptr[i] = (unsigned short)__ldg(g.row_ptr + i);
+    for (int i = tid; i < m; i += kFrameThreads) rord[i] = (unsigned short)__ldg(g.row_order + i);
     for (int v = tid; v <= n; v += kFrameThreads) vptr[v] = (unsigned short)__ldg(g.var_ptr + v);
     const int npart = ci.nqb * kWarps;
     const int per = (npart + kQParts - 1) / kQParts;
@@ -167,7 +170,8 @@ __global__ void __launch_bounds__(kFrameThreads, 1) csr_frame_kernel(Params<floa
             const bool want_synd = k >= 1 && (p.rule != kRuleNone || k >= p.max_iter);
             if constexpr (W) fc.wrow = weight_row(p, k);
             bool unsat = false;
-            for (int row = tid; row < m; row += kFrameThreads) {
+            for (int i = tid; i < m; i += kFrameThreads) {  // checks by degree: warps run one degree's code
+                const int row = rord[i];
                 const int e0 = rptr[row];
                 const int d = (int)rptr[row + 1] - e0;
                 const unsigned sbit = (sb[row >> 5] >> (row & 31)) & 1u;
@@ -198,12 +202,15 @@ __global__ void __launch_bounds__(kFrameThreads, 1) csr_frame_kernel(Params<floa
                 }
                 asm volatile("bar.sync 1, %0;" ::"r"(kQParts * 32) : "memory");  // the range warps only
                 if (warp == 0) {
-                    double qv = 0.0, q0 = 0.0;
+                    // 0.0 + s_q[0] == s_q[0]; empty ranges hold +0.0 and are skipped
+                    double qv = s_q[0], q0 = s_q0[0];
 #pragma unroll
-                    for (int r = 0; r < kQParts; ++r) qv += s_q[r];
+                    for (int r = 1; r < kQParts; ++r)
+                        if (r * per < npart) qv += s_q[r];
                     if (with_q0) {
 #pragma unroll
-                        for (int r = 0; r < kQParts; ++r) q0 += s_q0[r];
+                        for (int r = 1; r < kQParts; ++r)
+                            if (r * per < npart) q0 += s_q0[r];
                     }
                     const bool sat = s_unsat[k & 1] == 0;
                     const double qp = with_q0 ? q0 : qprev;

@@ -942,13 +942,18 @@ ldpc_status ldpc_graph_create_csr(int32_t m, int32_t n, const int32_t* row_ptr, 
     g->m = m;
     g->n = n;
     g->E = E;
+    // checks ordered by degree (stable), so that the warps of a check pass that
+    // walks this order meet one degree at a time
+    std::vector<int> ro(m);
+    for (int i = 0; i < m; ++i) ro[i] = i;
+    std::stable_sort(ro.begin(), ro.end(), [&](int a, int b) { return rp[a + 1] - rp[a] < rp[b + 1] - rp[b]; });
     std::vector<const int*> d;
-    ldpc_status st = upload_arrays({rp, ci, vp, ve}, &g->dmem, d);
+    ldpc_status st = upload_arrays({rp, ci, vp, ve, ro}, &g->dmem, d);
     if (st != LDPC_OK) {
         delete g;
         return st;
     }
-    g->csr = CsrDev{m, n, d[0], d[1], d[2], d[3]};
+    g->csr = CsrDev{m, n, d[0], d[1], d[2], d[3], d[4]};
     g->cn_tiles = (m + kCnTile - 1) / kCnTile;
     g->vn_tiles = (n + kVnTile - 1) / kVnTile;
     *out = g;

@@ -52,3 +52,18 @@ def test_algorithmic_bytes():
     assert bench.algorithmic_bytes_per_frame_iter(qc) == 8 * qc.edges + 12 * qc.n
     csr = gen.workload_code(1)
     assert bench.algorithmic_bytes_per_frame_iter(csr) == 16 * csr.edges + 12 * csr.n
+
+
+def test_frame_kernel_naming_follows_the_shared_memory_rule():
+    """The bench names the frame-per-CTA kernel for the n = 4096 CSR code (about
+    148 KB of shared memory) and lock-step for QC codes and for a CSR code of
+    60000 edges, whose messages alone exceed the 220 KB limit."""
+    small = gen.workload_code(1)
+    assert bench.frame_schedule_applies(small)
+    assert bench.decoder_kernel_name(small) == "csr_frame_kernel<false>"
+    assert bench.decoder_kernel_name(small, "lockstep") == "bp_decode_kernel<float,CsrDev>"
+    big = gen.random_csr_code(20000, 10000, 3, {6: 10000}, seed=77)
+    assert not bench.frame_schedule_applies(big)
+    qc = gen.workload_code(2, Z=64)
+    assert not bench.frame_schedule_applies(qc)
+    assert bench.decoder_kernel_name(qc) == "bp_decode_kernel<float,QcDev>"
