@@ -20,6 +20,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "cn_math.cuh"
@@ -262,10 +263,6 @@ __device__ __forceinline__ bool grid_sync(Ctrl* bar, int* err, unsigned nblocks,
     return ld_volatile(err) == kErrNone;
 }
 
-__device__ __forceinline__ void prefetch_l2(const void* ptr) {
-    asm volatile("prefetch.global.L2 [%0];" ::"l"(ptr));
-}
-
 __device__ __forceinline__ unsigned syndrome_bit(const unsigned* sb, int row) {
     return (__ldg(sb + (row >> 5)) >> (row & 31)) & 1u;
 }
@@ -282,6 +279,44 @@ constexpr int kQcCnChunk = 2048;         // default checks of one base row per i
 constexpr int kQcVnChunk = 4096;         // default variables of one base column per item (multiple of kQBlock)
 constexpr int kQBlock = 4 * kThreads;    // variables per q partial sum (per warp: 128)
 constexpr int kQParts = 8;               // a frame's q is reduced in this many fixed ranges, by different CTAs
+
+// Bulk L2 prefetch of a window [ptr, ptr + bytes) by the copy engine: one
+// instruction for the whole window, no registers held while the lines arrive.
+// Only its 16-byte-aligned interior is requested (the bulk copy needs 16-byte
+// alignment), so no byte outside the window is touched.
+__device__ __forceinline__ void prefetch_l2_range(const void* ptr, size_t bytes) {
+    const uintptr_t lo = ((uintptr_t)ptr + 15) & ~uintptr_t(15);
+    const uintptr_t hi = ((uintptr_t)ptr + bytes) & ~uintptr_t(15);
+    if (hi > lo) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"((unsigned)(hi - lo)) : "memory");
+}
+
+// Bulk L2 prefetch of a QC check item's windows: per block of the row, the
+// rotated run of positions the item reads, in one or two pieces, of the
+// messages and of the APP values (of Lch in the first iteration).  Issued by
+// one thread: one copy-engine request per piece, no registers held while the
+// lines arrive.  (Prefetching the CTA's next item as well measured slower.)
+template <bool FIRST, typename T>
+__device__ __forceinline__ void qc_cn_prefetch(const QcDev& q, const FrameCtx<T>& fc, int i, int t0, int b0, int d) {
+    const int Z = q.Z;
+    const int len = min(t0 + fc.cn_chunk, Z) - t0;
+    for (int j = 0; j < d; ++j) {
+        int st = t0 + __ldg(q.blk_shift + b0 + j);
+        st = st >= Z ? st - Z : st;
+        const int first = min(len, Z - st);
+        if constexpr (FIRST) {
+            const float* b = fc.llr + (size_t)__ldg(q.blk_col + b0 + j) * Z;
+            prefetch_l2_range(b + st, (size_t)first * sizeof(float));
+            if (len > first) prefetch_l2_range(b, (size_t)(len - first) * sizeof(float));
+        } else {
+            const T* b = fc.c2v + (size_t)(b0 + j) * Z;
+            prefetch_l2_range(b + st, (size_t)first * sizeof(T));
+            if (len > first) prefetch_l2_range(b, (size_t)(len - first) * sizeof(T));
+            const T* a = fc.app + (size_t)__ldg(q.blk_col + b0 + j) * Z;
+            prefetch_l2_range(a + st, (size_t)first * sizeof(T));
+            if (len > first) prefetch_l2_range(a, (size_t)(len - first) * sizeof(T));
+        }
+    }
+}
 
 template <int D, int MODE, bool SYND, bool W, typename T>
 __device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, const FrameCtx<T>& fc, int i, int t0,
@@ -301,25 +336,11 @@ __device__ __forceinline__ bool qc_cn_item(const Params<T>& p, const QcDev& q, c
         vo[j] = __ldg(q.blk_col + b0 + j) * Z;
         mo[j] = (b0 + j) * Z;
     }
-    // L2 prefetch of the item's message windows (one 128-byte line per 32
-    // positions): fire-and-forget requests that hold no registers, so many more
-    // lines are in flight than the loads below could keep.  APP needs none: each
-    // APP value is read by every block of its column and mostly hits in L2.
+    // L2 prefetch of the item's windows: many more lines in flight than the
+    // loads below could keep
 #ifndef LDPC_BOUNDS_CHECK  // the index-checking build issues no unchecked prefetches
     if constexpr (MODE != kModeSynd) {
-        const int len = t_end - t0;
-        for (int off = 32 * (int)threadIdx.x; off < len; off += 32 * kThreads) {
-#pragma unroll
-            for (int j = 0; j < D; ++j) {
-                int pp = t0 + off + sh[j];
-                pp = pp >= Z ? pp - Z : pp;
-                if constexpr (MODE == kModeFirst) {
-                    prefetch_l2(llr + vo[j] + pp);
-                } else {
-                    prefetch_l2(c2v + mo[j] + pp);
-                }
-            }
-        }
+        if (threadIdx.x == 0) qc_cn_prefetch<MODE == kModeFirst, T>(q, fc, i, t0, b0, D);
     }
 #endif
     // checks in flight per thread
@@ -619,10 +640,11 @@ __device__ __forceinline__ void qc_vn_cols(const Params<T>& p, const QcDev& q, c
     if constexpr (sizeof(T) == 4) vec = fc.vec4 != 0;
     const int qb_per_col = (Z + kQBlock - 1) / kQBlock;
 #ifndef LDPC_BOUNDS_CHECK
-    // L2 prefetch of the item's message blocks and channel values (contiguous)
-    for (int off = u0 + 32 * (int)threadIdx.x; off < u_end; off += 32 * kThreads) {
-        prefetch_l2(llr + off);
-        for (int b = 0; b < nd; ++b) prefetch_l2(c2v + __ldg(q.col_blk + cb0 + b) * Z + off);
+    // bulk L2 prefetch of the item's message blocks and channel values (contiguous), by one thread
+    if (threadIdx.x == 0) {
+        prefetch_l2_range(llr + u0, (size_t)(u_end - u0) * sizeof(float));
+        for (int b = 0; b < nd; ++b)
+            prefetch_l2_range(c2v + (size_t)__ldg(q.col_blk + cb0 + b) * Z + u0, (size_t)(u_end - u0) * sizeof(T));
     }
 #endif
     for (int ub = u0; ub < u_end; ub += kQBlock) {
