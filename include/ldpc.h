@@ -112,8 +112,8 @@ typedef struct ldpc_decode_opts {
                                    the first grid-wide wait expect one CTA more than the grid
                                    has, so the waits run out after barrier_timeout_ms and the
                                    call returns LDPC_ERR_TIMEOUT.  Leave 0.                    */
-    int32_t groups;            /* independent CTA groups, 0 = automatic (one CTA of each group
-                                  per SM, at most one group per running frame).  Each group
+    int32_t groups;            /* independent CTA groups, 0 = automatic (two groups per
+                                  resident CTA per SM, at most one group per running frame).  Each group
                                   advances its own frames in lock-step between its own
                                   barriers, and frames that stop are replaced from one shared
                                   queue.  Results are bit-identical for any value.             */
