@@ -91,10 +91,12 @@ typedef struct ldpc_decode_opts {
                                   default 25.  Must be finite and > 0.                         */
     int32_t fp64;              /* 0: FP32 messages (default).  1: FP64 debug mode, which takes
                                   the tanh/atanh rule literally (slow on GB300's FP64 units).  */
-    int32_t max_active_frames; /* frames decoded concurrently (slots), 0 = automatic (all of
-                                  them, at most 1024).  Others wait in a queue and start as
-                                  running frames terminate.  Rounded up to a multiple of the
-                                  group count.                                                */
+    int32_t max_active_frames; /* frames decoded concurrently (slots), 0 = automatic: about
+                                  192 MB of algorithmic traffic (8E + 12n bytes per frame and
+                                  iteration) per CTA group and step, so 48 frames at n = 10^6
+                                  with 8 groups, at most all frames and 1024.  Others wait in a
+                                  queue and start as running frames terminate.  Rounded up to
+                                  a multiple of the group count.                              */
     int32_t grid_ctas;         /* CTAs of the persistent kernel, 0 = all that fit on the GPU;
                                   rounded down to a multiple of the group count.              */
     int32_t trace_iters;       /* record messages of iterations 1..trace_iters (0 = off)      */

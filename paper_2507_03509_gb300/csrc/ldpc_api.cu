@@ -26,6 +26,7 @@ using namespace ldpcgb;
 namespace {
 
 constexpr unsigned long long kBarrierTimeoutNs = 10ull * 1000ull * 1000ull * 1000ull;  // 10 s
+constexpr double kStepBytes = 192e6;  // default algorithmic bytes per group step (frames in flight)
 
 // Upload a set of host int arrays into one device allocation.
 ldpc_status upload_arrays(const std::vector<std::vector<int>>& arrays, void** dmem,
@@ -718,11 +719,22 @@ ldpc_status launch_decode(Workspace& ws, const Job& job, const ldpc_decode_opts&
     int grid = std::min(per_sm * sms, kMaxGrid);
     if (o.grid_ctas > 0) grid = std::min(grid, o.grid_ctas);
     // groups and slots: by default two groups per resident CTA per SM (at most
-    // one per frame) and every frame in a slot.  Measured at n = 1e6 with 32
-    // frames: 8 groups 274 Mbit/s, 4 groups 270, 16 groups 272, 32 groups 268;
-    // fewer frames in flight 212-248.
+    // one per frame).  Measured at n = 1e6 with 32 frames, all in flight: 8 groups
+    // 274 Mbit/s, 4 groups 270, 16 groups 272, 32 groups 268; fewer frames in
+    // flight 212-248.
     int groups = o.groups > 0 ? o.groups : 2 * per_sm;
-    int want_slots = o.max_active_frames > 0 ? o.max_active_frames : frames;
+    int want_slots = o.max_active_frames;
+    if (want_slots <= 0) {
+        // frames in flight: about kStepBytes of algorithmic traffic (8E + 12n per
+        // frame-iteration of the largest code, in FP32) per group step.  Measured at
+        // n = 1e6 with 512 frames and 8 groups: 48 in flight 227.6 Mbit/s, 32: 225.8,
+        // 64: 220.3, 96: 218.9, all 512: 200.4.  Small codes keep many more in flight.
+        double bpf = 1.0;
+        for (int c = 0; c < job.ngraphs; ++c)
+            bpf = std::max(bpf, (8.0 * (double)job.graphs[c]->E + 12.0 * job.graphs[c]->n) * (sizeof(T) / 4.0));
+        const long long per_group = std::max(1LL, (long long)std::ceil(kStepBytes / bpf));
+        want_slots = (int)std::min<long long>(frames, per_group * std::max(1, std::min(groups, kMaxGroups)));
+    }
     want_slots = std::min(std::min(want_slots, job.max_slot_frames), kMaxSlots);
     groups = std::max(1, std::min(std::min(groups, want_slots), std::min(grid, kMaxGroups)));
     const int slots_per_group = (want_slots + groups - 1) / groups;
