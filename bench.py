@@ -92,6 +92,28 @@ def algorithmic_bytes_per_frame_iter(code) -> int:
     return 8 * int(code.edges) + 12 * int(code.n) + csr_index_bytes_per_frame_iter(code)
 
 
+MUFU_PER_SM_CLK = 16  # special-function (exp2, log2, reciprocal) lanes per SM and clock
+
+
+def check_degrees_of(code) -> np.ndarray:
+    """Degree of every check of a CSR or QC code."""
+    if hasattr(code, "shifts"):
+        return np.repeat((np.asarray(code.shifts) >= 0).sum(axis=1).astype(np.int64), code.Z)
+    return code.check_degrees()
+
+
+def mufu_per_frame_iter(code) -> int:
+    """Special-function operations of one check pass (the FP32 check rule): a
+    check of degree d in 3..6 takes d exponentials (r = exp(-|v|)), 3(d - 2)
+    reciprocals (the prefix, suffix and middle boxplus combinations) and d
+    logarithms (the outputs), 5d - 6 in all; the general path for d > 6 takes
+    one combination more (5d - 5); checks of degree 1 and 2 take none (a
+    constant and a copy)."""
+    d = check_degrees_of(code)
+    small = (d >= 3) & (d <= 6)
+    return int((5 * d[small] - 6).sum() + (5 * d[d > 6] - 5).sum())
+
+
 def frame_schedule_applies(code) -> bool:
     """Whether the frame-per-CTA kernel takes a CSR code: 16-bit indices and its
     shared memory (frame, q partials and index lists, 16-byte aligned pieces)
@@ -142,6 +164,20 @@ def measured_traffic(workload_name: str):
         if parts.get("source") == want and parts.get("workload") == workload_name:
             return float(parts["dram_bytes_per_frame_iter"])
     return None
+
+
+def sfu_roof(code, fi_per_launch, kernel_ms, clk, dev):
+    """Secondary roof: special-function operations per launch over the kernel
+    time, against MUFU_PER_SM_CLK x SMs x the SM clock sampled under load (the
+    maximum clock when no sample was taken)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = (clk or {}).get("sm_mhz") or (clk or {}).get("sm_max_mhz") or 2070.0
+    per_fi = mufu_per_frame_iter(code)
+    achieved = fi_per_launch * per_fi / (kernel_ms * 1e-3)
+    peak = MUFU_PER_SM_CLK * sms * mhz * 1e6
+    return {"bound": "sfu", "achieved": achieved, "peak": peak, "unit": "MUFU op/s", "frac": achieved / peak,
+            "mufu_per_frame_iter": per_fi, "sms": sms, "sm_mhz": mhz}
 
 
 def hbm_peak():
@@ -467,6 +503,7 @@ def run_ours(args):
         "gpu_launches": main["launches"],
         "clocks": clk,
     }
+    line["secondary_roofs"] = {"sfu": sfu_roof(code, per_launch_fi, main["kernel_ms"] / main["steps"], clk, dev)}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

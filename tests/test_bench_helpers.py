@@ -67,3 +67,18 @@ def test_frame_kernel_naming_follows_the_shared_memory_rule():
     qc = gen.workload_code(2, Z=64)
     assert not bench.frame_schedule_applies(qc)
     assert bench.decoder_kernel_name(qc) == "bp_decode_kernel<float,QcDev>"
+
+
+def test_mufu_count_follows_the_check_rule():
+    """Special-function operations per check pass, counted by hand: degree 3
+    takes 3 exponentials + 3 reciprocals + 3 logarithms = 9, degree 4 takes
+    4 + 6 + 4 = 14, degree 7 (general path) 7 + 6 + 7 = 30 with its extra
+    combination; degrees 1 and 2 take none."""
+    rowptr = np.array([0, 1, 3, 6, 10, 17], dtype=np.int32)  # degrees 1, 2, 3, 4, 7
+    colidx = np.concatenate([[0], [0, 1], [0, 1, 2], [0, 1, 2, 3], np.arange(7)]).astype(np.int32)
+    code = gen.CSRCode(m=5, n=7, rowptr=rowptr, colidx=colidx)
+    assert bench.mufu_per_frame_iter(code) == 9 + 14 + 30
+    qc = gen.workload_code(2, Z=64)
+    deg = (np.asarray(qc.shifts) >= 0).sum(axis=1)
+    want = int(sum(5 * d - 6 for d in deg if 3 <= d <= 6)) * 64
+    assert bench.mufu_per_frame_iter(qc) == want
