@@ -340,8 +340,11 @@ typedef struct ldpc_wbp ldpc_wbp;
  * base block, in row-major block order (length = nonzero blocks); for a CSR
  * graph one class per edge in CSR order (length = edges); values in
  * [0, n_classes).  checkpoint_every (>= 1): the forward pass keeps the
- * messages of every checkpoint_every-th iteration and the backward pass
- * recomputes the iterations in between (1 = keep all; >= iters = keep none).
+ * messages of every checkpoint_every-th iteration, and the backward pass
+ * recomputes the iterations in between.  The iterations of the last segment
+ * (after the last checkpoint) are kept whole by the forward pass, since the
+ * backward pass needs them first (1 = keep all; >= iters = keep all but the
+ * last).
  * The graph must outlive the plan.  LDPC_ERR_INVALID_ARG on bad sizes or
  * classes. */
 LDPC_API ldpc_status ldpc_wbp_create(const ldpc_graph* graph, int32_t frames, int32_t iters, int32_t n_classes,
@@ -364,7 +367,7 @@ LDPC_API ldpc_status ldpc_wbp_loss(ldpc_wbp* plan, const void* app, const uint8_
  * syndrome and weights, unchanged since): from grad_app = dloss/dAPP
  * [frames][n] writes grad_weights [iters][n_classes] and, if not NULL,
  * grad_llr [frames][n] = dloss/dLch.  LDPC_ERR_INVALID_ARG if the plan keeps
- * checkpoints and no forward has saved them. */
+ * iterations and no forward has saved them. */
 LDPC_API ldpc_status ldpc_wbp_backward(ldpc_wbp* plan, const float* llr, const uint8_t* syndrome,
                                        const void* weights, const void* grad_app, void* grad_weights,
                                        void* grad_llr, void* cuda_stream);

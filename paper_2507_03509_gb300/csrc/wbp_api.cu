@@ -26,6 +26,8 @@ struct ldpc_wbp {
     long long E = 0;
     int nckpt = 0;               // checkpoints kept by the forward pass (iterations every, 2 every, ... < T)
     int nseg = 0;                // recomputed iterations held during the backward pass (every - 1)
+    int k0_last = 0;             // first iteration of the last checkpoint segment
+    int ntail = 0;               // iterations of the last segment kept by the forward pass (T - 1 - k0_last)
     bool saved = false;          // a forward pass has stored checkpoints
     void* tables = nullptr;      // cls | class_ptr | class_slot
     const int* cls = nullptr;
@@ -38,6 +40,7 @@ struct ldpc_wbp {
     char* app_work = nullptr;    // [F][n]
     std::vector<char*> ck_c2v, ck_app;    // [nckpt] of [F][E] / [F][n]
     std::vector<char*> seg_c2v, seg_app;  // [nseg]
+    std::vector<char*> tail_c2v, tail_app;  // [ntail]: iterations k0_last + 1 .. T - 1 from the forward pass
     char* G = nullptr;           // [F][E]
     char* pbuf = nullptr;        // [F][E]
     double* partial = nullptr;   // loss partial sums [loss_blocks]
@@ -163,6 +166,9 @@ struct Runner {
             if (save && k % p->every == 0 && k < p->T) {
                 cdst = (float*)ck_c2v(k / p->every - 1);
                 adst = (float*)ck_app(k / p->every - 1);
+            } else if (save && k > p->k0_last && k < p->T) {  // the last segment, kept whole
+                cdst = (float*)p->tail_c2v[k - p->k0_last - 1];
+                adst = (float*)p->tail_app[k - p->k0_last - 1];
             }
             st = fwd4(w, k, cprev, aprev, cdst, adst, k == p->T ? app_out : nullptr);
             if (st != LDPC_OK) return st;
@@ -188,16 +194,20 @@ struct Runner {
                 const int k0 = sg * every, k1 = std::min((sg + 1) * every, p->T);
                 const float* c0 = k0 == 0 ? nullptr : (const float*)ck_c2v(sg - 1);
                 const float* a0 = k0 == 0 ? nullptr : (const float*)ck_app(sg - 1);
-                for (int k = k0 + 1; k < k1; ++k) {
-                    const float* cp = k - 1 == k0 ? c0 : (const float*)p->seg_c2v[k - 1 - k0 - 1];
-                    const float* ap = k - 1 == k0 ? a0 : (const float*)p->seg_app[k - 1 - k0 - 1];
-                    st = fwd4(w, k, cp, ap, (float*)p->seg_c2v[k - k0 - 1], (float*)p->seg_app[k - k0 - 1], nullptr);
+                // the last segment was kept by the forward pass; the others are recomputed
+                const bool last = sg == nseg_total - 1;
+                const std::vector<char*>& sc = last ? p->tail_c2v : p->seg_c2v;
+                const std::vector<char*>& sa = last ? p->tail_app : p->seg_app;
+                for (int k = k0 + 1; k < k1 && !last; ++k) {
+                    const float* cp = k - 1 == k0 ? c0 : (const float*)sc[k - 1 - k0 - 1];
+                    const float* ap = k - 1 == k0 ? a0 : (const float*)sa[k - 1 - k0 - 1];
+                    st = fwd4(w, k, cp, ap, (float*)sc[k - k0 - 1], (float*)sa[k - k0 - 1], nullptr);
                     if (st != LDPC_OK) return st;
                 }
                 for (int k = k1; k > k0; --k) {
                     a.w = w + (size_t)(k - 1) * p->C;
-                    a.c2v_prev = (const float4*)(k - 1 == k0 ? c0 : (const float*)p->seg_c2v[k - 1 - k0 - 1]);
-                    a.app_prev = (const float4*)(k - 1 == k0 ? a0 : (const float*)p->seg_app[k - 1 - k0 - 1]);
+                    a.c2v_prev = (const float4*)(k - 1 == k0 ? c0 : (const float*)sc[k - 1 - k0 - 1]);
+                    a.app_prev = (const float4*)(k - 1 == k0 ? a0 : (const float*)sa[k - 1 - k0 - 1]);
                     wbp::qc_cn4_kernel<true><<<(unsigned)p->grid_qcn, wbp::kThreads, 0, s>>>(a, code, p->tiles_cn,
                                                                                              p->fpq_cn, p->wpart);
                     LDPC_TRY(cudaGetLastError());
@@ -230,6 +240,9 @@ struct Runner {
             if (save && k % p->every == 0 && k < p->T) {
                 cdst = ck_c2v(k / p->every - 1);
                 adst = ck_app(k / p->every - 1);
+            } else if (save && k > p->k0_last && k < p->T) {  // the last segment, kept whole
+                cdst = (T*)p->tail_c2v[k - p->k0_last - 1];
+                adst = (T*)p->tail_app[k - p->k0_last - 1];
             }
             ldpc_status st = fwd(llr, syn, w, k, cprev, aprev, cdst, adst);
             if (st != LDPC_OK) return st;
@@ -261,17 +274,20 @@ struct Runner {
             const int k0 = sg * every, k1 = std::min((sg + 1) * every, p->T);
             const T* c0 = k0 == 0 ? nullptr : ck_c2v(sg - 1);
             const T* a0 = k0 == 0 ? nullptr : ck_app(sg - 1);
-            // recompute c2v^(k), APP^(k) for k0 < k < k1
-            for (int k = k0 + 1; k < k1; ++k) {
-                const T* cp = k - 1 == k0 ? c0 : (T*)p->seg_c2v[k - 1 - k0 - 1];
-                const T* ap = k - 1 == k0 ? a0 : (T*)p->seg_app[k - 1 - k0 - 1];
-                ldpc_status st = fwd(llr, syn, w, k, cp, ap, (T*)p->seg_c2v[k - k0 - 1], (T*)p->seg_app[k - k0 - 1]);
+            // recompute c2v^(k), APP^(k) for k0 < k < k1; the last segment was kept by the forward pass
+            const bool last = sg == nseg_total - 1;
+            const std::vector<char*>& sc = last ? p->tail_c2v : p->seg_c2v;
+            const std::vector<char*>& sa = last ? p->tail_app : p->seg_app;
+            for (int k = k0 + 1; k < k1 && !last; ++k) {
+                const T* cp = k - 1 == k0 ? c0 : (T*)sc[k - 1 - k0 - 1];
+                const T* ap = k - 1 == k0 ? a0 : (T*)sa[k - 1 - k0 - 1];
+                ldpc_status st = fwd(llr, syn, w, k, cp, ap, (T*)sc[k - k0 - 1], (T*)sa[k - k0 - 1]);
                 if (st != LDPC_OK) return st;
             }
             for (int k = k1; k > k0; --k) {
                 a.w = w + (size_t)(k - 1) * p->C;
-                a.c2v_prev = k - 1 == k0 ? c0 : (T*)p->seg_c2v[k - 1 - k0 - 1];
-                a.app_prev = k - 1 == k0 ? a0 : (T*)p->seg_app[k - 1 - k0 - 1];
+                a.c2v_prev = k - 1 == k0 ? c0 : (T*)sc[k - 1 - k0 - 1];
+                a.app_prev = k - 1 == k0 ? a0 : (T*)sa[k - 1 - k0 - 1];
                 if constexpr (kQc) {
                     wbp::qc_cn_kernel<true, T><<<(unsigned)p->grid_qcn, wbp::kThreads, 0, s>>>(
                         a, code, p->tiles_cn, p->fpc_cn, p->wpart);
@@ -377,6 +393,8 @@ ldpc_status ldpc_wbp_create(const ldpc_graph* graph, int32_t frames, int32_t ite
     p->elem = fp64 ? sizeof(double) : sizeof(float);
     p->nckpt = (iters - 1) / p->every;
     p->nseg = p->every - 1;
+    p->k0_last = ((iters + p->every - 1) / p->every - 1) * p->every;
+    p->ntail = iters - 1 - p->k0_last;
     DeviceGuard guard;
     cudaError_t ce = guard.enter(p->device);
     int sms = 0;
@@ -451,7 +469,7 @@ ldpc_status ldpc_wbp_create(const ldpc_graph* graph, int32_t frames, int32_t ite
     // interleaved plans: Lch copy, syndrome bits, accumulated dloss/dLch
     const size_t s4n = p->x4 ? align_up((size_t)p->F4 * graph->n * 4 * sizeof(float), 256) : 0;
     const size_t s4m = p->x4 ? align_up((size_t)p->F4 * graph->m, 256) : 0;
-    const size_t total = sE + sN + (size_t)p->nckpt * (sE + sN) + (size_t)p->nseg * (sE + sN) + sE + sP + sW +
+    const size_t total = sE + sN + (size_t)p->nckpt * (sE + sN) + (size_t)(p->nseg + p->ntail) * (sE + sN) + sE + sP + sW +
                          align_up((size_t)p->loss_blocks * sizeof(double), 256) + 2 * s4n + s4m;
     if (ce == cudaSuccess) ce = cudaMalloc(&p->buf, total);
     if (ce != cudaSuccess) {
@@ -464,6 +482,7 @@ ldpc_status ldpc_wbp_create(const ldpc_graph* graph, int32_t frames, int32_t ite
     p->app_work = b; b += sN;
     for (int i = 0; i < p->nckpt; ++i) { p->ck_c2v.push_back(b); b += sE; p->ck_app.push_back(b); b += sN; }
     for (int i = 0; i < p->nseg; ++i) { p->seg_c2v.push_back(b); b += sE; p->seg_app.push_back(b); b += sN; }
+    for (int i = 0; i < p->ntail; ++i) { p->tail_c2v.push_back(b); b += sE; p->tail_app.push_back(b); b += sN; }
     p->G = b; b += sE;
     p->pbuf = sP ? b : nullptr; b += sP;
     p->wpart = sW ? (double*)b : nullptr; b += sW;
@@ -531,7 +550,7 @@ ldpc_status ldpc_wbp_backward(ldpc_wbp* p, const float* llr, const uint8_t* synd
                               const void* grad_app, void* grad_weights, void* grad_llr, void* cuda_stream) {
     NvtxRange nvtx("ldpc_wbp_backward");
     if (!p || !llr || !syndrome || !weights || !grad_app || !grad_weights) return LDPC_ERR_INVALID_ARG;
-    if (p->nckpt > 0 && !p->saved) return LDPC_ERR_INVALID_ARG;
+    if ((p->nckpt > 0 || p->ntail > 0) && !p->saved) return LDPC_ERR_INVALID_ARG;
     DeviceGuard guard;
     LDPC_TRY(guard.enter(p->device));
     return dispatch(p, (cudaStream_t)cuda_stream, [&](auto r) {
