@@ -51,7 +51,8 @@ struct ldpc_wbp {
     int fpc_cn = 1, fpc_vn = 1;  // frames per CTA group, check / variable side
     int groups_cn = 1;
     long long grid_qcn = 1, grid_qvn = 1;
-    double* wpart = nullptr;     // [groups_cn][nblk][tiles_cn]
+    double* wpart = nullptr;     // [iters][groups_cn][nblk][tiles_cn]
+    size_t wpart_per = 0;        // doubles of wpart per iteration
     const int* cblk_ptr = nullptr;
     const int* cblk = nullptr;
     // FP32 QC plans: state interleaved by frame quads (wbp_kernels.cuh, Args4);
@@ -208,18 +209,15 @@ struct Runner {
                     a.w = w + (size_t)(k - 1) * p->C;
                     a.c2v_prev = (const float4*)(k - 1 == k0 ? c0 : (const float*)sc[k - 1 - k0 - 1]);
                     a.app_prev = (const float4*)(k - 1 == k0 ? a0 : (const float*)sa[k - 1 - k0 - 1]);
-                    wbp::qc_cn4_kernel<true><<<(unsigned)p->grid_qcn, wbp::kThreads, 0, s>>>(a, code, p->tiles_cn,
-                                                                                             p->fpq_cn, p->wpart);
-                    LDPC_TRY(cudaGetLastError());
-                    wbp::class_reduce_kernel<float><<<p->grid_w, wbp::kThreads, 0, s>>>(
-                        p->wpart, p->groups_cn, p->graph->nblk, p->tiles_cn, p->cblk_ptr, p->cblk, p->C,
-                        gw + (size_t)(k - 1) * p->C);
+                    wbp::qc_cn4_kernel<true><<<(unsigned)p->grid_qcn, wbp::kThreads, 0, s>>>(
+                        a, code, p->tiles_cn, p->fpq_cn, p->wpart + (size_t)(k - 1) * p->wpart_per);
                     LDPC_TRY(cudaGetLastError());
                     wbp::qc_vn4_kernel<wbp::kVnBwd><<<(unsigned)p->grid_qvn, wbp::kThreads, 0, s>>>(a, code,
                                                                                                     p->fpq_vn);
                     LDPC_TRY(cudaGetLastError());
                 }
             }
+            LDPC_TRY(class_reduce_all(gw));
             if (gl) {
                 wbp::unpack4_kernel<<<p->grid_pack, wbp::kThreads, 0, s>>>((const float4*)p->grad4, p->F, p->n, gl);
                 LDPC_TRY(cudaGetLastError());
@@ -290,11 +288,7 @@ struct Runner {
                 a.app_prev = k - 1 == k0 ? a0 : (T*)sa[k - 1 - k0 - 1];
                 if constexpr (kQc) {
                     wbp::qc_cn_kernel<true, T><<<(unsigned)p->grid_qcn, wbp::kThreads, 0, s>>>(
-                        a, code, p->tiles_cn, p->fpc_cn, p->wpart);
-                    LDPC_TRY(cudaGetLastError());
-                    wbp::class_reduce_kernel<T><<<p->grid_w, wbp::kThreads, 0, s>>>(
-                        p->wpart, p->groups_cn, p->graph->nblk, p->tiles_cn, p->cblk_ptr, p->cblk, p->C,
-                        gw + (size_t)(k - 1) * p->C);
+                        a, code, p->tiles_cn, p->fpc_cn, p->wpart + (size_t)(k - 1) * p->wpart_per);
                     LDPC_TRY(cudaGetLastError());
                     wbp::qc_vn_kernel<wbp::kVnBwd, T><<<(unsigned)p->grid_qvn, wbp::kThreads, 0, s>>>(
                         a, code, p->fpc_vn, nullptr);
@@ -310,7 +304,18 @@ struct Runner {
                 LDPC_TRY(cudaGetLastError());
             }
         }
+        if constexpr (kQc) LDPC_TRY(class_reduce_all(gw));
         return LDPC_OK;
+    }
+    // dloss/dw of every iteration and class from the adjoint check passes' per-tile
+    // partials, in one launch once the backward pass is done (QC plans)
+    template <typename G>
+    cudaError_t class_reduce_all(G* gw) const {
+        const unsigned grid = (unsigned)std::min(p->T * p->C, 8192);
+        wbp::class_reduce_kernel<G><<<grid, wbp::kThreads, 0, s>>>(p->wpart, p->wpart_per, p->groups_cn,
+                                                                   p->graph->nblk, p->tiles_cn, p->cblk_ptr,
+                                                                   p->cblk, p->C, p->T, gw);
+        return cudaGetLastError();
     }
 };
 
@@ -465,7 +470,8 @@ ldpc_status ldpc_wbp_create(const ldpc_graph* graph, int32_t frames, int32_t ite
         p->grid_qvn = std::min<long long>((long long)((frames + p->fpc_vn - 1) / p->fpc_vn) * graph->nb, 1LL << 24);
     }
     const size_t sP = qc ? 0 : sE;  // per-edge G * t (CSR plans only)
-    const size_t sW = qc ? align_up((size_t)p->groups_cn * graph->nblk * p->tiles_cn * sizeof(double), 256) : 0;
+    p->wpart_per = qc ? (size_t)p->groups_cn * graph->nblk * p->tiles_cn : 0;
+    const size_t sW = qc ? align_up((size_t)iters * p->wpart_per * sizeof(double), 256) : 0;
     // interleaved plans: Lch copy, syndrome bits, accumulated dloss/dLch
     const size_t s4n = p->x4 ? align_up((size_t)p->F4 * graph->n * 4 * sizeof(float), 256) : 0;
     const size_t s4m = p->x4 ? align_up((size_t)p->F4 * graph->m, 256) : 0;

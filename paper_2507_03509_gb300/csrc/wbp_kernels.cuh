@@ -808,12 +808,16 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 6 : 1) qc_vn_kernel
 }
 
 // dloss/dw_k[cl] = sum over the class's blocks b, the frame groups g and the
-// tiles of wpart (one CTA per class, grid-stride over classes, fixed order).
+// tiles of wpart (one CTA per iteration and class, grid-stride, fixed order).
 template <typename T>
-__global__ void __launch_bounds__(kThreads) class_reduce_kernel(const double* wpart, int groups, int nblk, int tiles,
-                                                                const int* cblk_ptr, const int* cblk, int C, T* gw) {
+__global__ void __launch_bounds__(kThreads) class_reduce_kernel(const double* wpart, size_t per, int groups,
+                                                                int nblk, int tiles, const int* cblk_ptr,
+                                                                const int* cblk, int C, int iters, T* gw) {
+    // one CTA per (iteration, class); iteration it's partials start at wpart + it * per
     __shared__ double sm[kThreads / 32];
-    for (int c = blockIdx.x; c < C; c += gridDim.x) {
+    for (int ic = blockIdx.x; ic < iters * C; ic += gridDim.x) {
+        const int it = ic / C, c = ic - it * C;
+        const double* wp = wpart + (size_t)it * per;
         const int lo = __ldg(cblk_ptr + c), nbk = __ldg(cblk_ptr + c + 1) - lo;
         const long long per_g = (long long)nbk * tiles;
         const long long total = (long long)groups * per_g;
@@ -822,10 +826,10 @@ __global__ void __launch_bounds__(kThreads) class_reduce_kernel(const double* wp
             const int g = (int)(i / per_g);
             const int r = (int)(i - (long long)g * per_g);
             const int bi = r / tiles, tile = r - bi * tiles;
-            acc += wpart[((size_t)g * nblk + __ldg(cblk + lo + bi)) * tiles + tile];
+            acc += wp[((size_t)g * nblk + __ldg(cblk + lo + bi)) * tiles + tile];
         }
         const double s = block_sum(acc, sm);
-        if (threadIdx.x == 0) gw[c] = (T)s;
+        if (threadIdx.x == 0) gw[(size_t)it * C + c] = (T)s;
     }
 }
 
