@@ -420,15 +420,18 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads) loss_kernel(const T* app, const unsigned char* x, long long total,
                                                         double scale, T* grad_app, double* partial) {
     __shared__ double sm[kThreads / 32];
-    double acc = 0.0;
+    // each thread sums its elements in the plan's type and widens once: FP64
+    // additions are scarce on this part, and the FP32 loss is a diagnostic (the
+    // gradient below does not depend on it)
+    T acc = T(0);
     for (long long id = (long long)blockIdx.x * kThreads + threadIdx.x; id < total;
          id += (long long)gridDim.x * kThreads) {
         const T sx = __ldg(x + id) ? T(-1) : T(1);
         const T z = -sx * app[id];
-        acc += (double)softplus_t(z);
+        acc += softplus_t(z);
         if (grad_app) grad_app[id] = -sx * sigmoid_t(z) * (T)scale;
     }
-    const double s = block_sum(acc, sm);
+    const double s = block_sum((double)acc, sm);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
