@@ -344,7 +344,9 @@ typedef struct ldpc_wbp ldpc_wbp;
  * recomputes the iterations in between.  The iterations of the last segment
  * (after the last checkpoint) are kept whole by the forward pass, since the
  * backward pass needs them first (1 = keep all; >= iters = keep all but the
- * last).
+ * last).  FP32 QC plans own a second CUDA stream, on which the backward pass
+ * recomputes one segment while the adjoint of the next runs on the caller's
+ * stream; it joins the caller's stream before the call's work ends.
  * The graph must outlive the plan.  LDPC_ERR_INVALID_ARG on bad sizes or
  * classes. */
 LDPC_API ldpc_status ldpc_wbp_create(const ldpc_graph* graph, int32_t frames, int32_t iters, int32_t n_classes,

@@ -40,7 +40,10 @@ struct ldpc_wbp {
     char* app_work = nullptr;    // [F][n]
     std::vector<char*> ck_c2v, ck_app;    // [nckpt] of [F][E] / [F][n]
     std::vector<char*> seg_c2v, seg_app;  // [nseg]
-    std::vector<char*> tail_c2v, tail_app;  // [ntail]: iterations k0_last + 1 .. T - 1 from the forward pass
+    std::vector<char*> tail_c2v, tail_app;  // [max(ntail, nseg)]: iterations k0_last + 1 .. T - 1 from the
+                                            // forward pass; later the second recompute buffer set
+    cudaStream_t s2 = nullptr;              // interleaved plans: the backward pass's recompute stream
+    std::vector<cudaEvent_t> ev;            // [1 + 2 * segments]: ordering between the two streams
     char* G = nullptr;           // [F][E]
     char* pbuf = nullptr;        // [F][E]
     double* partial = nullptr;   // loss partial sums [loss_blocks]
@@ -140,6 +143,10 @@ struct Runner {
     // frame-major buffer) receives APP^(k) instead of app_dst when given
     ldpc_status fwd4(const float* w, int k, const float* c2v_prev, const float* app_prev, float* c2v_dst,
                      float* app_dst, float* app_rows) const {
+        return fwd4_on(s, w, k, c2v_prev, app_prev, c2v_dst, app_dst, app_rows);
+    }
+    ldpc_status fwd4_on(cudaStream_t st, const float* w, int k, const float* c2v_prev, const float* app_prev,
+                        float* c2v_dst, float* app_dst, float* app_rows) const {
         if constexpr (kQc) {
             wbp::Args4 a = base4();
             a.w = w + (size_t)(k - 1) * p->C;
@@ -148,10 +155,10 @@ struct Runner {
             a.c2v_out = (float4*)c2v_dst;
             a.app_out = app_rows ? nullptr : (float4*)app_dst;
             a.app_rows = app_rows;
-            wbp::qc_cn4_kernel<false><<<(unsigned)p->grid_qcn, wbp::kThreads, 0, s>>>(a, code, p->tiles_cn,
-                                                                                       p->fpq_cn, nullptr);
+            wbp::qc_cn4_kernel<false><<<(unsigned)p->grid_qcn, wbp::kThreads, 0, st>>>(a, code, p->tiles_cn,
+                                                                                        p->fpq_cn, nullptr);
             LDPC_TRY(cudaGetLastError());
-            wbp::qc_vn4_kernel<wbp::kVnFwd><<<(unsigned)p->grid_qvn, wbp::kThreads, 0, s>>>(a, code, p->fpq_vn);
+            wbp::qc_vn4_kernel<wbp::kVnFwd><<<(unsigned)p->grid_qvn, wbp::kThreads, 0, st>>>(a, code, p->fpq_vn);
             LDPC_TRY(cudaGetLastError());
         }
         return LDPC_OK;
@@ -190,20 +197,52 @@ struct Runner {
             wbp::qc_vn4_kernel<wbp::kVnSeed><<<(unsigned)p->grid_qvn, wbp::kThreads, 0, s>>>(a, code, p->fpq_vn);
             LDPC_TRY(cudaGetLastError());
             const int every = p->every;
-            const int nseg_total = (p->T + every - 1) / every;
-            for (int sg = nseg_total - 1; sg >= 0; --sg) {
+            const int L = (p->T + every - 1) / every - 1;  // the last segment
+            // Segment sg works in buffer set A (the kept tail) if L - sg is even, else in set B (the
+            // recompute buffers).  The recomputation of segment sg - 1 runs on the second stream
+            // while segment sg's adjoint runs on the caller's; recomputing segment sg - 2, which
+            // reuses segment sg's set, waits for that adjoint.  No result depends on this overlap.
+            const bool overlap = p->s2 != nullptr && (int)p->ev.size() >= 2 * (L + 1) + 1;
+            cudaStream_t rs = overlap ? p->s2 : s;
+            auto set_c = [&](int sg) -> const std::vector<char*>& { return (L - sg) % 2 == 0 ? p->tail_c2v : p->seg_c2v; };
+            auto set_a = [&](int sg) -> const std::vector<char*>& { return (L - sg) % 2 == 0 ? p->tail_app : p->seg_app; };
+            auto recompute = [&](int sg) -> ldpc_status {
                 const int k0 = sg * every, k1 = std::min((sg + 1) * every, p->T);
                 const float* c0 = k0 == 0 ? nullptr : (const float*)ck_c2v(sg - 1);
                 const float* a0 = k0 == 0 ? nullptr : (const float*)ck_app(sg - 1);
-                // the last segment was kept by the forward pass; the others are recomputed
-                const bool last = sg == nseg_total - 1;
-                const std::vector<char*>& sc = last ? p->tail_c2v : p->seg_c2v;
-                const std::vector<char*>& sa = last ? p->tail_app : p->seg_app;
-                for (int k = k0 + 1; k < k1 && !last; ++k) {
+                const std::vector<char*>& sc = set_c(sg);
+                const std::vector<char*>& sa = set_a(sg);
+                for (int k = k0 + 1; k < k1; ++k) {
                     const float* cp = k - 1 == k0 ? c0 : (const float*)sc[k - 1 - k0 - 1];
                     const float* ap = k - 1 == k0 ? a0 : (const float*)sa[k - 1 - k0 - 1];
-                    st = fwd4(w, k, cp, ap, (float*)sc[k - k0 - 1], (float*)sa[k - k0 - 1], nullptr);
-                    if (st != LDPC_OK) return st;
+                    const ldpc_status s3 =
+                        fwd4_on(rs, w, k, cp, ap, (float*)sc[k - k0 - 1], (float*)sa[k - k0 - 1], nullptr);
+                    if (s3 != LDPC_OK) return s3;
+                }
+                if (overlap) LDPC_TRY(cudaEventRecord(p->ev[1 + 2 * sg], rs));  // recomputed
+                return LDPC_OK;
+            };
+            if (overlap) {
+                LDPC_TRY(cudaEventRecord(p->ev[0], s));  // packed inputs and the seed are in place
+                LDPC_TRY(cudaStreamWaitEvent(rs, p->ev[0], 0));
+            }
+            if (L >= 1 && overlap) {
+                st = recompute(L - 1);
+                if (st != LDPC_OK) return st;
+            }
+            for (int sg = L; sg >= 0; --sg) {
+                const int k0 = sg * every, k1 = std::min((sg + 1) * every, p->T);
+                const float* c0 = k0 == 0 ? nullptr : (const float*)ck_c2v(sg - 1);
+                const float* a0 = k0 == 0 ? nullptr : (const float*)ck_app(sg - 1);
+                const std::vector<char*>& sc = set_c(sg);
+                const std::vector<char*>& sa = set_a(sg);
+                if (sg < L) {
+                    if (overlap) {
+                        LDPC_TRY(cudaStreamWaitEvent(s, p->ev[1 + 2 * sg], 0));
+                    } else {
+                        st = recompute(sg);  // the last segment was kept by the forward pass
+                        if (st != LDPC_OK) return st;
+                    }
                 }
                 for (int k = k1; k > k0; --k) {
                     a.w = w + (size_t)(k - 1) * p->C;
@@ -215,6 +254,12 @@ struct Runner {
                     wbp::qc_vn4_kernel<wbp::kVnBwd><<<(unsigned)p->grid_qvn, wbp::kThreads, 0, s>>>(a, code,
                                                                                                     p->fpq_vn);
                     LDPC_TRY(cudaGetLastError());
+                }
+                if (overlap && sg >= 2) {  // segment sg - 2 reuses this segment's buffers
+                    LDPC_TRY(cudaEventRecord(p->ev[2 + 2 * sg], s));
+                    LDPC_TRY(cudaStreamWaitEvent(rs, p->ev[2 + 2 * sg], 0));
+                    st = recompute(sg - 2);
+                    if (st != LDPC_OK) return st;
                 }
             }
             LDPC_TRY(class_reduce_all(gw));
@@ -330,6 +375,10 @@ ldpc_status dispatch(ldpc_wbp* p, cudaStream_t s, Fn&& fn) {
 }
 
 void release(ldpc_wbp* p) {
+    for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+    p->ev.clear();
+    if (p->s2) cudaStreamDestroy(p->s2);
+    p->s2 = nullptr;
     if (p->tables) cudaFree(p->tables);
     if (p->buf) cudaFree(p->buf);
     p->tables = nullptr;
@@ -400,6 +449,7 @@ ldpc_status ldpc_wbp_create(const ldpc_graph* graph, int32_t frames, int32_t ite
     p->nseg = p->every - 1;
     p->k0_last = ((iters + p->every - 1) / p->every - 1) * p->every;
     p->ntail = iters - 1 - p->k0_last;
+    const int ntailbuf = std::max(p->ntail, p->nseg);  // the tail set also serves as a recompute set
     DeviceGuard guard;
     cudaError_t ce = guard.enter(p->device);
     int sms = 0;
@@ -475,7 +525,7 @@ ldpc_status ldpc_wbp_create(const ldpc_graph* graph, int32_t frames, int32_t ite
     // interleaved plans: Lch copy, syndrome bits, accumulated dloss/dLch
     const size_t s4n = p->x4 ? align_up((size_t)p->F4 * graph->n * 4 * sizeof(float), 256) : 0;
     const size_t s4m = p->x4 ? align_up((size_t)p->F4 * graph->m, 256) : 0;
-    const size_t total = sE + sN + (size_t)p->nckpt * (sE + sN) + (size_t)(p->nseg + p->ntail) * (sE + sN) + sE + sP + sW +
+    const size_t total = sE + sN + (size_t)p->nckpt * (sE + sN) + (size_t)(p->nseg + ntailbuf) * (sE + sN) + sE + sP + sW +
                          align_up((size_t)p->loss_blocks * sizeof(double), 256) + 2 * s4n + s4m;
     if (ce == cudaSuccess) ce = cudaMalloc(&p->buf, total);
     if (ce != cudaSuccess) {
@@ -488,7 +538,7 @@ ldpc_status ldpc_wbp_create(const ldpc_graph* graph, int32_t frames, int32_t ite
     p->app_work = b; b += sN;
     for (int i = 0; i < p->nckpt; ++i) { p->ck_c2v.push_back(b); b += sE; p->ck_app.push_back(b); b += sN; }
     for (int i = 0; i < p->nseg; ++i) { p->seg_c2v.push_back(b); b += sE; p->seg_app.push_back(b); b += sN; }
-    for (int i = 0; i < p->ntail; ++i) { p->tail_c2v.push_back(b); b += sE; p->tail_app.push_back(b); b += sN; }
+    for (int i = 0; i < ntailbuf; ++i) { p->tail_c2v.push_back(b); b += sE; p->tail_app.push_back(b); b += sN; }
     p->G = b; b += sE;
     p->pbuf = sP ? b : nullptr; b += sP;
     p->wpart = sW ? (double*)b : nullptr; b += sW;
@@ -501,6 +551,24 @@ ldpc_status ldpc_wbp_create(const ldpc_graph* graph, int32_t frames, int32_t ite
     p->grid_cn = grid_for((long long)frames * graph->m, sms);
     p->grid_vn = grid_for((long long)frames * graph->n, sms);
     p->grid_w = std::min(n_classes, sms * 16);
+    if (p->x4) {
+        // the backward pass recomputes the next segment on a stream of its own while the current
+        // segment's adjoint runs; without them it runs everything on the caller's stream
+        const int segments = (iters + p->every - 1) / p->every;
+        bool ok = cudaStreamCreateWithFlags(&p->s2, cudaStreamNonBlocking) == cudaSuccess;
+        for (int i = 0; ok && i < 1 + 2 * segments; ++i) {
+            cudaEvent_t e = nullptr;
+            ok = cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+            if (ok) p->ev.push_back(e);
+        }
+        if (!ok) {
+            for (cudaEvent_t e : p->ev) cudaEventDestroy(e);
+            p->ev.clear();
+            if (p->s2) cudaStreamDestroy(p->s2);
+            p->s2 = nullptr;
+            cudaGetLastError();
+        }
+    }
     *out = p;
     return LDPC_OK;
 }
