@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--slots", type=int, default=0, help="max_active_frames (0 = automatic)")
     ap.add_argument("--grid", type=int, default=0, help="grid_ctas (0 = all that fit)")
     ap.add_argument("--groups", type=int, default=0, help="independent CTA groups (0 = automatic)")
-    ap.add_argument("--schedule", default="auto", choices=["auto", "lockstep", "dataflow", "frame"],
+    ap.add_argument("--schedule", default="auto", choices=["auto", "lockstep", "dataflow", "frame", "frame_pair"],
                     help="decode schedule (auto: frame per CTA for small CSR codes, lock-step otherwise)")
     ap.add_argument("--flow-lag", type=int, default=0, help="dataflow schedule lag (0 = default)")
     ap.add_argument("--compare-steps", type=int, default=2, help="timed steps of each fixed-iteration rule")
@@ -128,13 +128,16 @@ def frame_schedule_applies(code) -> bool:
     return total <= 220 * 1024
 
 
-def decoder_kernel_name(code, schedule="auto") -> str:
-    """The decode kernel a decode of this code runs (FP32)."""
+def decoder_kernel_name(code, schedule="auto", frames=None, sms=152) -> str:
+    """The decode kernel a decode of this code runs (FP32).  Automatic
+    selection takes a CTA pair per frame when every frame gets its own pair at
+    once (taken here as 2 x frames <= SMs)."""
     qc = hasattr(code, "shifts")
     if qc and schedule == "dataflow":
         return "bp_flow_kernel<float>"
-    if not qc and schedule in ("auto", "frame") and frame_schedule_applies(code):
-        return "csr_frame_kernel<false>"
+    if not qc and schedule in ("auto", "frame", "frame_pair") and frame_schedule_applies(code):
+        pair = schedule == "frame_pair" or (schedule == "auto" and frames is not None and 2 * frames <= sms)
+        return "csr_frame_kernel<false,%d>" % (2 if pair else 1)
     return "bp_decode_kernel<float,%s>" % ("QcDev" if qc else "CsrDev")
 
 
@@ -502,7 +505,8 @@ def run_ours(args):
                      "frac": achieved / peak, "peak_source": peak_src,
                      "traffic": (traffic_fi * per_launch_fi) if traffic_fi else None,
                      "algorithmic_bytes_per_launch": per_launch_fi * B,
-                     "kernel": decoder_kernel_name(code, args.schedule),
+                     "kernel": decoder_kernel_name(code, args.schedule, int(frames.llr.shape[0]),
+                                                   torch.cuda.get_device_properties(dev).multi_processor_count),
                      "kernel_ms_per_launch": main["kernel_ms"] / main["steps"]},
         "cpu_baseline": cpu,
         "e2e": e2e,
@@ -622,7 +626,7 @@ def l2_resident(ldpc, dev, steps=10):
     out = {"workload": wl["name"], "frames": int(fr.llr.shape[0]), "n": code.n, "edges": int(code.edges),
            "max_iter": wl["max_iter"], "bytes_per_frame_iter": B, "l2_copy_gbs_measured": l2, "rules": {},
            "schedules": {}}
-    for sched in ("auto", "lockstep", "frame"):
+    for sched in ("auto", "lockstep", "frame", "frame_pair"):
         res = {}
         for rule in ("pce_vnr", "pce", "none"):
             for _ in range(3):

@@ -120,8 +120,9 @@ typedef struct ldpc_decode_opts {
                                   barriers, and frames that stop are replaced from one shared
                                   queue.  Results are bit-identical for any value.             */
     int32_t schedule;          /* LDPC_SCHEDULE_*: how the persistent kernel orders its work.
-                                  0 = automatic (frame per CTA where it applies, lock-step
-                                  otherwise).  Results are bit-identical for every schedule.  */
+                                  0 = automatic (frame per CTA pair or per CTA where it
+                                  applies, lock-step otherwise).  Results are bit-identical
+                                  for every schedule.                                          */
     int32_t flow_lag;          /* dataflow schedule only: how many slot-steps after a frame's
                                   check pass its variable pass is scheduled (0 = 2; at most the
                                   number of frames in flight).                                */
@@ -133,8 +134,10 @@ typedef struct ldpc_decode_opts {
 } ldpc_decode_opts;
 
 /* Values of ldpc_decode_opts.schedule.  Automatic selection takes frame per
- * CTA for one small CSR code in FP32 (on GB300 at n = 4096 with 64 frames it
- * ran 1.9-2.6x faster than lock-step) and lock-step otherwise: at n = 10^6
+ * CTA pair (when every frame gets its own pair at once) or frame per CTA for
+ * one small CSR code in FP32 (on GB300 at n = 4096 with 64 frames they ran
+ * 2-3x faster than lock-step, the pair 3-4 % faster than one CTA) and
+ * lock-step otherwise: at n = 10^6
  * with 32 frames the dataflow schedule measured half the lock-step rate (its
  * items wait on each frame's decision, a join over all of the frame's check
  * items, every iteration). */
@@ -156,6 +159,15 @@ typedef struct ldpc_decode_opts {
  * max_active_frames and groups do not apply.  Asking for it where it does not
  * apply returns LDPC_ERR_INVALID_ARG. */
 #define LDPC_SCHEDULE_FRAME 3
+/* Frame per cluster (where frame per CTA applies): a thread-block cluster of
+ * two CTAs on two SMs decodes each frame, each CTA running half of the checks
+ * and variables and storing the messages and APP values the other one reads
+ * into its shared memory (distributed shared memory), with cluster barriers
+ * between the passes.  grid_ctas counts CTAs (two per frame in flight).
+ * Automatic selection takes it over frame per CTA when every frame gets its
+ * own pair at once.  Asking for it where it does not apply returns
+ * LDPC_ERR_INVALID_ARG. */
+#define LDPC_SCHEDULE_FRAME_PAIR 4
 
 /* Fill *opts with the defaults (vnr_first_iter 2, clamp 25, FP32, automatic
  * concurrency and grid, no trace, no stats).  NULL is ignored. */

@@ -19,6 +19,19 @@
 // FP64 work is scarce on this part (about two FP64 operations per clock per
 // SM), so only the eight range warps sum q and only warp 0 takes the decision;
 // the other warps wait at the CTA barrier.
+//
+// Frame per cluster (NC = 2): when there are fewer frames than SMs, a
+// thread-block cluster of two CTAs on two SMs decodes each frame.  Both CTAs
+// hold the whole frame; CTA r runs the runs of 32 checks of the degree-sorted
+// order with index mod 2 = r and the variables of the 1024-variable blocks b
+// with b mod 2 = r.  A
+// new message whose variable lies in the other CTA's blocks, and every APP
+// value, is also stored into the other CTA's copy through distributed shared
+// memory (st.shared::cluster: stores only, so no pass waits on a remote load),
+// and cluster barriers separate the passes.  Both CTAs then read identical
+// copies, so they compute the same q^(k) (its per-warp partials are formed
+// from the shared APP copy, in the variable pass's order) and take the same
+// decisions in lock-step; CTA 0 alone writes the frame's outputs.
 #pragma once
 
 #include "bp_kernels.cuh"
@@ -28,6 +41,39 @@ namespace ldpcgb {
 
 constexpr int kFrameThreads = 1024;
 constexpr int kFrameVirt = kFrameThreads / kThreads;  // virtual 256-thread CTAs per frame CTA
+// frame per cluster: variable v belongs to CTA (v >> kPairShift) & 1, one variable per thread
+constexpr int kPairShift = 10;
+static_assert(kVnTile == (1 << kPairShift) && kFrameThreads == (1 << kPairShift), "pair blocks are q tiles");
+
+// ---- thread-block cluster primitives (inline PTX, sm_90 and later) ----
+__device__ __forceinline__ unsigned cluster_ctarank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// address, in the cluster's shared window, of this CTA's shared variable p in CTA `rank`
+__device__ __forceinline__ unsigned dsmem_addr(const void* p, unsigned rank) {
+    const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void dsmem_st_f32(unsigned addr, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+__device__ __forceinline__ void dsmem_st_s32(unsigned addr, int v) {
+    asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void dsmem_or_b32(unsigned addr, unsigned v) {
+    unsigned old;
+    asm volatile("atom.shared::cluster.or.b32 %0, [%1], %2;" : "=r"(old) : "r"(addr), "r"(v) : "memory");
+    (void)old;
+}
+// All threads of every CTA of the cluster: the cluster's shared-memory writes
+// before it are visible to every thread's reads after it.
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 
 __host__ __device__ constexpr long long frame_round(long long x, long long a) { return (x + a - 1) / a * a; }
 
@@ -60,14 +106,19 @@ __host__ __device__ constexpr size_t frame_smem_bytes(long long E, int n, int m,
 }
 
 // One check of degree D (compile time) from shared memory: the arithmetic of csr_cn_check.
-template <int D, bool W>
+// NC = 2: a message whose variable belongs to the other CTA of the pair is
+// also stored into that CTA's copy (peer_c2v: its c2v array in the cluster window).
+template <int D, bool W, int NC>
 __device__ __forceinline__ bool smem_cn_check(const Params<float>& p, const FrameCtx<float>& fc, int mode,
                                               bool want_synd, unsigned sbit, int e0, const unsigned short* col,
-                                              const float* app, const float* lch, float* c2v) {
+                                              const float* app, const float* lch, float* c2v, unsigned peer_c2v,
+                                              unsigned rank) {
     float a[D], o[D];
+    int vis[D];
 #pragma unroll
     for (int j = 0; j < D; ++j) {
         const int vi = (int)LDPC_IX(p.ctrl, col[e0 + j], fc.n, kIxCsrVar);
+        vis[j] = vi;
         o[j] = 0.0f;
         if (mode == kModeFirst) {
             a[j] = lch[vi];
@@ -89,16 +140,21 @@ __device__ __forceinline__ bool smem_cn_check(const Params<float>& p, const Fram
     for (int j = 0; j < D; ++j) v[j] = clampm(a[j] - o[j], p.lmax);
     cn_core<D>(v, sbit, p.lmax, out);
 #pragma unroll
-    for (int j = 0; j < D; ++j) c2v[e0 + j] = weighted<W>(p, fc, out[j], e0 + j);
+    for (int j = 0; j < D; ++j) {
+        const float msg = weighted<W>(p, fc, out[j], e0 + j);
+        c2v[e0 + j] = msg;
+        if constexpr (NC == 2)
+            if ((unsigned)((vis[j] >> kPairShift) & 1) != rank) dsmem_st_f32(peer_c2v + 4u * (unsigned)(e0 + j), msg);
+    }
     return unsat;
 }
 
 // Any degree (0 and > 6): the arithmetic of csr_cn_check_n.
-template <bool W>
+template <bool W, int NC>
 __device__ __noinline__ bool smem_cn_check_n(const Params<float>& p, const FrameCtx<float>& fc, int mode,
                                              bool want_synd, unsigned sbit, int e0, int d,
                                              const unsigned short* col, const float* app, const float* lch,
-                                             float* c2v) {
+                                             float* c2v, unsigned peer_c2v, unsigned rank) {
     if (d == 0) return want_synd && sbit != 0u;
     float v[kMaxDeg], out[kMaxDeg];
     unsigned pr = sbit;
@@ -117,13 +173,21 @@ __device__ __noinline__ bool smem_cn_check_n(const Params<float>& p, const Frame
     const bool unsat = want_synd && pr != 0u;
     if (mode == kModeSynd) return unsat;
     cn_core_n(v, d, sbit, p.lmax, out);
-    for (int j = 0; j < d; ++j) c2v[e0 + j] = weighted<W>(p, fc, out[j], e0 + j);
+    for (int j = 0; j < d; ++j) {
+        const float msg = weighted<W>(p, fc, out[j], e0 + j);
+        c2v[e0 + j] = msg;
+        if constexpr (NC == 2) {
+            const int vi = (int)LDPC_IX(p.ctrl, col[e0 + j], fc.n, kIxCsrVar);
+            if ((unsigned)((vi >> kPairShift) & 1) != rank) dsmem_st_f32(peer_c2v + 4u * (unsigned)(e0 + j), msg);
+        }
+    }
     return unsat;
 }
 
-template <bool W>
+template <bool W, int NC>
 __global__ void __launch_bounds__(kFrameThreads, 1) csr_frame_kernel(Params<float> p, CodeInfo<CsrDev> ci,
                                                                       FrameSmem L) {
+    static_assert(NC == 1 || NC == 2, "one CTA or a pair per frame");
     extern __shared__ __align__(16) unsigned char smem_frame[];
     double* part = (double*)(smem_frame + L.part);      // [nqb * kWarps] q partials of APP^(k)
     double* part0 = (double*)(smem_frame + L.part0);    // [nqb * kWarps] the same for q^(0)
@@ -142,6 +206,15 @@ __global__ void __launch_bounds__(kFrameThreads, 1) csr_frame_kernel(Params<floa
     const CsrDev& g = ci.code;
     const int n = ci.n, m = ci.m;
     const long long E = ci.E;
+    // the pair's other CTA: its copies of c2v, APP, the syndrome flags and the frame number
+    const unsigned rank = NC == 2 ? cluster_ctarank() : 0u;
+    unsigned peer_c2v = 0, peer_app = 0, peer_unsat = 0, peer_frame = 0;
+    if constexpr (NC == 2) {
+        peer_c2v = dsmem_addr(c2v, rank ^ 1u);
+        peer_app = dsmem_addr(app, rank ^ 1u);
+        peer_unsat = dsmem_addr(s_unsat, rank ^ 1u);
+        peer_frame = dsmem_addr(&s_frame, rank ^ 1u);
+    }
     // the code's index lists, once per CTA (values < 2^16: checked by the launcher)
     for (long long e = tid; e < E; e += kFrameThreads) {
         col[e] = (unsigned short)__ldg(g.col_idx + e);
@@ -153,10 +226,16 @@ __global__ void __launch_bounds__(kFrameThreads, 1) csr_frame_kernel(Params<floa
     const int npart = ci.nqb * kWarps;
     const int per = (npart + kQParts - 1) / kQParts;
     const int vt = tid & (kThreads - 1);  // thread of the virtual 256-thread CTA
+    // this CTA's checks: runs of 32 in the degree-sorted order, alternating between the CTAs of a pair
+    const int c_first = (warp * NC + (int)rank) * 32 + lane, c_step = NC * kFrameThreads;
 
     for (;;) {
-        if (tid == 0) s_frame = atomicAdd(&p.ctrl->next_frame, 1);
-        __syncthreads();
+        if (tid == 0 && rank == 0) {
+            const int nf = atomicAdd(&p.ctrl->next_frame, 1);
+            s_frame = nf;
+            if constexpr (NC == 2) dsmem_st_s32(peer_frame, nf);
+        }
+        if constexpr (NC == 2) cluster_barrier(); else __syncthreads();
         const int f = s_frame;
         if (f >= p.frames) break;
         FrameCtx<float> fc = frame_ctx(p, ci, 0, f);
@@ -170,28 +249,59 @@ __global__ void __launch_bounds__(kFrameThreads, 1) csr_frame_kernel(Params<floa
             const bool want_synd = k >= 1 && (p.rule != kRuleNone || k >= p.max_iter);
             if constexpr (W) fc.wrow = weight_row(p, k);
             bool unsat = false;
-            for (int i = tid; i < m; i += kFrameThreads) {  // checks by degree: warps run one degree's code
+            for (int i = c_first; i < m; i += c_step) {  // checks by degree: warps run one degree's code
                 const int row = rord[i];
                 const int e0 = rptr[row];
                 const int d = (int)rptr[row + 1] - e0;
                 const unsigned sbit = (sb[row >> 5] >> (row & 31)) & 1u;
+#define LDPC_FRAME_CHECK(D) \
+    unsat |= smem_cn_check<D, W, NC>(p, fc, mode, want_synd, sbit, e0, col, app, lch, c2v, peer_c2v, rank)
                 switch (d) {
-                    case 1: unsat |= smem_cn_check<1, W>(p, fc, mode, want_synd, sbit, e0, col, app, lch, c2v); break;
-                    case 2: unsat |= smem_cn_check<2, W>(p, fc, mode, want_synd, sbit, e0, col, app, lch, c2v); break;
-                    case 3: unsat |= smem_cn_check<3, W>(p, fc, mode, want_synd, sbit, e0, col, app, lch, c2v); break;
-                    case 4: unsat |= smem_cn_check<4, W>(p, fc, mode, want_synd, sbit, e0, col, app, lch, c2v); break;
-                    case 5: unsat |= smem_cn_check<5, W>(p, fc, mode, want_synd, sbit, e0, col, app, lch, c2v); break;
-                    case 6: unsat |= smem_cn_check<6, W>(p, fc, mode, want_synd, sbit, e0, col, app, lch, c2v); break;
+                    case 1: LDPC_FRAME_CHECK(1); break;
+                    case 2: LDPC_FRAME_CHECK(2); break;
+                    case 3: LDPC_FRAME_CHECK(3); break;
+                    case 4: LDPC_FRAME_CHECK(4); break;
+                    case 5: LDPC_FRAME_CHECK(5); break;
+                    case 6: LDPC_FRAME_CHECK(6); break;
                     default:
-                        unsat |= smem_cn_check_n<W>(p, fc, mode, want_synd, sbit, e0, d, col, app, lch, c2v);
+                        unsat |= smem_cn_check_n<W, NC>(p, fc, mode, want_synd, sbit, e0, d, col, app, lch, c2v,
+                                                        peer_c2v, rank);
                         break;
                 }
+#undef LDPC_FRAME_CHECK
             }
-            if (want_synd && __any_sync(0xffffffffu, unsat) && lane == 0) atomicOr(&s_unsat[k & 1], 1);
-            __syncthreads();
+            if (want_synd && __any_sync(0xffffffffu, unsat) && lane == 0) {
+                atomicOr(&s_unsat[k & 1], 1);
+                if constexpr (NC == 2) dsmem_or_b32(peer_unsat + 4u * (unsigned)(k & 1), 1u);
+            }
+            const bool with_q0 = k == 1 && p.vnr_first_iter <= 1;
+            if constexpr (NC == 2) {
+                // q partials of APP^(k) (and of Lch for q^(0)) from this CTA's full APP copy:
+                // slot tile * kWarps + w sums, per lane, the tile's variables
+                // tile * kVnTile + c * kThreads + 32 w + lane for c = 0 .. kVPT - 1 in order,
+                // exactly as the variable pass of the one-CTA schedule does
+                if (k >= 1) {
+                    for (int sl = warp; sl < npart; sl += kFrameThreads / 32) {
+                        const int tile = sl / kWarps, wv = sl - tile * kWarps;
+                        float acc = 0.0f, acc0 = 0.0f;
+#pragma unroll
+                        for (int c = 0; c < kVPT; ++c) {
+                            const int v = tile * kVnTile + c * kThreads + wv * 32 + lane;
+                            if (v < n && (int)vptr[v + 1] - (int)vptr[v] > 1) {
+                                acc += fabsf(app[v]);
+                                acc0 += fabsf(lch[v]);
+                            }
+                        }
+                        warp_sum_to(acc, part + sl);
+                        if (with_q0) warp_sum_to(acc0, part0 + sl);
+                    }
+                }
+                cluster_barrier();  // both CTAs' messages and syndrome flags are in place
+            } else {
+                __syncthreads();
+            }
             // ---- q^(k): one warp per fixed range, the 256-thread CTA's tree; then warp 0
             //      takes the decision ----
-            const bool with_q0 = k == 1 && p.vnr_first_iter <= 1;
             if (k >= 1 && warp < kQParts) {
                 const int lo = warp * per, cnt = max(0, min(npart, lo + per) - lo);
                 const double qr = warp_block_sum_fixed(part + lo, cnt);
@@ -218,11 +328,13 @@ __global__ void __launch_bounds__(kFrameThreads, 1) csr_frame_kernel(Params<floa
                     const bool abort_ = !succ && p.rule == kRulePceVnr && k >= p.vnr_first_iter && qv < qp;
                     const bool stop_k = succ || abort_ || k >= p.max_iter;
                     if (lane == 0) {
-                        if (k <= p.trace_iters && p.trace_q) p.trace_q[(long long)(k - 1) * p.frames + f] = qv;
-                        if (stop_k) {
-                            p.flags_out[f] = (unsigned char)((sat ? 1 : 0) | (abort_ ? 2 : 0));
-                            p.iters_out[f] = k;
-                            atomicAdd(&p.ctrl->frame_iters, (unsigned long long)k);
+                        if (rank == 0) {  // both CTAs of a pair decide alike; one writes
+                            if (k <= p.trace_iters && p.trace_q) p.trace_q[(long long)(k - 1) * p.frames + f] = qv;
+                            if (stop_k) {
+                                p.flags_out[f] = (unsigned char)((sat ? 1 : 0) | (abort_ ? 2 : 0));
+                                p.iters_out[f] = k;
+                                atomicAdd(&p.ctrl->frame_iters, (unsigned long long)k);
+                            }
                         }
                         s_stop = stop_k ? 1 : 0;
                     }
@@ -232,39 +344,65 @@ __global__ void __launch_bounds__(kFrameThreads, 1) csr_frame_kernel(Params<floa
             if (tid == 0) s_unsat[(k + 1) & 1] = 0;  // the flag of the next check pass
             __syncthreads();
             if (k >= 1 && s_stop != 0) {
-                for (int v = tid; v < n; v += kFrameThreads) fc.bits[v] = (unsigned char)(app[v] < 0.0f);
+                for (int v0 = (int)rank << kPairShift; v0 < n; v0 += NC << kPairShift) {
+                    const int v = v0 + tid;
+                    if (v < n) fc.bits[v] = (unsigned char)(app[v] < 0.0f);
+                }
                 break;  // the next frame starts behind a barrier
             }
-            // ---- variable pass: APP^(k+1) and its q partials, as virtual 256-thread CTAs ----
-            const bool want_q0 = k == 0 && p.vnr_first_iter <= 1;
+            // ---- variable pass: APP^(k+1) (and, one CTA per frame, its q partials) ----
             const bool trace = k < p.trace_iters;
-            for (int tile = tid / kThreads; tile < ci.vn_tiles; tile += kFrameVirt) {
-                float acc = 0.0f, acc0 = 0.0f;
-#pragma unroll
-                for (int c = 0; c < kVPT; ++c) {
-                    const int v = tile * kVnTile + c * kThreads + vt;
+            if constexpr (NC == 2) {
+                // one variable per thread, in this CTA's 1024-variable blocks; APP into both copies
+                for (int v0 = (int)rank << kPairShift; v0 < n; v0 += NC << kPairShift) {
+                    const int v = v0 + tid;
                     if (v < n) {
                         const int a0 = vptr[v], a1 = vptr[v + 1];
-                        const float Lv = lch[v];
-                        float sum = Lv;
+                        float sum = lch[v];
                         for (int a = a0; a < a1; ++a) sum += c2v[LDPC_IX(p.ctrl, vedge[a], E, kIxCsrMsg)];
                         app[v] = sum;
-                        if (a1 - a0 > 1) {
-                            acc += fabsf(sum);
-                            acc0 += fabsf(Lv);
-                        }
+                        dsmem_st_f32(peer_app + 4u * (unsigned)v, sum);
                         if (trace && p.trace_app) p.trace_app[((size_t)k * p.frames + f) * (size_t)n + v] = sum;
                     }
                 }
-                const int slot = tile * kWarps + (vt >> 5);
-                warp_sum_to(acc, part + slot);
-                if (want_q0) warp_sum_to(acc0, part0 + slot);
+            } else {
+                // as virtual 256-thread CTAs, with the q partials
+                const bool want_q0 = k == 0 && p.vnr_first_iter <= 1;
+                for (int tile = tid / kThreads; tile < ci.vn_tiles; tile += kFrameVirt) {
+                    float acc = 0.0f, acc0 = 0.0f;
+#pragma unroll
+                    for (int c = 0; c < kVPT; ++c) {
+                        const int v = tile * kVnTile + c * kThreads + vt;
+                        if (v < n) {
+                            const int a0 = vptr[v], a1 = vptr[v + 1];
+                            const float Lv = lch[v];
+                            float sum = Lv;
+                            for (int a = a0; a < a1; ++a) sum += c2v[LDPC_IX(p.ctrl, vedge[a], E, kIxCsrMsg)];
+                            app[v] = sum;
+                            if (a1 - a0 > 1) {
+                                acc += fabsf(sum);
+                                acc0 += fabsf(Lv);
+                            }
+                            if (trace && p.trace_app) p.trace_app[((size_t)k * p.frames + f) * (size_t)n + v] = sum;
+                        }
+                    }
+                    const int slot = tile * kWarps + (vt >> 5);
+                    warp_sum_to(acc, part + slot);
+                    if (want_q0) warp_sum_to(acc0, part0 + slot);
+                }
             }
             if (trace && p.trace_c2v) {
                 float* tr = p.trace_c2v + ((size_t)k * p.frames + f) * (size_t)E;
-                for (long long e = tid; e < E; e += kFrameThreads) tr[e] = c2v[e];
+                if constexpr (NC == 2) {  // the messages of this CTA's checks
+                    for (int i = c_first; i < m; i += c_step) {
+                        const int row = rord[i];
+                        for (int e = rptr[row]; e < (int)rptr[row + 1]; ++e) tr[e] = c2v[e];
+                    }
+                } else {
+                    for (long long e = tid; e < E; e += kFrameThreads) tr[e] = c2v[e];
+                }
             }
-            __syncthreads();
+            if constexpr (NC == 2) cluster_barrier(); else __syncthreads();
         }
     }
 }

@@ -582,20 +582,61 @@ size_t frame_schedule_smem(const Job& job, bool fp64) {
     return b <= kFrameSmemMax ? b : 0;
 }
 
+// Launch configuration of the frame-per-cluster kernel: pairs of CTAs.
+cudaLaunchConfig_t pair_config(int grid, size_t smem, cudaStream_t stream, cudaLaunchAttribute* attr) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kFrameThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
 // One decode with the frame-per-CTA schedule (frame_kernel.cuh): every CTA
-// takes whole frames from the queue and decodes each in shared memory.
+// (pair: every cluster of two CTAs) takes whole frames from the queue and
+// decodes each in shared memory.  pair: 0 = automatic (pairs when every frame
+// gets its own pair at once, so that more SMs work), 1 = one CTA per frame,
+// 2 = a pair per frame.
 ldpc_status launch_frame(Workspace& ws, const Job& job, const ldpc_decode_opts& o, cudaStream_t stream,
-                         int32_t* status_out, size_t smem) {
+                         int32_t* status_out, size_t smem, int pair) {
     const int frames = job.frames;
-    auto kernel = job.wts ? csr_frame_kernel<true> : csr_frame_kernel<false>;
-    int dev = 0, sms = 0, per_sm = 0;
+    auto kernel1 = job.wts ? csr_frame_kernel<true, 1> : csr_frame_kernel<false, 1>;
+    auto kernel2 = job.wts ? csr_frame_kernel<true, 2> : csr_frame_kernel<false, 2>;
+    int dev = 0, sms = 0, per_sm = 0, pairs_fit = 0;
     LDPC_TRY(cudaGetDevice(&dev));
     LDPC_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    LDPC_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    LDPC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kFrameThreads, smem));
+    LDPC_TRY(cudaFuncSetAttribute(kernel1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LDPC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel1, kFrameThreads, smem));
     if (per_sm < 1) return LDPC_ERR_CUDA;
-    int grid = std::min(std::min(per_sm * sms, kMaxGrid), frames);
-    if (o.grid_ctas > 0) grid = std::min(grid, o.grid_ctas);
+    if (pair != 1) {
+        cudaLaunchAttribute attr[1];
+        const cudaLaunchConfig_t cfg = pair_config(2, smem, nullptr, attr);
+        cudaError_t e = cudaFuncSetAttribute(kernel2, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&pairs_fit, (const void*)kernel2, &cfg);
+        if (e != cudaSuccess) {
+            if (pair == 2) LDPC_TRY(e);
+            (void)cudaGetLastError();  // automatic selection falls back to one CTA per frame
+            pairs_fit = 0;
+        }
+        if (pair == 2 && pairs_fit < 1) return LDPC_ERR_CUDA;
+        if (pair == 0) pair = (pairs_fit >= 1 && frames <= pairs_fit) ? 2 : 1;
+    }
+    int grid = 0, units = 0;  // CTAs, and frames decoded at once
+    if (pair == 2) {
+        units = std::min(std::min(pairs_fit, kMaxGrid / 2), frames);
+        if (o.grid_ctas > 0) units = std::min(units, std::max(1, o.grid_ctas / 2));
+        grid = 2 * units;
+    } else {
+        grid = std::min(std::min(per_sm * sms, kMaxGrid), frames);
+        if (o.grid_ctas > 0) grid = std::min(grid, o.grid_ctas);
+        units = grid;
+    }
     CodeSet<CsrDev> cs{};
     SlotSizes sz{};
     PackInfo pi{};
@@ -666,11 +707,17 @@ ldpc_status launch_frame(Workspace& ws, const Job& job, const ldpc_decode_opts& 
     {
         const CodeInfo<CsrDev>& ci = cs.c[0];
         const FrameSmem fl = frame_smem_layout(ci.E, ci.n, ci.m, ci.nqb, ci.swords);
-        kernel<<<grid, kFrameThreads, smem, stream>>>(p, ci, fl);
+        if (pair == 2) {
+            cudaLaunchAttribute attr[1];
+            const cudaLaunchConfig_t cfg = pair_config(grid, smem, stream, attr);
+            LDPC_TRY(cudaLaunchKernelEx(&cfg, kernel2, p, ci, fl));
+        } else {
+            kernel1<<<grid, kFrameThreads, smem, stream>>>(p, ci, fl);
+        }
     }
     LDPC_TRY(cudaGetLastError());
     if (timing) LDPC_TRY(cudaEventRecord(ws.ev[2], stream));
-    return finish_decode(ws, o, stream, status_out, grid, grid);
+    return finish_decode(ws, o, stream, status_out, grid, units);
 }
 
 // Schedule of a job: lock-step unless the caller asks for dataflow (QC only).
@@ -696,12 +743,13 @@ ldpc_status launch_decode(Workspace& ws, const Job& job, const ldpc_decode_opts&
         // frame per CTA: asked for, or automatic for one small CSR code (unless the
         // unreachable-barrier test hook asks for a grid barrier, which it has none of)
         const size_t smem = frame_schedule_smem(job, false);
-        if (o.schedule == LDPC_SCHEDULE_FRAME && smem == 0) return LDPC_ERR_INVALID_ARG;
-        if (smem && (o.schedule == LDPC_SCHEDULE_FRAME ||
-                     (o.schedule == LDPC_SCHEDULE_AUTO && o.test_unreachable_barrier == 0)))
-            return launch_frame(ws, job, o, stream, status_out, smem);
+        const bool frame_sched = o.schedule == LDPC_SCHEDULE_FRAME || o.schedule == LDPC_SCHEDULE_FRAME_PAIR;
+        if (frame_sched && smem == 0) return LDPC_ERR_INVALID_ARG;
+        if (smem && (frame_sched || (o.schedule == LDPC_SCHEDULE_AUTO && o.test_unreachable_barrier == 0)))
+            return launch_frame(ws, job, o, stream, status_out, smem,
+                                o.schedule == LDPC_SCHEDULE_FRAME ? 1 : (o.schedule == LDPC_SCHEDULE_FRAME_PAIR ? 2 : 0));
     }
-    if (o.schedule == LDPC_SCHEDULE_FRAME) return LDPC_ERR_INVALID_ARG;
+    if (o.schedule == LDPC_SCHEDULE_FRAME || o.schedule == LDPC_SCHEDULE_FRAME_PAIR) return LDPC_ERR_INVALID_ARG;
     const int frames = job.frames;
     // the weighted kernel is a separate instantiation: the unweighted one carries no weight code
     auto kernel = job.wts ? bp_decode_kernel<T, Code, true> : bp_decode_kernel<T, Code, false>;
@@ -881,7 +929,7 @@ ldpc_status check_decode_args(const ldpc_graph* graph, int32_t frames, const voi
         o.barrier_timeout_ms < 0 || o.groups < 0 || o.groups > kMaxGroups)
         return LDPC_ERR_INVALID_ARG;
     if (o.debug_guards != 0 && o.debug_guards != 1) return LDPC_ERR_INVALID_ARG;
-    if (o.schedule < LDPC_SCHEDULE_AUTO || o.schedule > LDPC_SCHEDULE_FRAME || o.flow_lag < 0 ||
+    if (o.schedule < LDPC_SCHEDULE_AUTO || o.schedule > LDPC_SCHEDULE_FRAME_PAIR || o.flow_lag < 0 ||
         (o.schedule == LDPC_SCHEDULE_DATAFLOW && graph->kind != 1))
         return LDPC_ERR_INVALID_ARG;
     if ((long long)frames * graph->n > (1LL << 40)) return LDPC_ERR_INVALID_ARG;

@@ -67,7 +67,7 @@ class ldpc_decode_opts(ctypes.Structure):
                 ("groups", ctypes.c_int32), ("schedule", ctypes.c_int32), ("flow_lag", ctypes.c_int32),
                 ("debug_guards", ctypes.c_int32)]
 
-SCHEDULES = {"auto": 0, "lockstep": 1, "dataflow": 2, "frame": 3}
+SCHEDULES = {"auto": 0, "lockstep": 1, "dataflow": 2, "frame": 3, "frame_pair": 4}
 
 
 def _load():

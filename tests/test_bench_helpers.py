@@ -55,12 +55,17 @@ def test_algorithmic_bytes():
 
 
 def test_frame_kernel_naming_follows_the_shared_memory_rule():
-    """The bench names the frame-per-CTA kernel for the n = 4096 CSR code (about
+    """The bench names the frame-per-CTA (or per-pair) kernel for the n = 4096 CSR code (about
     148 KB of shared memory) and lock-step for QC codes and for a CSR code of
     60000 edges, whose messages alone exceed the 220 KB limit."""
     small = gen.workload_code(1)
     assert bench.frame_schedule_applies(small)
-    assert bench.decoder_kernel_name(small) == "csr_frame_kernel<false>"
+    assert bench.decoder_kernel_name(small) == "csr_frame_kernel<false,1>"
+    # a CTA pair per frame when every frame gets its own pair (64 frames on 152 SMs), one CTA otherwise
+    assert bench.decoder_kernel_name(small, "auto", 64, 152) == "csr_frame_kernel<false,2>"
+    assert bench.decoder_kernel_name(small, "auto", 100, 152) == "csr_frame_kernel<false,1>"
+    assert bench.decoder_kernel_name(small, "frame", 64, 152) == "csr_frame_kernel<false,1>"
+    assert bench.decoder_kernel_name(small, "frame_pair") == "csr_frame_kernel<false,2>"
     assert bench.decoder_kernel_name(small, "lockstep") == "bp_decode_kernel<float,CsrDev>"
     big = gen.random_csr_code(20000, 10000, 3, {6: 10000}, seed=77)
     assert not bench.frame_schedule_applies(big)

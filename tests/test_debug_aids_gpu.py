@@ -2,7 +2,7 @@
 (opts.debug_guards, checked by ldpc_graph_check_guards / ldpc_batch_check_guards)
 and the index-checking build (-DLDPC_BOUNDS_CHECK), which must find no index
 outside its array on decodes that cover every kernel path: QC and CSR codes,
-lock-step, dataflow and frame-per-CTA schedules, FP32 and FP64, learned weights, a batch of
+lock-step, dataflow, frame-per-CTA and frame-per-pair schedules, FP32 and FP64, learned weights, a batch of
 codes, ragged item tails and refilled slots.  Every other GPU parity test
 already decodes with guards and checks them (tests/_decode_helpers.py)."""
 import os
@@ -74,6 +74,7 @@ run(tbp, gen.workload_frames(7, tbp, frames=6, beta=0.8), 60, schedule="dataflow
 csr = gen.workload_code(1)
 run(csr, gen.workload_frames(1, csr, frames=9), 50)
 run(csr, gen.workload_frames(1, csr, frames=9), 50, schedule="frame", grid_ctas=2)
+run(csr, gen.workload_frames(1, csr, frames=9), 50, schedule="frame_pair", grid_ctas=4)
 run(csr, gen.workload_frames(1, csr, frames=3), 10, fp64=True)
 reg = gen.workload_code(6, Z=64)
 codes = [qc, reg]

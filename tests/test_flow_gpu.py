@@ -187,7 +187,9 @@ def test_frame_schedule_equals_lockstep(ldpc, case):
     for rule in ("pce_vnr", "pce", "none"):
         ref = gpu_decode(ldpc, g, fr.llr, fr.syndrome, 60, rule, trace_iters=5, schedule="lockstep")
         for opts in (dict(schedule="frame"), dict(schedule="auto"), dict(schedule="frame", grid_ctas=2),
-                     dict(schedule="frame", vnr_first_iter=1)):
+                     dict(schedule="frame", vnr_first_iter=1), dict(schedule="frame_pair"),
+                     dict(schedule="frame_pair", grid_ctas=2), dict(schedule="frame_pair", grid_ctas=6),
+                     dict(schedule="frame_pair", vnr_first_iter=1)):
             r = ref
             if opts.get("vnr_first_iter") == 1:
                 r = gpu_decode(ldpc, g, fr.llr, fr.syndrome, 60, rule, trace_iters=5, schedule="lockstep",
@@ -208,19 +210,21 @@ def test_frame_schedule_learned_weights_and_batch(ldpc):
     w = torch.from_numpy(np.random.default_rng(5).uniform(0.7, 1.1, size=(4, C)).astype(np.float32)).to(dev)
     llr, syn = torch.from_numpy(fr.llr).to(dev), torch.from_numpy(fr.syndrome).to(dev)
     out = {}
-    for sched in ("lockstep", "frame"):
+    for sched in ("lockstep", "frame", "frame_pair"):
         b, f, i = plan.decode(llr, syn, w, 80, "pce_vnr", schedule=sched)
         out[sched] = dict(bits=b.cpu().numpy(), flags=f.cpu().numpy(), iters=i.cpu().numpy())
     same(out["frame"], out["lockstep"], "weights")
+    same(out["frame_pair"], out["lockstep"], "weights, pair")
     plan.close()
     batch = ldpc.Batch([g], np.zeros(10, dtype=np.int32))
     res = {}
-    for sched in ("lockstep", "frame"):
+    for sched in ("lockstep", "frame", "frame_pair"):
         o = batch.decode(llr.reshape(-1), syn.reshape(-1), 80, "pce_vnr", schedule=sched, debug_guards=True)
         torch.cuda.synchronize()
         assert ldpc.ldpc_batch_check_guards(batch.handle) == ldpc.LDPC_OK
         res[sched] = dict(bits=o[0].cpu().numpy(), flags=o[1].cpu().numpy(), iters=o[2].cpu().numpy())
     same(res["frame"], res["lockstep"], "batch")
+    same(res["frame_pair"], res["lockstep"], "batch, pair")
     batch.close()
     g.close()
 
@@ -235,8 +239,9 @@ def test_frame_schedule_refused_where_it_does_not_apply(ldpc):
         else:
             fr = gen.workload_frames(2 if hasattr(code, "shifts") else 1, code, frames=2)
         g = ldpc.Graph.from_code(code)
-        with pytest.raises(ldpc.LdpcError) as ei:
-            ldpc.decode(g, torch.from_numpy(fr.llr).to(dev), torch.from_numpy(fr.syndrome).to(dev), 5, "pce",
-                        schedule="frame", **kw)
-        assert ei.value.status == ldpc.LDPC_ERR_INVALID_ARG
+        for sched in ("frame", "frame_pair"):
+            with pytest.raises(ldpc.LdpcError) as ei:
+                ldpc.decode(g, torch.from_numpy(fr.llr).to(dev), torch.from_numpy(fr.syndrome).to(dev), 5, "pce",
+                            schedule=sched, **kw)
+            assert ei.value.status == ldpc.LDPC_ERR_INVALID_ARG
         g.close()
