@@ -141,12 +141,13 @@ def decoder_kernel_name(code, schedule="auto", frames=None, sms=152) -> str:
     return "bp_decode_kernel<float,%s>" % ("QcDev" if qc else "CsrDev")
 
 
-DECODER_SOURCES = ("bp_kernels.cuh", "flow_kernel.cuh", "frame_kernel.cuh", "cn_math.cuh", "device_types.h",
-                   "host_common.h", "ldpc_api.cu")
+# the lock-step decoder's device code and its launcher (the dataflow and frame
+# kernels live in files of their own and do not change it)
+DECODER_SOURCES = ("bp_kernels.cuh", "cn_math.cuh", "device_types.h", "host_common.h", "ldpc_api.cu")
 
 
 def kernel_source_hash() -> str:
-    """Hash of the sources the persistent decoder kernel is built from."""
+    """Hash of the sources the lock-step persistent decoder kernel is built from."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2507_03509_gb300", "csrc")
     for name in DECODER_SOURCES:
