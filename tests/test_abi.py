@@ -115,3 +115,36 @@ def test_index_checking_build_compiles_and_exports(ldpc):
     lib = ctypes.CDLL(path)
     for name in declared_functions():
         assert hasattr(lib, name), name
+
+
+def header_constants():
+    """Integer constants of include/ldpc.h: enum members (NAME = value) and
+    #define NAME value lines (a value of the form (a * b * c) is multiplied out)."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    consts = {k: int(v) for k, v in re.findall(r"\b(LDPC_[A-Z0-9_]+)\s*=\s*(\d+)", text)}
+    for name, expr in re.findall(r"#define\s+(LDPC_[A-Z0-9_]+)\s+(.+)", text):
+        factors = re.findall(r"(\d+)u?", expr)
+        if factors and re.fullmatch(r"[\s()*\du]+", expr.strip()):
+            val = 1
+            for f in factors:
+                val *= int(f)
+            consts[name] = val
+    return consts
+
+
+def test_binding_constants_match_the_header(ldpc):
+    """The Python binding's status codes, rules, flags, schedule values and
+    no-alloc scratch size are the header's (the binding restates them)."""
+    h = header_constants()
+    for name in ("LDPC_OK", "LDPC_ERR_INVALID_ARG", "LDPC_ERR_INVALID_GRAPH", "LDPC_ERR_OOM", "LDPC_ERR_CUDA",
+                 "LDPC_ERR_TIMEOUT", "LDPC_ERR_TOO_LARGE", "LDPC_ERR_BOUNDS", "LDPC_TERM_NONE", "LDPC_TERM_PCE",
+                 "LDPC_TERM_PCE_VNR", "LDPC_FLAG_SUCCESS", "LDPC_FLAG_ABORTED"):
+        assert getattr(ldpc, name) == h[name], name
+    assert ldpc.NOALLOC_SCRATCH_BYTES == h["LDPC_NOALLOC_SCRATCH_BYTES"]
+    schedules = {"auto": "LDPC_SCHEDULE_AUTO", "lockstep": "LDPC_SCHEDULE_LOCKSTEP",
+                 "dataflow": "LDPC_SCHEDULE_DATAFLOW", "frame": "LDPC_SCHEDULE_FRAME",
+                 "frame_pair": "LDPC_SCHEDULE_FRAME_PAIR"}
+    assert set(ldpc.SCHEDULES) == set(schedules)
+    for key, name in schedules.items():
+        assert ldpc.SCHEDULES[key] == h[name], key
+    assert ldpc.RULES == {"none": h["LDPC_TERM_NONE"], "pce": h["LDPC_TERM_PCE"], "pce_vnr": h["LDPC_TERM_PCE_VNR"]}
