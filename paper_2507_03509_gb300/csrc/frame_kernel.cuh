@@ -64,10 +64,11 @@ __device__ __forceinline__ void dsmem_st_f32(unsigned addr, float v) {
 __device__ __forceinline__ void dsmem_st_s32(unsigned addr, int v) {
     asm volatile("st.shared::cluster.s32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
 }
-__device__ __forceinline__ void dsmem_or_b32(unsigned addr, unsigned v) {
+// returns the word's previous value
+__device__ __forceinline__ unsigned dsmem_or_b32(unsigned addr, unsigned v) {
     unsigned old;
     asm volatile("atom.shared::cluster.or.b32 %0, [%1], %2;" : "=r"(old) : "r"(addr), "r"(v) : "memory");
-    (void)old;
+    return old;
 }
 // All threads of every CTA of the cluster: the cluster's shared-memory writes
 // before it are visible to every thread's reads after it.
@@ -272,7 +273,7 @@ __global__ void __launch_bounds__(kFrameThreads, 1) csr_frame_kernel(Params<floa
             }
             if (want_synd && __any_sync(0xffffffffu, unsat) && lane == 0) {
                 atomicOr(&s_unsat[k & 1], 1);
-                if constexpr (NC == 2) dsmem_or_b32(peer_unsat + 4u * (unsigned)(k & 1), 1u);
+                if constexpr (NC == 2) (void)dsmem_or_b32(peer_unsat + 4u * (unsigned)(k & 1), 1u);
             }
             const bool with_q0 = k == 1 && p.vnr_first_iter <= 1;
             if constexpr (NC == 2) {
