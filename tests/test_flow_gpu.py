@@ -166,7 +166,7 @@ def degenerate_csr():
     return gen.CSRCode(len(rows), 13, rowptr, np.concatenate([np.asarray(r, np.int32) for r in rows]))
 
 
-@pytest.mark.parametrize("case", ["csr_n4096", "fd_n256", "degenerate", "decodable"])
+@pytest.mark.parametrize("case", ["csr_n4096", "fd_n256", "degenerate", "decodable", "degree24"])
 def test_frame_schedule_equals_lockstep(ldpc, case):
     if case == "csr_n4096":
         code = gen.workload_code(1)
@@ -180,9 +180,14 @@ def test_frame_schedule_equals_lockstep(ldpc, case):
         x = rng.integers(0, 2, size=(11, code.n)).astype(np.uint8)
         llr = ((1.0 - 2.0 * x) + 1.1 * rng.standard_normal(x.shape)).astype(np.float32) * 1.3
         fr = gen.Frames(x, llr, gen.syndrome(code, x), np.full(11, 1.1))
-    else:
+    elif case == "decodable":
         code = gen.random_csr_code(2000, 1000, 3, {6: 1000}, seed=4242)
         fr = gen.make_frames(code, np.full(12, 0.78), seeds=range(800, 812))
+    else:
+        # checks of degree about 24 (the generic check path) spread over both CTAs of a
+        # pair, with variables in both CTAs' blocks
+        code = gen.random_csr_code(2048, 256, 3, {24: 256}, seed=4343)
+        fr = gen.make_frames(code, np.full(10, 0.6), seeds=range(900, 910))
     g = ldpc.Graph.from_code(code)
     for rule in ("pce_vnr", "pce", "none"):
         ref = gpu_decode(ldpc, g, fr.llr, fr.syndrome, 60, rule, trace_iters=5, schedule="lockstep")
